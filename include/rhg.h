@@ -1,0 +1,223 @@
+/*
+ * rhg.h -- C ABI of the GB300 generator of threshold random hyperbolic graphs
+ * (band-based neighbour query of von Looz, Ozdayi, Laue, Meyerhenke,
+ * "Generating massive complex networks with hyperbolic geometry faster in
+ * practice", arXiv:1606.09481).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named d_* are device pointers on the CUDA device that is current
+ *   for the calling thread; pointers named h_* (and every struct pointer) are
+ *   host pointers.  The library never frees or retains caller memory.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Device work is enqueued on it in order; an entry point that
+ *   returns a count to the host (m, R) synchronises that stream once, after the
+ *   count is known.
+ * - The caller provides all device memory: a workspace whose size
+ *   rhg_workspace_bytes() reports, and the output buffers.  Inside an entry
+ *   point the library allocates no device or host memory.
+ * - Vertex ids are the Philox counter indices 0..n-1 (uint32).  An edge {u,v}
+ *   is reported once as the pair (u, v) with u < v; the order of pairs is
+ *   unspecified.  CSR rows list both directions with ascending columns.
+ * - Every entry point returns an rhg_status.  Invalid arguments are reported
+ *   before any device work; nothing aborts the process.  After RHG_ERR_CUDA the
+ *   CUDA context may be unusable (the failing CUDA error is in
+ *   rhg_result.cuda_error when a result pointer was given).
+ *
+ * The model (all FP64):
+ * - alpha > 1/2, k > 0, 2 <= n <= 2^32 - 1.  R solves Krioukov's Eq. 22 for
+ *   average degree k (paper Sec. III-B, getTargetRadius), unless R_override > 0.
+ * - Point i: phi_i ~ U[0, 2pi), r_i by inverse CDF of Eq. 1 (Sec. II and
+ *   Alg. 1), both from Philox4x64-10 with counter (i,0,0,0) and key (seed,0).
+ * - Bands: num_bands rings with geometric boundaries of ratio band_ratio
+ *   (Sec. III-A; defaults ceil(log2 n) and 0.9).
+ * - Edge {v,w} iff the FP64 value cosh r_v cosh r_w - sinh r_v sinh r_w
+ *   cos|phi_v - phi_w| is <= cosh R (Eq. 3 and the threshold test of Alg. 1),
+ *   evaluated as one fixed sequence of rounded IEEE operations with the
+ *   library's deterministic exp/log/cos; the edge set is therefore a pure
+ *   function of (n, k, alpha, seed) and does not depend on num_bands,
+ *   band_ratio or the filter flags.
+ */
+#ifndef RHG_H
+#define RHG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rhg_status {
+    RHG_OK = 0,
+    RHG_ERR_INVALID_ARG = 1,  /* a parameter or buffer is outside its domain          */
+    RHG_ERR_NO_SOLUTION = 2,  /* no R gives average degree k (Eq. 22 peaks below k)   */
+    RHG_ERR_OOM = 3,          /* the workspace passed is smaller than required        */
+    RHG_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed          */
+    RHG_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up                   */
+    RHG_ERR_OVERFLOW = 6      /* the output buffer holds fewer entries than required;
+                                 rhg_result.m reports the exact edge count            */
+} rhg_status;
+
+#define RHG_MAX_BANDS 64u
+
+/* flags */
+#define RHG_FLAG_FP64_ONLY 0x1u  /* evaluate every candidate with the FP64 predicate
+                                    (no FP32 filter); same edge set, slower          */
+
+/* Parameters of one graph (Alg. 1 input: n, average degree k, alpha = (gamma-1)/2). */
+typedef struct rhg_params {
+    uint64_t n;          /* vertices, 2 <= n <= 2^32 - 1                              */
+    double k;            /* target average degree (Eq. 22), > 0                       */
+    double alpha;        /* radial dispersion, > 1/2 and <= 100; gamma = 2 alpha + 1  */
+    uint64_t seed;       /* Philox key word 0                                         */
+    uint32_t num_bands;  /* 0 = ceil(log2 n); otherwise 1..64 (Sec. III-A)            */
+    uint32_t flags;      /* RHG_FLAG_*                                                */
+    double band_ratio;   /* 0 = 0.9; otherwise > 0 (Sec. III-A, ratio p)              */
+    double R_override;   /* > 0: use this disk radius instead of solving Eq. 22       */
+} rhg_params;
+
+/* Per-call report, filled on the host when the pointer is non-NULL. */
+typedef struct rhg_result {
+    uint64_t m;               /* undirected edges of the graph (exact, also on OVERFLOW) */
+    double R;                 /* disk radius used                                        */
+    uint32_t num_bands;       /* bands used                                              */
+    int32_t cuda_error;       /* cudaError_t of the failing call when status is CUDA     */
+    uint64_t candidates;      /* candidate pairs examined by the range query             */
+    uint64_t near_threshold;  /* candidates with |L - cosh R| <= 1e-12 cosh R            */
+    uint64_t rechecks;        /* candidates the FP32 filter sent to the FP64 predicate   */
+} rhg_result;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *rhg_status_str(int status);
+
+/* ABI version of this header: 1. */
+int rhg_version(void);
+
+/*
+ * rhg_plan_workspace_bytes -- device workspace rhg_target_radius and rhg_plan
+ * need (a few KB of per-graph metadata).  Host-only.
+ */
+size_t rhg_plan_workspace_bytes(void);
+
+/*
+ * rhg_target_radius -- R such that Eq. 22 (Krioukov et al., with zeta = 1) gives
+ * average degree k (paper Sec. III-B, getTargetRadius): the largest integer
+ * grid point j in [0, 255] with kbar(j) > k brackets the crossing, then binary
+ * search until the bracket holds adjacent doubles; R is the upper end, the
+ * smallest double found with kbar(R) <= k.  Runs one kernel on `stream` in
+ * d_workspace (>= rhg_plan_workspace_bytes()) and synchronises the stream.
+ * Errors: INVALID_ARG (n, k, alpha out of domain, NULL pointer), OOM (workspace
+ * too small), NO_SOLUTION, CUDA.
+ */
+int rhg_target_radius(uint64_t n, double k, double alpha, void *d_workspace, size_t workspace_bytes,
+                      void *stream, double *R_out);
+
+/*
+ * rhg_plan -- R and the band boundaries c_0 = 0 < c_1 < ... < c_B = R that
+ * rhg_generate_* use for these parameters (Sec. III-A; c_{j+1} - c_j =
+ * c_1 p^j, c_1 = (1-p) R / (1-p^B)).  Computed on the device in d_workspace
+ * (>= rhg_plan_workspace_bytes()); synchronises the stream.  h_c receives
+ * B + 1 doubles (it must hold RHG_MAX_BANDS + 1); *num_bands_out receives B.
+ */
+int rhg_plan(const rhg_params *p, void *d_workspace, size_t workspace_bytes, void *stream, double *R_out,
+             double *h_c, uint32_t *num_bands_out);
+
+/*
+ * rhg_workspace_bytes -- device workspace that rhg_generate_pairs needs for p
+ * (capacity_entries = 0) or that rhg_generate_csr needs for an output of
+ * capacity_entries directed column entries.  Host-only; no device work.
+ */
+int rhg_workspace_bytes(const rhg_params *p, uint64_t capacity_entries, size_t *bytes);
+
+/*
+ * rhg_sample_points -- the points of Alg. 1 ("draw phi", "draw r"), by id:
+ * d_phi[i], d_r[i] for i < n (FP64; Philox4x64-10, inverse CDF of Eq. 1).
+ * d_workspace must hold rhg_plan_workspace_bytes().  Writes R to *R_out and
+ * synchronises the stream.
+ */
+int rhg_sample_points(const rhg_params *p, void *d_workspace, size_t workspace_bytes,
+                      double *d_phi, double *d_r, void *stream, double *R_out);
+
+/*
+ * rhg_generate_pairs -- the whole hot path of Alg. 1 on the device: R, band
+ * boundaries, sampling, band assignment, radix sort by (band, phi), windows
+ * (getMinMaxPhi), binary search, candidate test, and compaction of the edges
+ * into d_pairs as m pairs (u, v), u < v, uint32 (2 m words).
+ * capacity_edges is the number of pairs d_pairs holds; if m exceeds it the call
+ * writes no pairs and returns RHG_ERR_OVERFLOW with result->m = m.
+ */
+int rhg_generate_pairs(const rhg_params *p, void *d_workspace, size_t workspace_bytes,
+                       uint32_t *d_pairs, uint64_t capacity_edges, void *stream,
+                       rhg_result *result);
+
+/*
+ * rhg_generate_pairs_host -- rhg_generate_pairs followed by a copy of the m
+ * pairs into host memory h_pairs (2 * h_capacity_edges uint32 words; pinned
+ * memory makes the copy asynchronous-capable).  Synchronises the stream.
+ * OVERFLOW if m exceeds either capacity.
+ */
+int rhg_generate_pairs_host(const rhg_params *p, void *d_workspace, size_t workspace_bytes,
+                            uint32_t *d_pairs, uint64_t capacity_edges, uint32_t *h_pairs,
+                            uint64_t h_capacity_edges, void *stream, rhg_result *result);
+
+/*
+ * rhg_generate_csr -- the same graph as symmetric CSR: d_row_ptr (n + 1 uint64)
+ * and d_col (2 m uint32, ascending within each row).  capacity_entries is the
+ * number of uint32 d_col holds; the workspace must hold
+ * rhg_workspace_bytes(p, capacity_entries).  OVERFLOW if 2 m > capacity_entries.
+ */
+int rhg_generate_csr(const rhg_params *p, void *d_workspace, size_t workspace_bytes,
+                     uint64_t *d_row_ptr, uint32_t *d_col, uint64_t capacity_entries,
+                     void *stream, rhg_result *result);
+
+/*
+ * rhg_edges_from_points -- the range query of Alg. 1 on caller-given points
+ * (d_phi[i] in [0, 2pi), d_r[i] in [0, R], FP64, by id) with disk radius R:
+ * bands, sort, windows, candidate test and compaction, as in
+ * rhg_generate_pairs.  The workspace must hold rhg_workspace_bytes_points(n,
+ * num_bands).  Points outside the domain give INVALID_ARG.
+ */
+int rhg_workspace_bytes_points(uint64_t n, uint32_t num_bands, size_t *bytes);
+int rhg_edges_from_points(const double *d_phi, const double *d_r, uint64_t n, double R,
+                          uint32_t num_bands, double band_ratio, uint32_t flags,
+                          void *d_workspace, size_t workspace_bytes, uint32_t *d_pairs,
+                          uint64_t capacity_edges, void *stream, rhg_result *result);
+
+/*
+ * rhg_dm_eval -- the library's deterministic FP64 functions on a device array,
+ * for verification against an independent implementation: fn = 0 exp, 1 log,
+ * 2 cos, 3 cosh, 4 sinh.  d_out[i] = f(d_in[i]), i < count.
+ */
+int rhg_dm_eval(int fn, const double *d_in, double *d_out, uint64_t count, void *stream);
+
+/*
+ * Profiling aids (not part of the method).
+ *
+ * rhg_set_stage_events -- when `events` is non-NULL, every later generate /
+ * edges_from_points call records events[2 s] and events[2 s + 1] (cudaEvent_t
+ * handles created by the caller, passed as void*) on its stream immediately
+ * before and after stage s, for s < count / 2 and s < RHG_NUM_STAGES, so that
+ * cudaEventElapsedTime gives each stage's device time.  Process-wide and not
+ * thread-safe; NULL switches it off.  Stages that do not run record nothing.
+ *
+ * rhg_launch_count -- number of kernels this library has launched in this
+ * process so far (all devices, all threads).
+ */
+#define RHG_STAGE_PLAN 0u     /* R solve and band boundaries                     */
+#define RHG_STAGE_SAMPLE 1u   /* Philox sampling / point load and band histogram */
+#define RHG_STAGE_SORT 2u     /* band offsets and radix sort by (band, angle)    */
+#define RHG_STAGE_GATHER 3u   /* sorted structure-of-arrays                      */
+#define RHG_STAGE_COUNT 4u    /* range query, count pass                         */
+#define RHG_STAGE_SCAN 5u     /* exclusive scan of the counts                    */
+#define RHG_STAGE_EMIT 6u     /* range query, emit pass                          */
+#define RHG_STAGE_CSR 7u      /* CSR sort and row pointers                       */
+#define RHG_NUM_STAGES 8u
+int rhg_set_stage_events(void *const *events, uint32_t count);
+uint64_t rhg_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RHG_H */

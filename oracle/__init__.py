@@ -85,6 +85,11 @@ def lib() -> ctypes.CDLL:
             L.ro_band_count_subset.restype = _i64
             L.ro_openmp_threads.restype = ctypes.c_int
             L.ro_constants.argtypes = [_p]
+            L.ro_prepare.argtypes = [_u64, _p, _p, _dbl, _u32, _dbl]
+            L.ro_prepare.restype = _p
+            L.ro_prepared_count.argtypes = [_p, _p, _u64, _p]
+            L.ro_prepared_count.restype = _i64
+            L.ro_prepared_free.argtypes = [_p]
             _lib = L
     return _lib
 
@@ -243,6 +248,31 @@ def band_count_subset(phi, r, R: float, B: int, p: float, ids: np.ndarray):
     m = lib().ro_band_count_subset(len(phi), _ptr(phi), _ptr(r), R, B, p, _ptr(ids), len(ids),
                                    ctypes.byref(nt), None)
     return int(m), int(nt.value)
+
+
+class Prepared:
+    """Band structure of Alg. 1 built once over given points; count_edges(ids)
+    runs the outward range queries of those vertices (OpenMP when available)."""
+
+    def __init__(self, phi, r, R: float, B: int, p: float = 0.9):
+        self.phi, self.r = _pts(phi, r)
+        self.h = lib().ro_prepare(len(self.phi), _ptr(self.phi), _ptr(self.r), R, B, p)
+        if not self.h:
+            raise MemoryError("ro_prepare failed")
+
+    def count_edges(self, ids):
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        nt = ctypes.c_int32(0)
+        m = lib().ro_prepared_count(self.h, _ptr(ids), len(ids), ctypes.byref(nt))
+        return int(m), int(nt.value)
+
+    def close(self):
+        if self.h:
+            lib().ro_prepared_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
 
 
 def openmp_threads() -> int:

@@ -692,3 +692,63 @@ void ro_constants(double *out)
     out[4] = RO_LN2_LO; out[5] = RO_TWO_OVER_PI; out[6] = RO_PIO2_1; out[7] = RO_PIO2_2;
     out[8] = RO_PIO2_3; out[9] = RO_SQRT_HALF;
 }
+
+/* The same band structure built once and queried many times (timed CPU baseline). */
+typedef struct {
+    uint64_t n;
+    const double *phi, *r;
+    ro_pts P;
+    ro_bands S;
+} ro_prepared;
+
+void *ro_prepare(uint64_t n, const double *phi, const double *r, double R, uint32_t B, double p)
+{
+    ro_prepared *h = (ro_prepared *)calloc(1, sizeof(ro_prepared));
+    if (!h) return NULL;
+    h->n = n;
+    h->phi = phi;
+    h->r = r;
+    if (ro_pts_init(&h->P, n, r, R) != RO_OK) { free(h); return NULL; }
+    if (ro_bands_build(&h->S, n, phi, r, R, B, p) != RO_OK) {
+        ro_pts_free(&h->P);
+        ro_bands_free(&h->S);
+        free(h);
+        return NULL;
+    }
+    return h;
+}
+
+int64_t ro_prepared_count(void *handle, const uint32_t *ids, uint64_t nids, int32_t *threads)
+{
+    ro_prepared *h = (ro_prepared *)handle;
+    int64_t m = 0;
+    int nt = 1;
+#ifdef _OPENMP
+#pragma omp parallel reduction(+ : m)
+    {
+#pragma omp single
+        nt = omp_get_num_threads();
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t q = 0; q < (int64_t)nids; ++q) {
+            ro_stats s = {0, 0, 0};
+            m += ro_query_range(&h->S, &h->P, h->phi, h->r, ids[q], (uint64_t)ids[q] + 1, NULL, 0, 0, &s);
+        }
+    }
+#else
+    for (uint64_t q = 0; q < nids; ++q) {
+        ro_stats s = {0, 0, 0};
+        m += ro_query_range(&h->S, &h->P, h->phi, h->r, ids[q], (uint64_t)ids[q] + 1, NULL, 0, 0, &s);
+    }
+#endif
+    if (threads) *threads = nt;
+    return m;
+}
+
+void ro_prepared_free(void *handle)
+{
+    ro_prepared *h = (ro_prepared *)handle;
+    if (!h) return;
+    ro_pts_free(&h->P);
+    ro_bands_free(&h->S);
+    free(h);
+}

@@ -1,0 +1,319 @@
+"""GB300 generator of threshold random hyperbolic graphs (arXiv:1606.09481).
+
+Thin ctypes binding over the C ABI declared in ``include/rhg.h``: argument
+marshalling only.  Every step of the method runs in the CUDA kernels of
+``librhg.so``; PyTorch provides device memory and the current stream.  There is
+no fallback: if the library is not built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+from .build import LIB, build
+
+__all__ = [
+    "RhgError", "Params", "Result", "load", "status_str", "target_radius", "plan", "workspace_bytes",
+    "sample_points", "generate_pairs", "generate_pairs_host", "generate_csr", "edges_from_points",
+    "dm_eval", "default_bands", "FLAG_FP64_ONLY", "MAX_BANDS", "build",
+]
+
+OK, INVALID_ARG, NO_SOLUTION, OOM, CUDA_ERROR, TIMEOUT, OVERFLOW = range(7)
+FLAG_FP64_ONLY = 0x1
+MAX_BANDS = 64
+DM_FUNCS = {"exp": 0, "log": 1, "cos": 2, "cosh": 3, "sinh": 4}
+
+_c_u64, _c_u32, _c_dbl, _c_size, _p = (ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
+                                       ctypes.c_size_t, ctypes.c_void_p)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n", _c_u64), ("k", _c_dbl), ("alpha", _c_dbl), ("seed", _c_u64),
+                ("num_bands", _c_u32), ("flags", _c_u32), ("band_ratio", _c_dbl),
+                ("R_override", _c_dbl)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("m", _c_u64), ("R", _c_dbl), ("num_bands", _c_u32), ("cuda_error", ctypes.c_int32),
+                ("candidates", _c_u64), ("near_threshold", _c_u64), ("rechecks", _c_u64)]
+
+    def asdict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class RhgError(RuntimeError):
+    def __init__(self, status: int, where: str, result: Result | None = None):
+        self.status = status
+        self.result = result
+        super().__init__(f"{where}: {status_str(status)} ({status})")
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load librhg.so (built by build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"CUDA library {LIB} is not built; run paper_1606_09481_gb300.build()")
+    L = ctypes.CDLL(LIB)
+    L.rhg_status_str.restype = ctypes.c_char_p
+    L.rhg_status_str.argtypes = [ctypes.c_int]
+    L.rhg_version.restype = ctypes.c_int
+    L.rhg_plan_workspace_bytes.restype = _c_size
+    L.rhg_plan_workspace_bytes.argtypes = []
+    L.rhg_target_radius.argtypes = [_c_u64, _c_dbl, _c_dbl, _p, _c_size, _p, ctypes.POINTER(_c_dbl)]
+    L.rhg_plan.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, ctypes.POINTER(_c_dbl), _p,
+                           ctypes.POINTER(_c_u32)]
+    L.rhg_workspace_bytes.argtypes = [ctypes.POINTER(Params), _c_u64, ctypes.POINTER(_c_size)]
+    L.rhg_workspace_bytes_points.argtypes = [_c_u64, _c_u32, ctypes.POINTER(_c_size)]
+    L.rhg_sample_points.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _p, _p, ctypes.POINTER(_c_dbl)]
+    L.rhg_generate_pairs.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _c_u64, _p,
+                                     ctypes.POINTER(Result)]
+    L.rhg_generate_pairs_host.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _c_u64, _p, _c_u64, _p,
+                                          ctypes.POINTER(Result)]
+    L.rhg_generate_csr.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _p, _c_u64, _p,
+                                   ctypes.POINTER(Result)]
+    L.rhg_edges_from_points.argtypes = [_p, _p, _c_u64, _c_dbl, _c_u32, _c_dbl, _c_u32, _p, _c_size, _p,
+                                        _c_u64, _p, ctypes.POINTER(Result)]
+    L.rhg_dm_eval.argtypes = [ctypes.c_int, _p, _p, _c_u64, _p]
+    L.rhg_set_stage_events.argtypes = [_p, _c_u32]
+    L.rhg_launch_count.restype = _c_u64
+    L.rhg_launch_count.argtypes = []
+    _lib = L
+    return L
+
+
+STAGES = ("plan", "sample", "sort", "gather", "count", "scan", "emit", "csr")
+
+
+class StageTimer:
+    """Per-stage CUDA events recorded by the library on its stream (profiling)."""
+
+    def __init__(self):
+        torch = _torch()
+        self.events = [torch.cuda.Event(enable_timing=True) for _ in range(2 * len(STAGES))]
+        for e in self.events:  # torch creates the CUDA event on first record
+            e.record()
+        torch.cuda.synchronize()
+        self._arr = (ctypes.c_void_p * len(self.events))(*[e.cuda_event for e in self.events])
+        self.totals = {s: 0.0 for s in STAGES}
+        self.recorded = {s: 0 for s in STAGES}
+
+    def __enter__(self):
+        load().rhg_set_stage_events(self._arr, len(self.events))
+        return self
+
+    def __exit__(self, *exc):
+        load().rhg_set_stage_events(None, 0)
+
+    def reset_marks(self):
+        """Re-record every event so that a stage that does not run reads ~0."""
+        for e in self.events:
+            e.record()
+
+    def accumulate(self):
+        """After a synchronised call: add each stage's elapsed ms to the totals."""
+        for i, s in enumerate(STAGES):
+            ms = self.events[2 * i].elapsed_time(self.events[2 * i + 1])
+            if ms > 0:
+                self.totals[s] += ms
+                self.recorded[s] += 1
+
+
+def launch_count() -> int:
+    return int(load().rhg_launch_count())
+
+
+def status_str(status: int) -> str:
+    return load().rhg_status_str(status).decode()
+
+
+def default_bands(n: int) -> int:
+    B = 0
+    while B < 63 and (1 << B) < n:
+        B += 1
+    return max(B, 1)
+
+
+def make_params(n, k=0.0, alpha=1.0, seed=0, num_bands=0, band_ratio=0.0, R_override=0.0, flags=0):
+    return Params(int(n), float(k), float(alpha), int(seed), int(num_bands), int(flags), float(band_ratio),
+                  float(R_override))
+
+
+# ---------------------------------------------------------------- torch plumbing
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _empty_bytes(nbytes: int, device=None):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device or "cuda")
+
+
+def _check(rc: int, where: str, result: Result | None = None):
+    if rc != OK:
+        raise RhgError(rc, where, result)
+
+
+# ------------------------------------------------------------------- entry points
+def plan_workspace_bytes() -> int:
+    return int(load().rhg_plan_workspace_bytes())
+
+
+def target_radius(n: int, k: float, alpha: float, stream=None) -> float:
+    ws = _empty_bytes(plan_workspace_bytes())
+    R = _c_dbl(0.0)
+    _check(load().rhg_target_radius(n, k, alpha, ws.data_ptr(), ws.numel(), _stream(stream), ctypes.byref(R)),
+           "rhg_target_radius")
+    return R.value
+
+
+def plan(n, k, alpha, seed=0, num_bands=0, band_ratio=0.0, R_override=0.0, stream=None):
+    p = make_params(n, k, alpha, seed, num_bands, band_ratio, R_override)
+    ws = _empty_bytes(plan_workspace_bytes())
+    R = _c_dbl(0.0)
+    B = _c_u32(0)
+    c = (ctypes.c_double * (MAX_BANDS + 1))()
+    _check(load().rhg_plan(ctypes.byref(p), ws.data_ptr(), ws.numel(), _stream(stream), ctypes.byref(R), c,
+                           ctypes.byref(B)), "rhg_plan")
+    return R.value, [c[j] for j in range(B.value + 1)]
+
+
+def workspace_bytes(params: Params, capacity_entries: int = 0) -> int:
+    out = _c_size(0)
+    _check(load().rhg_workspace_bytes(ctypes.byref(params), capacity_entries, ctypes.byref(out)),
+           "rhg_workspace_bytes")
+    return int(out.value)
+
+
+def sample_points(n, k, alpha, seed, R_override=0.0, stream=None):
+    """Points by id as two float64 CUDA tensors (phi, r), and R."""
+    torch = _torch()
+    p = make_params(n, k, alpha, seed, R_override=R_override)
+    ws = _empty_bytes(plan_workspace_bytes())
+    phi = torch.empty(n, dtype=torch.float64, device="cuda")
+    r = torch.empty(n, dtype=torch.float64, device="cuda")
+    R = _c_dbl(0.0)
+    _check(load().rhg_sample_points(ctypes.byref(p), ws.data_ptr(), ws.numel(), phi.data_ptr(), r.data_ptr(),
+                                    _stream(stream), ctypes.byref(R)), "rhg_sample_points")
+    return phi, r, R.value
+
+
+def estimate_capacity(n: int, k: float) -> int:
+    """Pairs buffer size from the expected edge count n k / 2, with slack."""
+    return int(math.ceil(n * k / 2 * 1.25)) + 4096
+
+
+@dataclass
+class Workspace:
+    """Reusable device buffers for repeated calls with the same parameters."""
+    ws: object
+    out: object
+    capacity: int
+
+
+def allocate_pairs(params: Params, capacity: int | None = None) -> Workspace:
+    torch = _torch()
+    cap = capacity if capacity is not None else estimate_capacity(params.n, params.k or 8.0)
+    ws = _empty_bytes(workspace_bytes(params, 0))
+    out = torch.empty(max(2 * cap, 2), dtype=torch.int32, device="cuda")
+    return Workspace(ws, out, cap)
+
+
+def generate_pairs(n, k, alpha, seed, num_bands=0, band_ratio=0.0, flags=0, R_override=0.0,
+                   workspace: Workspace | None = None, stream=None):
+    """Edges as an (m, 2) int32 CUDA tensor of uint32 ids (u < v), and the Result.
+
+    Allocates the output from n k / 2 with slack; on RHG_ERR_OVERFLOW it
+    reallocates to the exact size reported and calls again."""
+    p = make_params(n, k, alpha, seed, num_bands, band_ratio, R_override, flags)
+    wsp = workspace or allocate_pairs(p)
+    res = Result()
+    L = load()
+    rc = L.rhg_generate_pairs(ctypes.byref(p), wsp.ws.data_ptr(), wsp.ws.numel(), wsp.out.data_ptr(),
+                              wsp.capacity, _stream(stream), ctypes.byref(res))
+    if rc == OVERFLOW:
+        wsp = allocate_pairs(p, int(res.m))
+        rc = L.rhg_generate_pairs(ctypes.byref(p), wsp.ws.data_ptr(), wsp.ws.numel(), wsp.out.data_ptr(),
+                                  wsp.capacity, _stream(stream), ctypes.byref(res))
+    _check(rc, "rhg_generate_pairs", res)
+    return wsp.out[: 2 * res.m].view(-1, 2), res
+
+
+def generate_pairs_host(n, k, alpha, seed, host_out, workspace: Workspace, num_bands=0, band_ratio=0.0,
+                        flags=0, stream=None):
+    """Generate into device buffers and copy the pairs to host_out (a pinned
+    int32 CPU tensor with room for 2 * capacity words); returns the Result."""
+    p = make_params(n, k, alpha, seed, num_bands, band_ratio, 0.0, flags)
+    res = Result()
+    rc = load().rhg_generate_pairs_host(ctypes.byref(p), workspace.ws.data_ptr(), workspace.ws.numel(),
+                                        workspace.out.data_ptr(), workspace.capacity, host_out.data_ptr(),
+                                        host_out.numel() // 2, _stream(stream), ctypes.byref(res))
+    _check(rc, "rhg_generate_pairs_host", res)
+    return res
+
+
+def generate_csr(n, k, alpha, seed, num_bands=0, band_ratio=0.0, flags=0, capacity_entries=None,
+                 stream=None):
+    """Symmetric CSR: (row_ptr int64[n+1], col int32[2m]) CUDA tensors, and the Result."""
+    torch = _torch()
+    p = make_params(n, k, alpha, seed, num_bands, band_ratio, 0.0, flags)
+    cap = capacity_entries if capacity_entries is not None else 2 * estimate_capacity(n, k)
+    L = load()
+    for _ in range(2):
+        ws = _empty_bytes(workspace_bytes(p, cap))
+        row_ptr = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(cap, 1), dtype=torch.int32, device="cuda")
+        res = Result()
+        rc = L.rhg_generate_csr(ctypes.byref(p), ws.data_ptr(), ws.numel(), row_ptr.data_ptr(), col.data_ptr(),
+                                cap, _stream(stream), ctypes.byref(res))
+        if rc != OVERFLOW:
+            break
+        cap = 2 * int(res.m)
+    _check(rc, "rhg_generate_csr", res)
+    return row_ptr, col[: 2 * res.m], res
+
+
+def edges_from_points(phi, r, R, num_bands=0, band_ratio=0.0, flags=0, capacity=None, stream=None):
+    """Edges among caller points (float64 CUDA tensors by id), as generate_pairs."""
+    torch = _torch()
+    n = int(phi.numel())
+    phi = phi.contiguous()
+    r = r.contiguous()
+    nb = _c_size(0)
+    L = load()
+    _check(L.rhg_workspace_bytes_points(n, num_bands, ctypes.byref(nb)), "rhg_workspace_bytes_points")
+    ws = _empty_bytes(nb.value)
+    cap = capacity if capacity is not None else max(4 * n, 4096)
+    for _ in range(2):
+        out = torch.empty(max(2 * cap, 2), dtype=torch.int32, device="cuda")
+        res = Result()
+        rc = L.rhg_edges_from_points(phi.data_ptr(), r.data_ptr(), n, float(R), num_bands, float(band_ratio),
+                                     flags, ws.data_ptr(), ws.numel(), out.data_ptr(), cap, _stream(stream),
+                                     ctypes.byref(res))
+        if rc != OVERFLOW:
+            break
+        cap = int(res.m)
+    _check(rc, "rhg_edges_from_points", res)
+    return out[: 2 * res.m].view(-1, 2), res
+
+
+def dm_eval(fn: str, x):
+    """The library's deterministic FP64 function `fn` on a float64 CUDA tensor."""
+    torch = _torch()
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    _check(load().rhg_dm_eval(DM_FUNCS[fn], x.data_ptr(), out.data_ptr(), x.numel(), _stream()), "rhg_dm_eval")
+    return out

@@ -1,0 +1,492 @@
+// api.cu -- the extern "C" entry points declared in include/rhg.h: argument
+// validation, workspace layout, and the stream-ordered pipeline
+//   plan -> sample -> band offsets -> radix sort -> gather -> query count ->
+//   scan -> (one 64-byte D2H of the metadata) -> query emit [-> CSR sort/finish].
+#include <atomic>
+#include <cmath>
+#include <cstring>
+
+#include "kernels.h"
+
+namespace rhg {
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+// rhg_set_stage_events state (profiling aid, process-wide)
+void *const *g_events = nullptr;
+uint32_t g_num_events = 0;
+
+void mark(uint32_t stage, bool end, cudaStream_t s)
+{
+    const uint32_t i = 2 * stage + (end ? 1 : 0);
+    if (g_events && i < g_num_events && g_events[i])
+        cudaEventRecord(static_cast<cudaEvent_t>(g_events[i]), s);
+}
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// Byte offsets of every buffer inside the caller's workspace.
+struct Layout {
+    size_t meta, keys0, keys1, ids0, ids1, r_by_id, phi, r, ch, sh, akey, id, counts, offsets, sort_tmp,
+        scan_tmp, csr0, csr1, total;
+};
+
+Layout make_layout(uint64_t n, uint64_t csr_entries)
+{
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    L.meta = take(sizeof(Meta));
+    L.keys0 = take(n * 8);
+    L.keys1 = take(n * 8);
+    L.ids0 = take(n * 4);
+    L.ids1 = take(n * 4);
+    L.r_by_id = take(n * 8);
+    L.phi = take(n * 8);
+    L.r = take(n * 8);
+    L.ch = take(n * 8);
+    L.sh = take(n * 8);
+    L.akey = take(n * 4);
+    L.id = take(n * 4);
+    L.counts = take(n * 4);
+    L.offsets = take((n + 1) * 8);
+    const size_t sort_points = radix_temp_bytes(n);
+    const size_t sort_csr = csr_entries ? radix_temp_bytes(csr_entries) : 0;
+    L.sort_tmp = take(sort_points > sort_csr ? sort_points : sort_csr);
+    L.scan_tmp = take(scan_temp_bytes(n));
+    L.csr0 = take(csr_entries * 8);
+    L.csr1 = take(csr_entries * 8);
+    L.total = o;
+    return L;
+}
+
+template <typename T>
+T *at(void *base, size_t off)
+{
+    return reinterpret_cast<T *>(static_cast<char *>(base) + off);
+}
+
+uint32_t default_bands(uint64_t n)
+{
+    uint32_t B = 0;
+    while (B < 63 && (uint64_t{1} << B) < n) ++B;
+    return B < 1 ? 1 : B;
+}
+
+// Host-side validation of rhg_params; fills B and p.
+int check_params(const rhg_params *p, uint32_t *B, double *ratio)
+{
+    if (!p) return RHG_ERR_INVALID_ARG;
+    if (p->n < 2 || p->n > 0xFFFFFFFFull) return RHG_ERR_INVALID_ARG;
+    if (!(p->alpha > 0.5) || !(p->alpha <= 100.0)) return RHG_ERR_INVALID_ARG;
+    const bool has_R = p->R_override > 0.0;
+    if (has_R && !(std::isfinite(p->R_override) && p->R_override <= 700.0)) return RHG_ERR_INVALID_ARG;
+    if (!has_R && !(p->k > 0.0 && p->k < 1e300)) return RHG_ERR_INVALID_ARG;
+    if (p->num_bands > RHG_MAX_BANDS) return RHG_ERR_INVALID_ARG;
+    if (p->band_ratio < 0.0 || !std::isfinite(p->band_ratio)) return RHG_ERR_INVALID_ARG;
+    if (p->flags & ~RHG_FLAG_FP64_ONLY) return RHG_ERR_INVALID_ARG;
+    *B = p->num_bands ? p->num_bands : default_bands(p->n);
+    *ratio = p->band_ratio > 0.0 ? p->band_ratio : 0.9;
+    return RHG_OK;
+}
+
+int finish(const Status &st, rhg_result *res)
+{
+    if (res && st.code == RHG_ERR_CUDA) res->cuda_error = static_cast<int32_t>(st.cuda);
+    return st.code;
+}
+
+int error_from_meta(uint32_t e)
+{
+    switch (e) {
+        case kErrNone: return RHG_OK;
+        case kErrNoSolution: return RHG_ERR_NO_SOLUTION;
+        case kErrBadPoint: return RHG_ERR_INVALID_ARG;
+        case kErrTimeout: return RHG_ERR_TIMEOUT;
+        default: return RHG_ERR_CUDA;
+    }
+}
+
+// The scalars of Meta the host reads back after a run.
+struct MetaTail {
+    double R;
+    uint32_t B, error;
+    uint64_t m, candidates, near_threshold, rechecks;
+};
+
+Status read_meta(const Meta *d_meta, MetaTail *t, cudaStream_t stream)
+{
+    Status st;
+    Meta h;
+    RHG_CUDA_TRY(cudaMemcpyAsync(&h, d_meta, sizeof(Meta), cudaMemcpyDeviceToHost, stream));
+    RHG_CUDA_TRY(cudaStreamSynchronize(stream));
+    t->R = h.R;
+    t->B = h.B;
+    t->error = h.error;
+    t->m = h.m;
+    t->candidates = h.candidates;
+    t->near_threshold = h.near_threshold;
+    t->rechecks = h.rechecks;
+    return st;
+}
+
+void fill_result(rhg_result *res, const MetaTail &t)
+{
+    if (!res) return;
+    res->m = t.m;
+    res->R = t.R;
+    res->num_bands = t.B;
+    res->candidates = t.candidates;
+    res->near_threshold = t.near_threshold;
+    res->rechecks = t.rechecks;
+}
+
+struct Pipeline {
+    void *ws;
+    Layout L;
+    uint64_t n;
+    Meta *meta() const { return at<Meta>(ws, L.meta); }
+    SortedPoints sorted(const uint64_t *sorted_keys) const
+    {
+        SortedPoints P;
+        P.n = n;
+        P.key = sorted_keys;
+        P.phi = at<double>(ws, L.phi);
+        P.r = at<double>(ws, L.r);
+        P.ch = at<double>(ws, L.ch);
+        P.sh = at<double>(ws, L.sh);
+        P.akey = at<uint32_t>(ws, L.akey);
+        P.id = at<uint32_t>(ws, L.id);
+        return P;
+    }
+};
+
+// Points, bands, sort and gather; leaves the sorted SoA in the workspace.
+Status build_points(const Pipeline &pl, uint64_t seed, const double *phi_in, const double *r_in,
+                    const uint64_t **sorted_keys, cudaStream_t stream)
+{
+    Status st;
+    Meta *M = pl.meta();
+    uint64_t *k0 = at<uint64_t>(pl.ws, pl.L.keys0), *k1 = at<uint64_t>(pl.ws, pl.L.keys1);
+    uint32_t *i0 = at<uint32_t>(pl.ws, pl.L.ids0), *i1 = at<uint32_t>(pl.ws, pl.L.ids1);
+    double *rid = at<double>(pl.ws, pl.L.r_by_id);
+    mark(RHG_STAGE_SAMPLE, false, stream);
+    if (phi_in) st = launch_load_points(M, pl.n, phi_in, r_in, k0, i0, stream);
+    else st = launch_sample(M, pl.n, seed, k0, i0, rid, stream);
+    if (st.code) return st;
+    mark(RHG_STAGE_SAMPLE, true, stream);
+    mark(RHG_STAGE_SORT, false, stream);
+    st = launch_band_offsets(M, stream);
+    if (st.code) return st;
+    // key = (band << 32) | angle key; band < 64 needs 6 more bits
+    const int shifts[5] = {0, 8, 16, 24, 32};
+    uint64_t *ks = nullptr;
+    uint32_t *is = nullptr;
+    st = radix_sort(pl.n, k0, k1, i0, i1, shifts, 5, at<void>(pl.ws, pl.L.sort_tmp), &ks, &is, stream);
+    if (st.code) return st;
+    mark(RHG_STAGE_SORT, true, stream);
+    mark(RHG_STAGE_GATHER, false, stream);
+    st = launch_gather(M, pl.n, seed, ks, is, phi_in, phi_in ? r_in : rid, pl.sorted(ks), stream);
+    mark(RHG_STAGE_GATHER, true, stream);
+    *sorted_keys = ks;
+    return st;
+}
+
+int bits_for(uint64_t v)
+{
+    int b = 0;
+    while (b < 64 && (v >> b)) ++b;
+    return b;
+}
+
+enum class Output { Pairs, Csr };
+
+// The query, scan and emit stages shared by every generate entry point.
+Status run_query(const Pipeline &pl, const uint64_t *sorted_keys, Output kind, uint32_t *d_pairs,
+                 uint64_t capacity, uint64_t *d_row_ptr, uint32_t *d_col, MetaTail *tail, int *status,
+                 cudaStream_t stream)
+{
+    Status st;
+    Meta *M = pl.meta();
+    const SortedPoints P = pl.sorted(sorted_keys);
+    uint32_t *counts = at<uint32_t>(pl.ws, pl.L.counts);
+    uint64_t *offsets = at<uint64_t>(pl.ws, pl.L.offsets);
+    mark(RHG_STAGE_COUNT, false, stream);
+    st = launch_query_count(M, P, counts, stream);
+    if (st.code) return st;
+    mark(RHG_STAGE_COUNT, true, stream);
+    mark(RHG_STAGE_SCAN, false, stream);
+    st = exclusive_scan_u32(counts, offsets, pl.n, &M->m, at<void>(pl.ws, pl.L.scan_tmp), stream);
+    if (st.code) return st;
+    mark(RHG_STAGE_SCAN, true, stream);
+    st = read_meta(M, tail, stream);
+    if (st.code) return st;
+    *status = error_from_meta(tail->error);
+    if (*status != RHG_OK) return st;
+    const uint64_t need = kind == Output::Pairs ? tail->m : 2 * tail->m;
+    if (need > capacity) {
+        *status = RHG_ERR_OVERFLOW;
+        return st;
+    }
+    if (kind == Output::Pairs) {
+        mark(RHG_STAGE_EMIT, false, stream);
+        if (tail->m) st = launch_query_emit(M, P, offsets, d_pairs, nullptr, stream);
+        if (st.code) return st;
+        mark(RHG_STAGE_EMIT, true, stream);
+    } else {
+        uint64_t *c0 = at<uint64_t>(pl.ws, pl.L.csr0), *c1 = at<uint64_t>(pl.ws, pl.L.csr1);
+        mark(RHG_STAGE_EMIT, false, stream);
+        if (tail->m) {
+            st = launch_query_emit(M, P, offsets, nullptr, c0, stream);
+            if (st.code) return st;
+        }
+        mark(RHG_STAGE_EMIT, true, stream);
+        mark(RHG_STAGE_CSR, false, stream);
+        const int nb = bits_for(pl.n - 1);
+        int shifts[16];
+        int ns = 0;
+        for (int s = 0; s < nb; s += 8) shifts[ns++] = s;
+        for (int s = 0; s < nb; s += 8) shifts[ns++] = 32 + s;
+        uint64_t *sorted = nullptr;
+        st = radix_sort(need, c0, c1, nullptr, nullptr, shifts, ns, at<void>(pl.ws, pl.L.sort_tmp), &sorted,
+                        nullptr, stream);
+        if (st.code) return st;
+        st = launch_csr_finish(sorted, need, pl.n, d_row_ptr, d_col, stream);
+        if (st.code) return st;
+        mark(RHG_STAGE_CSR, true, stream);
+    }
+    Meta h;
+    RHG_CUDA_TRY(cudaMemcpyAsync(&h, M, sizeof(Meta), cudaMemcpyDeviceToHost, stream));
+    RHG_CUDA_TRY(cudaStreamSynchronize(stream));
+    *status = error_from_meta(h.error);
+    return st;
+}
+
+int generate(const rhg_params *p, void *d_ws, size_t ws_bytes, Output kind, uint32_t *d_pairs,
+             uint64_t capacity, uint64_t *d_row_ptr, uint32_t *d_col, cudaStream_t stream, rhg_result *res)
+{
+    if (res) std::memset(res, 0, sizeof(*res));
+    uint32_t B;
+    double ratio;
+    int rc = check_params(p, &B, &ratio);
+    if (rc) return rc;
+    if (!d_ws) return RHG_ERR_INVALID_ARG;
+    if (kind == Output::Pairs && capacity && !d_pairs) return RHG_ERR_INVALID_ARG;
+    if (kind == Output::Csr && (!d_row_ptr || (capacity && !d_col))) return RHG_ERR_INVALID_ARG;
+    const Layout L = make_layout(p->n, kind == Output::Csr ? capacity : 0);
+    if (ws_bytes < L.total) return RHG_ERR_OOM;
+    Pipeline pl{d_ws, L, p->n};
+    mark(RHG_STAGE_PLAN, false, stream);
+    Status st = launch_plan(pl.meta(), p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override, stream);
+    if (st.code) return finish(st, res);
+    mark(RHG_STAGE_PLAN, true, stream);
+    const uint64_t *sk = nullptr;
+    st = build_points(pl, p->seed, nullptr, nullptr, &sk, stream);
+    if (st.code) return finish(st, res);
+    MetaTail tail{};
+    int status = RHG_OK;
+    st = run_query(pl, sk, kind, d_pairs, capacity, d_row_ptr, d_col, &tail, &status, stream);
+    if (st.code) return finish(st, res);
+    fill_result(res, tail);
+    return status;
+}
+
+}  // namespace
+}  // namespace rhg
+
+using namespace rhg;
+
+extern "C" {
+
+const char *rhg_status_str(int status)
+{
+    switch (status) {
+        case RHG_OK: return "RHG_OK";
+        case RHG_ERR_INVALID_ARG: return "RHG_ERR_INVALID_ARG";
+        case RHG_ERR_NO_SOLUTION: return "RHG_ERR_NO_SOLUTION";
+        case RHG_ERR_OOM: return "RHG_ERR_OOM";
+        case RHG_ERR_CUDA: return "RHG_ERR_CUDA";
+        case RHG_ERR_TIMEOUT: return "RHG_ERR_TIMEOUT";
+        case RHG_ERR_OVERFLOW: return "RHG_ERR_OVERFLOW";
+        default: return "RHG_ERR_UNKNOWN";
+    }
+}
+
+int rhg_version(void) { return 1; }
+
+int rhg_set_stage_events(void *const *events, uint32_t count)
+{
+    g_events = count ? events : nullptr;
+    g_num_events = events ? count : 0;
+    return RHG_OK;
+}
+
+uint64_t rhg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int rhg_workspace_bytes(const rhg_params *p, uint64_t capacity_entries, size_t *bytes)
+{
+    uint32_t B;
+    double ratio;
+    const int rc = check_params(p, &B, &ratio);
+    if (rc) return rc;
+    if (!bytes) return RHG_ERR_INVALID_ARG;
+    *bytes = make_layout(p->n, capacity_entries).total;
+    return RHG_OK;
+}
+
+int rhg_workspace_bytes_points(uint64_t n, uint32_t num_bands, size_t *bytes)
+{
+    if (!bytes || n < 1 || n > 0xFFFFFFFFull || num_bands > RHG_MAX_BANDS) return RHG_ERR_INVALID_ARG;
+    *bytes = make_layout(n, 0).total;
+    return RHG_OK;
+}
+
+size_t rhg_plan_workspace_bytes(void) { return align_up(sizeof(Meta)); }
+
+int rhg_plan(const rhg_params *p, void *d_workspace, size_t workspace_bytes, void *stream, double *R_out,
+             double *h_c, uint32_t *num_bands_out)
+{
+    uint32_t B;
+    double ratio;
+    const int rc = check_params(p, &B, &ratio);
+    if (rc) return rc;
+    if (!R_out || !h_c || !num_bands_out || !d_workspace) return RHG_ERR_INVALID_ARG;
+    if (workspace_bytes < sizeof(Meta)) return RHG_ERR_OOM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Meta *d = static_cast<Meta *>(d_workspace);
+    const Status st = launch_plan(d, p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override, s);
+    if (st.code) return st.code;
+    Meta h;
+    if (cudaMemcpyAsync(&h, d, sizeof(Meta), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RHG_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RHG_ERR_CUDA;
+    if (h.error) return error_from_meta(h.error);
+    *R_out = h.R;
+    *num_bands_out = h.B;
+    for (uint32_t j = 0; j <= h.B; ++j) h_c[j] = h.c[j];
+    return RHG_OK;
+}
+
+int rhg_target_radius(uint64_t n, double k, double alpha, void *d_workspace, size_t workspace_bytes,
+                      void *stream, double *R_out)
+{
+    if (!R_out) return RHG_ERR_INVALID_ARG;
+    rhg_params p{};
+    p.n = n;
+    p.k = k;
+    p.alpha = alpha;
+    double c[RHG_MAX_BANDS + 1];
+    uint32_t B = 0;
+    return rhg_plan(&p, d_workspace, workspace_bytes, stream, R_out, c, &B);
+}
+
+int rhg_sample_points(const rhg_params *p, void *d_workspace, size_t workspace_bytes, double *d_phi,
+                      double *d_r, void *stream, double *R_out)
+{
+    uint32_t B;
+    double ratio;
+    const int rc = check_params(p, &B, &ratio);
+    if (rc) return rc;
+    if (!d_workspace || !d_phi || !d_r) return RHG_ERR_INVALID_ARG;
+    if (workspace_bytes < sizeof(Meta)) return RHG_ERR_OOM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Meta *M = static_cast<Meta *>(d_workspace);
+    Status st = launch_plan(M, p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override, s);
+    if (st.code) return st.code;
+    st = launch_points_by_id(M, p->n, p->seed, d_phi, d_r, s);
+    if (st.code) return st.code;
+    Meta h;
+    if (cudaMemcpyAsync(&h, M, sizeof(Meta), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RHG_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RHG_ERR_CUDA;
+    if (h.error) return error_from_meta(h.error);
+    if (R_out) *R_out = h.R;
+    return RHG_OK;
+}
+
+int rhg_generate_pairs(const rhg_params *p, void *d_workspace, size_t workspace_bytes, uint32_t *d_pairs,
+                       uint64_t capacity_edges, void *stream, rhg_result *result)
+{
+    return generate(p, d_workspace, workspace_bytes, Output::Pairs, d_pairs, capacity_edges, nullptr, nullptr,
+                    static_cast<cudaStream_t>(stream), result);
+}
+
+int rhg_generate_pairs_host(const rhg_params *p, void *d_workspace, size_t workspace_bytes, uint32_t *d_pairs,
+                            uint64_t capacity_edges, uint32_t *h_pairs, uint64_t h_capacity_edges, void *stream,
+                            rhg_result *result)
+{
+    if (!h_pairs && h_capacity_edges) return RHG_ERR_INVALID_ARG;
+    rhg_result local{};
+    rhg_result *res = result ? result : &local;
+    const int rc = rhg_generate_pairs(p, d_workspace, workspace_bytes, d_pairs, capacity_edges, stream, res);
+    if (rc) return rc;
+    if (res->m > h_capacity_edges) return RHG_ERR_OVERFLOW;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (res->m) {
+        const cudaError_t e =
+            cudaMemcpyAsync(h_pairs, d_pairs, res->m * 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) {
+            res->cuda_error = e;
+            return RHG_ERR_CUDA;
+        }
+    }
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        res->cuda_error = e;
+        return RHG_ERR_CUDA;
+    }
+    return RHG_OK;
+}
+
+int rhg_generate_csr(const rhg_params *p, void *d_workspace, size_t workspace_bytes, uint64_t *d_row_ptr,
+                     uint32_t *d_col, uint64_t capacity_entries, void *stream, rhg_result *result)
+{
+    return generate(p, d_workspace, workspace_bytes, Output::Csr, nullptr, capacity_entries, d_row_ptr, d_col,
+                    static_cast<cudaStream_t>(stream), result);
+}
+
+int rhg_edges_from_points(const double *d_phi, const double *d_r, uint64_t n, double R, uint32_t num_bands,
+                          double band_ratio, uint32_t flags, void *d_workspace, size_t workspace_bytes,
+                          uint32_t *d_pairs, uint64_t capacity_edges, void *stream, rhg_result *result)
+{
+    if (result) std::memset(result, 0, sizeof(*result));
+    if (n < 1 || n > 0xFFFFFFFFull || !d_phi || !d_r || !d_workspace) return RHG_ERR_INVALID_ARG;
+    if (!(R > 0.0) || !(R <= 700.0) || num_bands > RHG_MAX_BANDS) return RHG_ERR_INVALID_ARG;
+    if (band_ratio < 0.0 || !std::isfinite(band_ratio) || (flags & ~RHG_FLAG_FP64_ONLY)) return RHG_ERR_INVALID_ARG;
+    if (capacity_edges && !d_pairs) return RHG_ERR_INVALID_ARG;
+    const uint32_t B = num_bands ? num_bands : default_bands(n < 2 ? 2 : n);
+    const double ratio = band_ratio > 0.0 ? band_ratio : 0.9;
+    const Layout L = make_layout(n, 0);
+    if (workspace_bytes < L.total) return RHG_ERR_OOM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Pipeline pl{d_workspace, L, n};
+    // alpha only enters the sampler, which is not used here
+    Status st = launch_plan(pl.meta(), n, 1.0, 1.0, 0, B, ratio, R, s);
+    if (st.code) return finish(st, result);
+    const uint64_t *sk = nullptr;
+    st = build_points(pl, 0, d_phi, d_r, &sk, s);
+    if (st.code) return finish(st, result);
+    MetaTail tail{};
+    int status = RHG_OK;
+    st = run_query(pl, sk, Output::Pairs, d_pairs, capacity_edges, nullptr, nullptr, &tail, &status, s);
+    if (st.code) return finish(st, result);
+    fill_result(result, tail);
+    return status;
+}
+
+int rhg_dm_eval(int fn, const double *d_in, double *d_out, uint64_t count, void *stream)
+{
+    if (fn < 0 || fn > 4 || (count && (!d_in || !d_out))) return RHG_ERR_INVALID_ARG;
+    if (!count) return RHG_OK;
+    const Status st = launch_dm_eval(fn, d_in, d_out, count, static_cast<cudaStream_t>(stream));
+    return st.code;
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// common.cuh -- shared definitions of the CUDA path: per-graph metadata kept in
+// device memory, the counter-based generator, the canonical edge predicate and
+// error-checking helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/rhg.h"
+#include "detmath.cuh"
+
+namespace rhg {
+
+constexpr int kMaxBands = static_cast<int>(RHG_MAX_BANDS);
+
+// Per-graph metadata, written by the plan kernel and read by all later stages.
+struct Meta {
+    double R;          // disk radius
+    double coshR;      // dm::cosh(R): the predicate's threshold
+    double alpha;
+    double inv_alpha;  // 1 / alpha
+    double cm1;        // dm::cosh(alpha R) - 1 (inverse CDF of Eq. 1)
+    double c[kMaxBands + 1];        // band boundaries c_0 = 0 .. c_B = R
+    double cosh_c[kMaxBands + 1];   // cosh / sinh of the boundaries (windows only)
+    double sinh_c[kMaxBands + 1];
+    uint64_t band_start[kMaxBands + 1];  // sorted position of each band's first point
+    uint32_t band_count[kMaxBands];
+    uint32_t B;
+    uint32_t error;          // nonzero: a device-side check failed (see kErr*)
+    uint64_t n;
+    uint64_t seed;
+    double k;
+    uint64_t m;              // edges found (exact)
+    uint64_t candidates;
+    uint64_t near_threshold;
+    uint64_t rechecks;
+    uint64_t work_counter;   // dynamic work distribution
+    uint64_t emit_cursor;    // output reservation
+};
+
+// device-side error codes (Meta::error)
+constexpr uint32_t kErrNone = 0;
+constexpr uint32_t kErrNoSolution = 1;
+constexpr uint32_t kErrBadPoint = 2;
+constexpr uint32_t kErrTimeout = 3;
+constexpr uint32_t kErrInternal = 4;
+
+// ----------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 64x64->128
+// multiplications with the published multipliers, key schedule by the published
+// Weyl increments.
+struct U64x4 {
+    uint64_t x0, x1, x2, x3;
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(U64x4 c, uint64_t k0, uint64_t k1)
+{
+    constexpr uint64_t kMul0 = 0xD2E7470EE14C6C93ULL, kMul1 = 0xCA5A826395121157ULL;
+    constexpr uint64_t kWeyl0 = 0x9E3779B97F4A7C15ULL, kWeyl1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += kWeyl0;
+            k1 += kWeyl1;
+        }
+        const uint64_t hi0 = __umul64hi(kMul0, c.x0), lo0 = kMul0 * c.x0;
+        const uint64_t hi1 = __umul64hi(kMul1, c.x2), lo1 = kMul1 * c.x2;
+        c = U64x4{hi1 ^ c.x1 ^ k0, lo1, hi0 ^ c.x3 ^ k1, lo0};
+    }
+    return c;
+}
+
+// Angle of point `id`: phi = fl(u53 * 2pi 2^-53), u53 = top 53 bits of word 0.
+constexpr double kPhiScale = 0x1.921fb54442d18p-51;  // kTwoPi * 2^-53, exact
+constexpr double kU53 = 0x1.0p-53;
+
+// Search key of an angle: floor(phi * 2^32 / 2pi) clamped to [0, 2^32 - 1]; a
+// monotone map of phi, so that key order refines angle order.
+constexpr double kKeyScale = 0x1.45f306dc9c883p+29;  // nearest double to 2^32 / (2 pi)
+
+__device__ __forceinline__ uint32_t angle_key(double phi)
+{
+    const double t = floor(__dmul_rn(phi, kKeyScale));
+    if (!(t > 0.0)) return 0u;
+    if (t >= 4294967295.0) return 0xffffffffu;
+    return static_cast<uint32_t>(t);
+}
+
+// Radial coordinate from its uniform variate (inverse CDF of Eq. 1):
+//   w = U (cosh(alpha R) - 1),  r = ln(1 + w + sqrt(w (w + 2))) / alpha, clamped to R.
+__device__ __forceinline__ double radius_from_u53(uint64_t u53, double R, double cm1,
+                                                  double inv_alpha)
+{
+    const double U = __dmul_rn(static_cast<double>(u53), kU53);
+    const double w = __dmul_rn(U, cm1);
+    const double sq = __dsqrt_rn(__dmul_rn(w, __dadd_rn(w, 2.0)));
+    const double y = __dadd_rn(__dadd_rn(1.0, w), sq);
+    const double r = __dmul_rn(dm::log(y), inv_alpha);
+    return r > R ? R : r;
+}
+
+// Canonical edge predicate (Eq. 3, threshold test of Alg. 1): returns L; the
+// pair is an edge iff L <= cosh R.
+__device__ __forceinline__ double predicate_L(double phv, double chv, double shv, double phw,
+                                              double chw, double shw)
+{
+    const double d = fabs(__dsub_rn(phv, phw));
+    const double c = dm::cos(d);
+    const double t1 = __dmul_rn(chv, chw);
+    const double t3 = __dmul_rn(__dmul_rn(shv, shw), c);
+    return __dsub_rn(t1, t3);
+}
+
+// Band of r: the largest j < B with c_j <= r (Sec. III-A: c_j <= r < c_{j+1}).
+__device__ __forceinline__ uint32_t band_of(double r, const double *c, uint32_t B)
+{
+    uint32_t lo = 0, hi = B;  // invariant: c[lo] <= r, answer in [lo, hi)
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (c[mid] <= r) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// ----------------------------------------------------------------------------
+// host-side helpers
+struct Status {
+    int code = RHG_OK;
+    cudaError_t cuda = cudaSuccess;
+};
+
+#define RHG_CUDA_TRY(expr)                                \
+    do {                                                  \
+        cudaError_t _e = (expr);                          \
+        if (_e != cudaSuccess) {                          \
+            st.code = RHG_ERR_CUDA;                       \
+            st.cuda = _e;                                 \
+            return st;                                    \
+        }                                                 \
+    } while (0)
+
+// Kernels launched by the library (rhg_launch_count); every launch site is
+// followed by RHG_LAUNCH_CHECK, which counts it.
+void note_launch();
+
+#define RHG_LAUNCH_CHECK()                                \
+    do {                                                  \
+        ::rhg::note_launch();                             \
+        cudaError_t _e = cudaGetLastError();              \
+        if (_e != cudaSuccess) {                          \
+            st.code = RHG_ERR_CUDA;                       \
+            st.cuda = _e;                                 \
+            return st;                                    \
+        }                                                 \
+    } while (0)
+
+inline int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+}  // namespace rhg

@@ -1,0 +1,309 @@
+// points.cu -- the point pipeline: disk radius R (Sec. III-B getTargetRadius),
+// band boundaries (Sec. III-A), Philox sampling of (phi, r) by inverse CDF
+// (Alg. 1 "draw phi" / "draw r", Eq. 1), band assignment (Alg. 1 "insert in b_i")
+// and the gather of the (band, angle)-sorted structure-of-arrays.
+#include "kernels.h"
+
+namespace rhg {
+namespace {
+
+using dm::add;
+using dm::div;
+using dm::mul;
+using dm::sub;
+
+// Eq. 22 of Krioukov et al. with zeta = 1 (Sec. III-B), in the fixed operation order
+// of the deterministic definition:
+//   kbar = ((2/pi) xi^2 n) * (e^{-R/2} + e^{-alpha R} ((alpha R / 2) inner - 1)),
+//   inner = (pi/4)/alpha^2 - (pi-1)/alpha + (pi-2),  xi = alpha/(alpha - 1/2).
+__device__ double kbar(double R, double nd, double alpha)
+{
+    const double xi = div(alpha, sub(alpha, 0.5));
+    const double pre = mul(mul(div(2.0, dm::kPi), mul(xi, xi)), nd);
+    const double e1 = dm::exp(-mul(R, 0.5));
+    const double e2 = dm::exp(-mul(alpha, R));
+    const double ta = mul(mul(dm::kPi, 0.25), div(1.0, mul(alpha, alpha)));
+    const double tb = div(sub(dm::kPi, 1.0), alpha);
+    const double inner = add(sub(ta, tb), sub(dm::kPi, 2.0));
+    const double br = sub(mul(mul(mul(alpha, R), 0.5), inner), 1.0);
+    return mul(pre, add(e1, mul(e2, br)));
+}
+
+constexpr int kPlanThreads = 256;  // grid points j = 0..255 of the bracket search
+
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, uint64_t n, double k,
+                                                            double alpha, uint64_t seed, uint32_t B,
+                                                            double p, double R_override)
+{
+    __shared__ int jstar;
+    __shared__ double R_sh;
+    __shared__ int fail;
+    const int t = threadIdx.x;
+    const double nd = static_cast<double>(n);
+    if (t == 0) {
+        jstar = -1;
+        fail = 0;
+        R_sh = R_override;
+    }
+    __syncthreads();
+    if (!(R_override > 0.0)) {
+        // bracket: the largest integer grid point j with kbar(j) > k
+        if (kbar(static_cast<double>(t), nd, alpha) > k) atomicMax(&jstar, t);
+        __syncthreads();
+        if (t == 0) {
+            if (jstar < 0 || jstar == kPlanThreads - 1) {
+                fail = 1;
+            } else {
+                // binary search: kbar(lo) > k >= kbar(hi) until lo, hi are adjacent
+                double lo = static_cast<double>(jstar), hi = static_cast<double>(jstar + 1);
+                for (int it = 0; it < 200; ++it) {
+                    const double mid = mul(add(lo, hi), 0.5);
+                    if (mid == lo || mid == hi) break;
+                    if (kbar(mid, nd, alpha) > k) lo = mid;
+                    else hi = mid;
+                }
+                R_sh = hi;
+            }
+        }
+    }
+    __syncthreads();
+    if (t != 0) return;
+    M->error = fail ? kErrNoSolution : kErrNone;
+    const double R = fail ? 1.0 : R_sh;
+    M->R = R;
+    M->coshR = dm::cosh(R);
+    M->alpha = alpha;
+    M->inv_alpha = div(1.0, alpha);
+    M->cm1 = sub(dm::cosh(mul(alpha, R)), 1.0);
+    M->B = B;
+    M->n = n;
+    M->seed = seed;
+    M->k = k;
+    // Sec. III-A: c_0 = 0, c_{j+1} - c_j = c_1 p^j, c_1 = (1-p) R / (1 - p^B), c_B = R
+    M->c[0] = 0.0;
+    if (p == 1.0) {
+        for (uint32_t j = 1; j < B; ++j) M->c[j] = div(mul(R, static_cast<double>(j)), static_cast<double>(B));
+    } else {
+        double pw = 1.0;
+        for (uint32_t j = 0; j < B; ++j) pw = mul(pw, p);
+        const double c1 = div(mul(sub(1.0, p), R), sub(1.0, pw));
+        double step = c1;
+        for (uint32_t j = 1; j < B; ++j) {
+            const double next = add(M->c[j - 1], step);
+            M->c[j] = next < R ? next : R;
+            step = mul(step, p);
+        }
+    }
+    M->c[B] = R;
+    for (uint32_t j = 0; j <= B; ++j) {
+        M->cosh_c[j] = ::cosh(M->c[j]);
+        M->sinh_c[j] = ::sinh(M->c[j]);
+    }
+    for (uint32_t j = 0; j < static_cast<uint32_t>(kMaxBands); ++j) M->band_count[j] = 0;
+    M->m = 0;
+    M->candidates = 0;
+    M->near_threshold = 0;
+    M->rechecks = 0;
+    M->work_counter = 0;
+    M->emit_cursor = 0;
+}
+
+__device__ __forceinline__ double phi_from_u53(uint64_t u53)
+{
+    double ph = mul(static_cast<double>(u53), kPhiScale);
+    return ph < dm::kTwoPi ? ph : 0x1.921fb54442d17p+2;  // largest double below 2pi
+}
+
+__device__ __forceinline__ U64x4 draw(uint64_t id, uint64_t seed)
+{
+    return philox4x64_10(U64x4{id, 0, 0, 0}, seed, 0);
+}
+
+constexpr int kSampleThreads = 256;
+
+__global__ void __launch_bounds__(kSampleThreads) sample_kernel(Meta *M, uint64_t n, uint64_t seed,
+                                                                uint64_t *keys, uint32_t *ids,
+                                                                double *r_by_id)
+{
+    __shared__ double c[kMaxBands + 1];
+    __shared__ unsigned int hist[kMaxBands];
+    const uint32_t B = M->B;
+    const double R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
+    if (threadIdx.x <= B) c[threadIdx.x] = M->c[threadIdx.x];
+    if (threadIdx.x < kMaxBands) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const U64x4 x = draw(i, seed);
+        const double ph = phi_from_u53(x.x0 >> 11);
+        const double r = radius_from_u53(x.x1 >> 11, R, cm1, inv_alpha);
+        const uint32_t b = band_of(r, c, B);
+        keys[i] = (static_cast<uint64_t>(b) << 32) | angle_key(ph);
+        ids[i] = static_cast<uint32_t>(i);
+        r_by_id[i] = r;
+        atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < B && hist[threadIdx.x]) atomicAdd(&M->band_count[threadIdx.x], hist[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(kSampleThreads) load_points_kernel(Meta *M, uint64_t n,
+                                                                     const double *phi,
+                                                                     const double *rr,
+                                                                     uint64_t *keys, uint32_t *ids)
+{
+    __shared__ double c[kMaxBands + 1];
+    __shared__ unsigned int hist[kMaxBands];
+    const uint32_t B = M->B;
+    const double R = M->R;
+    if (threadIdx.x <= B) c[threadIdx.x] = M->c[threadIdx.x];
+    if (threadIdx.x < kMaxBands) hist[threadIdx.x] = 0;
+    __syncthreads();
+    bool bad = false;
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const double ph = phi[i], r = rr[i];
+        if (!(ph >= 0.0 && ph < dm::kTwoPi && r >= 0.0 && r <= R)) bad = true;
+        const uint32_t b = band_of(r >= 0.0 ? r : 0.0, c, B);
+        keys[i] = (static_cast<uint64_t>(b) << 32) | angle_key(ph >= 0.0 ? ph : 0.0);
+        ids[i] = static_cast<uint32_t>(i);
+        atomicAdd(&hist[b], 1u);
+    }
+    if (bad) atomicMax(&M->error, kErrBadPoint);
+    __syncthreads();
+    if (threadIdx.x < B && hist[threadIdx.x]) atomicAdd(&M->band_count[threadIdx.x], hist[threadIdx.x]);
+}
+
+__global__ void band_offsets_kernel(Meta *M)
+{
+    if (threadIdx.x != 0) return;
+    uint64_t s = 0;
+    for (uint32_t j = 0; j < M->B; ++j) {
+        M->band_start[j] = s;
+        s += M->band_count[j];
+    }
+    M->band_start[M->B] = s;
+}
+
+__global__ void __launch_bounds__(256) gather_kernel(uint64_t n, uint64_t seed, const uint64_t *keys,
+                                                     const uint32_t *sids, const double *phi_by_id,
+                                                     const double *r_by_id, SortedPoints P)
+{
+    for (uint64_t p = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t id = sids[p];
+        const double ph = phi_by_id ? phi_by_id[id] : phi_from_u53(draw(id, seed).x0 >> 11);
+        const double r = r_by_id[id];
+        P.phi[p] = ph;
+        P.r[p] = r;
+        P.ch[p] = dm::cosh(r);
+        P.sh[p] = dm::sinh(r);
+        P.akey[p] = static_cast<uint32_t>(keys[p]);
+        P.id[p] = id;
+    }
+}
+
+__global__ void points_by_id_kernel(const Meta *M, uint64_t n, uint64_t seed, double *phi, double *r)
+{
+    const double R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const U64x4 x = draw(i, seed);
+        phi[i] = phi_from_u53(x.x0 >> 11);
+        r[i] = radius_from_u53(x.x1 >> 11, R, cm1, inv_alpha);
+    }
+}
+
+__global__ void dm_eval_kernel(int fn, const double *in, double *out, uint64_t count)
+{
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < count;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const double x = in[i];
+        double y;
+        switch (fn) {
+            case 0: y = dm::exp(x); break;
+            case 1: y = dm::log(x); break;
+            case 2: y = dm::cos(x); break;
+            case 3: y = dm::cosh(x); break;
+            default: y = dm::sinh(x); break;
+        }
+        out[i] = y;
+    }
+}
+
+unsigned grid_for(uint64_t n, int threads, int per_sm)
+{
+    const uint64_t need = ceil_div(n ? n : 1, static_cast<uint64_t>(threads));
+    const uint64_t cap = static_cast<uint64_t>(num_sms()) * per_sm;
+    return static_cast<unsigned>(need < cap ? need : cap);
+}
+
+}  // namespace
+
+Status launch_plan(Meta *d_meta, uint64_t n, double k, double alpha, uint64_t seed, uint32_t B,
+                   double p, double R_override, cudaStream_t stream)
+{
+    Status st;
+    plan_kernel<<<1, kPlanThreads, 0, stream>>>(d_meta, n, k, alpha, seed, B, p, R_override);
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+Status launch_sample(Meta *d_meta, uint64_t n, uint64_t seed, uint64_t *keys, uint32_t *ids,
+                     double *r_by_id, cudaStream_t stream)
+{
+    Status st;
+    sample_kernel<<<grid_for(n, kSampleThreads, 8), kSampleThreads, 0, stream>>>(d_meta, n, seed, keys,
+                                                                                ids, r_by_id);
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+Status launch_load_points(Meta *d_meta, uint64_t n, const double *phi, const double *r,
+                          uint64_t *keys, uint32_t *ids, cudaStream_t stream)
+{
+    Status st;
+    load_points_kernel<<<grid_for(n, kSampleThreads, 8), kSampleThreads, 0, stream>>>(d_meta, n, phi, r,
+                                                                                     keys, ids);
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+Status launch_band_offsets(Meta *d_meta, cudaStream_t stream)
+{
+    Status st;
+    band_offsets_kernel<<<1, 32, 0, stream>>>(d_meta);
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+Status launch_gather(const Meta *d_meta, uint64_t n, uint64_t seed, const uint64_t *sorted_keys,
+                     const uint32_t *sorted_ids, const double *phi_by_id, const double *r_by_id,
+                     SortedPoints P, cudaStream_t stream)
+{
+    (void)d_meta;
+    Status st;
+    gather_kernel<<<grid_for(n, 256, 8), 256, 0, stream>>>(n, seed, sorted_keys, sorted_ids, phi_by_id,
+                                                         r_by_id, P);
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+Status launch_dm_eval(int fn, const double *in, double *out, uint64_t count, cudaStream_t stream)
+{
+    Status st;
+    dm_eval_kernel<<<grid_for(count, 256, 8), 256, 0, stream>>>(fn, in, out, count);
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+Status launch_points_by_id(const Meta *d_meta, uint64_t n, uint64_t seed, double *phi, double *r,
+                           cudaStream_t stream)
+{
+    Status st;
+    points_by_id_kernel<<<grid_for(n, 256, 8), 256, 0, stream>>>(d_meta, n, seed, phi, r);
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+}  // namespace rhg

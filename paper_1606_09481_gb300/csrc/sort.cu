@@ -1,0 +1,189 @@
+// sort.cu -- stable LSD radix sort of 64-bit keys with optional uint32 payload
+// (Alg. 1 "sort points in b by their angular coordinates": one global sort keyed
+// by (band, angle key) orders every band at once).
+//
+// One pass per 8-bit digit:
+//   upsweep   each CTA histograms the digit over its contiguous chunk;
+//   scan      one CTA turns the digit-major [digit][cta] counts into offsets;
+//   downsweep each CTA walks its chunk tile by tile; inside a tile every warp
+//             ranks its 32 x kItems keys with __match_any_sync, warps are combined
+//             by a per-digit prefix over warps, so the order of equal digits is the
+//             input order (stable), and keys are scattered to their offsets.
+#include "kernels.h"
+
+namespace rhg {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 8;
+constexpr int kTile = kThreads * kItems;  // keys per tile
+constexpr int kRadix = 256;
+
+struct Grid {
+    uint32_t ctas;
+    uint64_t tiles_per_cta;
+};
+
+Grid sort_grid(uint64_t n)
+{
+    const uint64_t tiles = ceil_div(n ? n : 1, kTile);
+    const uint64_t max_ctas = static_cast<uint64_t>(num_sms()) * 4;
+    const uint64_t ctas = tiles < max_ctas ? tiles : max_ctas;
+    return Grid{static_cast<uint32_t>(ctas), ceil_div(tiles, ctas)};
+}
+
+__global__ void __launch_bounds__(kThreads) upsweep_kernel(const uint64_t *keys, uint64_t n, int shift,
+                                                           uint64_t tiles_per_cta, uint32_t *counts)
+{
+    __shared__ uint32_t hist[kRadix];
+    hist[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t begin = blockIdx.x * tiles_per_cta * kTile;
+    uint64_t end = begin + tiles_per_cta * kTile;
+    if (end > n) end = n;
+    for (uint64_t i = begin + threadIdx.x; i < end; i += kThreads)
+        atomicAdd(&hist[(keys[i] >> shift) & (kRadix - 1)], 1u);
+    __syncthreads();
+    counts[static_cast<uint64_t>(threadIdx.x) * gridDim.x + blockIdx.x] = hist[threadIdx.x];
+}
+
+// exclusive scan over total = kRadix * ctas counts, in place; one CTA of 1024 threads
+__global__ void __launch_bounds__(1024) scan_counts_kernel(uint32_t *counts, uint32_t total)
+{
+    __shared__ uint32_t part[1024];
+    const uint32_t per = (total + 1023) / 1024;
+    const uint32_t b = threadIdx.x * per;
+    uint32_t e = b + per;
+    if (e > total) e = total;
+    uint32_t s = 0;
+    for (uint32_t i = b; i < e; ++i) s += counts[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const uint32_t v = threadIdx.x >= static_cast<unsigned>(off) ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    for (uint32_t i = b; i < e; ++i) {
+        const uint32_t c = counts[i];
+        counts[i] = run;
+        run += c;
+    }
+}
+
+template <bool kValues>
+__global__ void __launch_bounds__(kThreads) downsweep_kernel(const uint64_t *keys_in, uint64_t *keys_out,
+                                                             const uint32_t *vals_in, uint32_t *vals_out,
+                                                             uint64_t n, int shift, uint64_t tiles_per_cta,
+                                                             const uint32_t *offsets)
+{
+    __shared__ uint32_t digit_base[kRadix];
+    __shared__ uint32_t warp_count[kWarps][kRadix];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lanemask_lt = (1u << lane) - 1u;
+    digit_base[threadIdx.x] = offsets[static_cast<uint64_t>(threadIdx.x) * gridDim.x + blockIdx.x];
+    const uint64_t chunk = blockIdx.x * tiles_per_cta * kTile;
+    for (uint64_t t = 0; t < tiles_per_cta; ++t) {
+        const uint64_t tile = chunk + t * kTile;
+        if (tile >= n) break;
+        for (int w = 0; w < kWarps; ++w) warp_count[w][threadIdx.x] = 0;
+        __syncthreads();
+        // rank within the warp's sub-tile: element (i, lane) = sub + i*32 + lane
+        const uint64_t sub = tile + static_cast<uint64_t>(warp) * 32 * kItems;
+        uint64_t key[kItems];
+        uint32_t val[kItems];
+        uint32_t rank[kItems];
+        int digit[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const uint64_t idx = sub + static_cast<uint64_t>(i) * 32 + lane;
+            const bool valid = idx < n;
+            key[i] = valid ? keys_in[idx] : 0;
+            if (kValues) val[i] = valid ? vals_in[idx] : 0;
+            digit[i] = static_cast<int>((key[i] >> shift) & (kRadix - 1));
+            const uint32_t active = __ballot_sync(0xffffffffu, valid);
+            rank[i] = 0xffffffffu;
+            if (valid) {
+                const uint32_t peers = __match_any_sync(active, digit[i]);
+                const uint32_t base = warp_count[warp][digit[i]];
+                rank[i] = base + __popc(peers & lanemask_lt);
+                __syncwarp(active);
+                if ((peers & lanemask_lt) == 0) warp_count[warp][digit[i]] = base + __popc(peers);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit: exclusive prefix over warps, then the tile total
+        {
+            const int d = threadIdx.x;
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t c = warp_count[w][d];
+                warp_count[w][d] = run;
+                run += c;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                if (rank[i] != 0xffffffffu) {
+                    const uint32_t pos = digit_base[digit[i]] + warp_count[warp][digit[i]] + rank[i];
+                    keys_out[pos] = key[i];
+                    if (kValues) vals_out[pos] = val[i];
+                }
+            }
+            __syncthreads();
+            digit_base[d] += run;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t radix_temp_bytes(uint64_t n)
+{
+    const Grid g = sort_grid(n);
+    return static_cast<size_t>(kRadix) * g.ctas * sizeof(uint32_t);
+}
+
+Status radix_sort(uint64_t n, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
+                  const int *shifts, int num_shifts, void *temp, uint64_t **keys_out,
+                  uint32_t **vals_out, cudaStream_t stream)
+{
+    Status st;
+    uint64_t *kin = keys, *kout = keys_alt;
+    uint32_t *vin = vals, *vout = vals_alt;
+    if (n > 1) {
+        const Grid g = sort_grid(n);
+        uint32_t *counts = static_cast<uint32_t *>(temp);
+        for (int s = 0; s < num_shifts; ++s) {
+            upsweep_kernel<<<g.ctas, kThreads, 0, stream>>>(kin, n, shifts[s], g.tiles_per_cta, counts);
+            RHG_LAUNCH_CHECK();
+            scan_counts_kernel<<<1, 1024, 0, stream>>>(counts, kRadix * g.ctas);
+            RHG_LAUNCH_CHECK();
+            if (vals) {
+                downsweep_kernel<true><<<g.ctas, kThreads, 0, stream>>>(kin, kout, vin, vout, n, shifts[s],
+                                                                       g.tiles_per_cta, counts);
+            } else {
+                downsweep_kernel<false><<<g.ctas, kThreads, 0, stream>>>(kin, kout, nullptr, nullptr, n,
+                                                                        shifts[s], g.tiles_per_cta, counts);
+            }
+            RHG_LAUNCH_CHECK();
+            uint64_t *tk = kin;
+            kin = kout;
+            kout = tk;
+            uint32_t *tv = vin;
+            vin = vout;
+            vout = tv;
+        }
+    }
+    *keys_out = kin;
+    if (vals_out) *vals_out = vin;
+    return st;
+}
+
+}  // namespace rhg

@@ -1,0 +1,92 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/rhg.h declares; host-side validation answers without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rhg():
+    import paper_1606_09481_gb300 as rhg
+    rhg.build()
+    return rhg
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "rhg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(rhg_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("rhg_generate_pairs", "rhg_generate_csr", "rhg_target_radius", "rhg_edges_from_points",
+                 "rhg_sample_points", "rhg_status_str", "rhg_workspace_bytes"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(rhg):
+    lib = ctypes.CDLL(rhg.LIB)
+    missing = [f for f in declared_functions() if not hasattr(lib, f)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version(rhg):
+    assert rhg.status_str(0) == "RHG_OK"
+    assert rhg.status_str(6) == "RHG_ERR_OVERFLOW"
+    assert rhg.status_str(99) == "RHG_ERR_UNKNOWN"
+    assert rhg.load().rhg_version() == 1
+
+
+def test_params_layout_matches_header(rhg):
+    assert ctypes.sizeof(rhg.Params) == 56
+    assert ctypes.sizeof(rhg.Result) == 48
+
+
+def _ws_status(rhg, **kw):
+    p = rhg.make_params(**kw)
+    out = ctypes.c_size_t(0)
+    return rhg.load().rhg_workspace_bytes(ctypes.byref(p), 0, ctypes.byref(out)), out.value
+
+
+def test_host_validation(rhg):
+    ok, nbytes = _ws_status(rhg, n=10_000_000, k=200, alpha=1.0)
+    assert ok == 0 and nbytes > 10_000_000 * 80
+    bad = [dict(n=1, k=6, alpha=1.0), dict(n=2**32, k=6, alpha=1.0), dict(n=100, k=6, alpha=0.5),
+           dict(n=100, k=0, alpha=1.0), dict(n=100, k=-1, alpha=1.0), dict(n=100, k=6, alpha=101.0),
+           dict(n=100, k=6, alpha=1.0, num_bands=65), dict(n=100, k=6, alpha=1.0, band_ratio=-0.5),
+           dict(n=100, k=6, alpha=1.0, flags=0x80), dict(n=100, k=6, alpha=float("nan"))]
+    for kw in bad:
+        assert _ws_status(rhg, **kw)[0] == rhg.INVALID_ARG, kw
+    # an R given directly replaces k
+    assert _ws_status(rhg, n=100, k=0, alpha=1.0, R_override=12.0)[0] == 0
+
+
+def test_invalid_arguments_rejected_before_device_work(rhg):
+    L = rhg.load()
+    p = rhg.make_params(n=1, k=6, alpha=1.0)
+    res = rhg.Result()
+    assert L.rhg_generate_pairs(ctypes.byref(p), None, 0, None, 0, None, ctypes.byref(res)) == rhg.INVALID_ARG
+    p = rhg.make_params(n=1000, k=6, alpha=1.0)
+    assert L.rhg_generate_pairs(ctypes.byref(p), None, 0, None, 0, None, ctypes.byref(res)) == rhg.INVALID_ARG
+    # workspace smaller than required: OOM, still before any device work
+    assert L.rhg_generate_pairs(ctypes.byref(p), ctypes.c_void_p(256), 16, ctypes.c_void_p(256), 10, None,
+                                ctypes.byref(res)) == rhg.OOM
+    assert L.rhg_dm_eval(7, None, None, 0, None) == rhg.INVALID_ARG
+    R = ctypes.c_double(0)
+    assert L.rhg_target_radius(100, 6.0, 0.4, None, 0, None, ctypes.byref(R)) == rhg.INVALID_ARG
+
+
+def test_product_package_does_not_touch_oracle():
+    """The product path never imports, loads or links the oracle."""
+    pkg = os.path.join(ROOT, "paper_1606_09481_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                for bad in ("import oracle", "from oracle", "rhg_oracle", "librhg_oracle"):
+                    assert bad not in txt, (f, bad)

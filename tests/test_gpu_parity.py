@@ -1,0 +1,104 @@
+"""Edge sets from the device equal the oracle's, exactly (Alg. 1 range query vs the
+all-pairs definition and the oracle's own Alg. 1)."""
+import numpy as np
+import pytest
+
+from gpu_util import assert_valid_pairs, require_gpu, sorted_pairs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_config1_equals_brute_force(O):
+    """n = 10^4, k = 6, alpha = 1, seed 1: uint32 pairs == O(n^2) all pairs."""
+    rhg = require_gpu()
+    n, k, alpha, seed = 10_000, 6, 1.0, 1
+    pairs, res = rhg.generate_pairs(n, k, alpha, seed)
+    got = sorted_pairs(pairs)
+    assert_valid_pairs(got, n)
+    R = O.target_radius(n, k, alpha)
+    phi, r = O.sample_points(n, alpha, R, seed)
+    ref = O.brute_edges(phi, r, R)
+    assert res.R == R and res.m == len(ref)
+    assert np.array_equal(got, ref)
+    _, st = O.band_edges(phi, r, R, O.default_bands(n), with_stats=True)
+    assert res.near_threshold == st["near_threshold"]
+
+
+SMALL = [(2, 0.5, 1.0, 1), (3, 1, 1.0, 2), (17, 4, 0.8, 3), (100, 6, 1.0, 4), (257, 10, 0.55, 5),
+         (1000, 30, 0.6, 6), (2047, 6, 1.0, 7), (2049, 6, 1.0, 8), (4097, 12, 0.75, 9), (5000, 3, 3.0, 10),
+         (3000, 60, 1.5, 11), (6000, 1, 1.0, 12), (8191, 8, 0.9, 2**40 + 3)]
+
+
+@pytest.mark.parametrize("n,k,alpha,seed", SMALL)
+def test_small_graphs_equal_brute_force(O, n, k, alpha, seed):
+    rhg = require_gpu()
+    pairs, res = rhg.generate_pairs(n, k, alpha, seed)
+    got = sorted_pairs(pairs)
+    R = O.target_radius(n, k, alpha)
+    phi, r = O.sample_points(n, alpha, R, seed)
+    assert np.array_equal(got, O.brute_edges(phi, r, R))
+
+
+@pytest.mark.parametrize("B,p,flags", [(1, 0.9, 0), (2, 0.9, 0), (7, 0.5, 0), (30, 0.9, 0), (64, 0.97, 0),
+                                       (14, 1.0, 0), (14, 0.9, 1)])
+def test_band_structure_does_not_change_edges(O, B, p, flags):
+    rhg = require_gpu()
+    n, k, alpha, seed = 10_000, 6, 1.0, 1
+    base, _ = rhg.generate_pairs(n, k, alpha, seed)
+    other, _ = rhg.generate_pairs(n, k, alpha, seed, num_bands=B, band_ratio=p, flags=flags)
+    assert np.array_equal(sorted_pairs(base), sorted_pairs(other))
+
+
+def test_config2_csr_equals_oracle(O):
+    """n = 10^6, k = 16, alpha = 0.75, seed 2: CSR (row_ptr, sorted columns) ==
+    the oracle's Alg. 1 edge set in CSR form."""
+    rhg = require_gpu()
+    n, k, alpha, seed = 10**6, 16, 0.75, 2
+    row_ptr, col, res = rhg.generate_csr(n, k, alpha, seed)
+    g = O.generate(n, k, alpha, seed, with_stats=True)
+    ref_rp, ref_col = O.pairs_to_csr(g["pairs"], n)
+    assert res.m == len(g["pairs"])
+    assert np.array_equal(row_ptr.cpu().numpy().astype(np.uint64), ref_rp)
+    assert np.array_equal(col.cpu().numpy().astype(np.uint32), ref_col)
+    assert res.near_threshold == g["stats"]["near_threshold"]
+
+
+def test_pairs_to_host_matches_device(O):
+    rhg = require_gpu()
+    import torch
+    n, k, alpha, seed = 20_000, 10, 0.8, 4
+    dev, res = rhg.generate_pairs(n, k, alpha, seed)
+    p = rhg.make_params(n, k, alpha, seed)
+    wsp = rhg.allocate_pairs(p)
+    host = torch.empty(2 * wsp.capacity, dtype=torch.int32).pin_memory()
+    res2 = rhg.generate_pairs_host(n, k, alpha, seed, host, wsp)
+    assert res2.m == res.m
+    assert np.array_equal(sorted_pairs(host[: 2 * res2.m].view(-1, 2)), sorted_pairs(dev))
+
+
+def test_overflow_reports_exact_count(O):
+    rhg = require_gpu()
+    import ctypes
+    n, k, alpha, seed = 10_000, 6, 1.0, 1
+    p = rhg.make_params(n, k, alpha, seed)
+    wsp = rhg.allocate_pairs(p, capacity=1000)
+    res = rhg.Result()
+    rc = rhg.load().rhg_generate_pairs(ctypes.byref(p), wsp.ws.data_ptr(), wsp.ws.numel(), wsp.out.data_ptr(),
+                                       wsp.capacity, rhg._stream(), ctypes.byref(res))
+    assert rc == rhg.OVERFLOW
+    R = O.target_radius(n, k, alpha)
+    phi, r = O.sample_points(n, alpha, R, seed)
+    assert res.m == len(O.brute_edges(phi, r, R))
+    # the retrying wrapper then succeeds
+    pairs, res2 = rhg.generate_pairs(n, k, alpha, seed, workspace=wsp)
+    assert res2.m == res.m and len(pairs) == res.m
+
+
+def test_no_solution_and_invalid():
+    rhg = require_gpu()
+    with pytest.raises(rhg.RhgError) as e:
+        rhg.generate_pairs(100, 1e6, 1.0, 1)
+    assert e.value.status == rhg.NO_SOLUTION
+    with pytest.raises(rhg.RhgError) as e:
+        rhg.generate_pairs(1, 6, 1.0, 1)
+    assert e.value.status == rhg.INVALID_ARG
