@@ -34,12 +34,12 @@ METRIC = "edges/s on 1 GB300 (plain vs batched/served, exact edge set); p50/p99 
 WORKLOAD = {"n": 10_000_000, "k": 200.0, "alpha": 1.0, "seed": 3}
 WORKLOAD_NAME = "plain large graph: n=1e7, k=200, alpha=1.0, seed 3, uint32 pairs (~1G edges)"
 
-# per-unit algorithmic bytes of the emit kernel (range query, emit pass): every
-# point is read once from the sorted arrays (phi, r, cosh r, sinh r: 32 B; sort
-# key 8 B; angle key 4 B; id 4 B; offset 8 B) and every edge is written once as
-# two uint32; candidate reads are served by L1/L2 reuse inside a band window.
-EMIT_BYTES_PER_POINT = 56
-EMIT_BYTES_PER_EDGE = 8
+# per-unit algorithmic bytes of the range query: every point is read once from
+# the sorted arrays (sort key 8 B, angle key 4 B, angle hi/lo 8 B, P/M/S/gamma
+# 16 B, id 4 B) and every edge is written once as two uint32; candidate reads are
+# served by L1/L2 reuse inside a band window.
+QUERY_BYTES_PER_POINT = 40
+QUERY_BYTES_PER_EDGE = 8
 
 
 def parse():
@@ -266,17 +266,17 @@ def run_ours(args):
     ms_per_step = elapsed_ms / args.steps
     value = total_m / (ms_per_step / 1000.0)
 
-    # roofline of the dominant kernel (the emit pass of the range query)
+    # roofline of the dominant stage: the range query (batch, heavy-chunk and
+    # recheck kernels), which writes the output
     stages = {s: timer.totals[s] / max(args.steps, 1) for s in rhg.STAGES}
-    dom = max(("count", "emit"), key=lambda s: stages[s])
-    emit_ms = stages["emit"]
-    alg_bytes = n * EMIT_BYTES_PER_POINT + m * EMIT_BYTES_PER_EDGE
+    q_ms = stages["query"]
+    alg_bytes = n * QUERY_BYTES_PER_POINT + m * QUERY_BYTES_PER_EDGE
     peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / (emit_ms / 1000.0) / 1e9 if emit_ms > 0 else 0.0
-    roofline = {"kernel": "query_kernel<emit>", "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": kernel_traffic("query_emit"),
-                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": emit_ms,
-                "peak_source": f"{peak_kind} hbm_gbs", "dominant_stage": dom}
+    achieved = alg_bytes / (q_ms / 1000.0) / 1e9 if q_ms > 0 else 0.0
+    roofline = {"kernel": "range query (batch_kernel + heavy_kernel + recheck_kernel)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": kernel_traffic("query"), "algorithmic_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": q_ms, "peak_source": f"{peak_kind} hbm_gbs"}
 
     line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -286,7 +286,9 @@ def run_ours(args):
                        "l2": "working set ~9 GB > 129 MB L2 (no flush)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "edges": m, "R": res.R, "candidates": int(res.candidates),
-            "near_threshold": int(res.near_threshold), "stages_ms": stages, "roofline": roofline,
+            "near_threshold": int(res.near_threshold), "rechecks": int(res.rechecks),
+            "mode": "fp32 filter + fp64 recheck" if res.mode else "fp64",
+            "stages_ms": stages, "roofline": roofline,
             "gpu_launches": launches, "clocks": clocks.summary()}
 
     if not args.no_e2e:

@@ -37,6 +37,9 @@
  *   library's deterministic exp/log/cos; the edge set is therefore a pure
  *   function of (n, k, alpha, seed) and does not depend on num_bands,
  *   band_ratio or the filter flags.
+ * - By default (R <= 32 and alpha R <= 80) an FP32 test decides each candidate
+ *   pair whenever its proven error bound, which includes the rounding of the FP64
+ *   predicate, allows; the remaining pairs are decided by the FP64 predicate.
  */
 #ifndef RHG_H
 #define RHG_H
@@ -64,6 +67,10 @@ typedef enum rhg_status {
 /* flags */
 #define RHG_FLAG_FP64_ONLY 0x1u  /* evaluate every candidate with the FP64 predicate
                                     (no FP32 filter); same edge set, slower          */
+#define RHG_FLAG_VERIFY 0x2u     /* debugging: also evaluate the FP64 predicate for
+                                    every pair the FP32 filter decides, and count
+                                    disagreements in rhg_result.verify_failures
+                                    (must be 0); much slower                         */
 
 /* Parameters of one graph (Alg. 1 input: n, average degree k, alpha = (gamma-1)/2). */
 typedef struct rhg_params {
@@ -86,6 +93,10 @@ typedef struct rhg_result {
     uint64_t candidates;      /* candidate pairs examined by the range query             */
     uint64_t near_threshold;  /* candidates with |L - cosh R| <= 1e-12 cosh R            */
     uint64_t rechecks;        /* candidates the FP32 filter sent to the FP64 predicate   */
+    uint64_t verify_failures; /* RHG_FLAG_VERIFY: filter decisions the FP64 predicate
+                                 contradicts (0 unless the filter's error bound fails) */
+    uint32_t mode;            /* 1: FP32 filter + FP64 recheck; 0: FP64 predicate only */
+    uint32_t reserved;
 } rhg_result;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -143,9 +154,10 @@ int rhg_sample_points(const rhg_params *p, void *d_workspace, size_t workspace_b
  * rhg_generate_pairs -- the whole hot path of Alg. 1 on the device: R, band
  * boundaries, sampling, band assignment, radix sort by (band, phi), windows
  * (getMinMaxPhi), binary search, candidate test, and compaction of the edges
- * into d_pairs as m pairs (u, v), u < v, uint32 (2 m words).
- * capacity_edges is the number of pairs d_pairs holds; if m exceeds it the call
- * writes no pairs and returns RHG_ERR_OVERFLOW with result->m = m.
+ * into d_pairs as m pairs (u, v), u < v, uint32 (2 m words, 8-byte aligned;
+ * d_workspace 256-byte aligned).  capacity_edges is the number of pairs d_pairs
+ * holds; if m exceeds it, d_pairs holds an unspecified subset and the call
+ * returns RHG_ERR_OVERFLOW with result->m = m (call again with room for m).
  */
 int rhg_generate_pairs(const rhg_params *p, void *d_workspace, size_t workspace_bytes,
                        uint32_t *d_pairs, uint64_t capacity_edges, void *stream,
@@ -204,15 +216,13 @@ int rhg_dm_eval(int fn, const double *d_in, double *d_out, uint64_t count, void 
  * rhg_launch_count -- number of kernels this library has launched in this
  * process so far (all devices, all threads).
  */
-#define RHG_STAGE_PLAN 0u     /* R solve and band boundaries                     */
-#define RHG_STAGE_SAMPLE 1u   /* Philox sampling / point load and band histogram */
-#define RHG_STAGE_SORT 2u     /* band offsets and radix sort by (band, angle)    */
-#define RHG_STAGE_GATHER 3u   /* sorted structure-of-arrays                      */
-#define RHG_STAGE_COUNT 4u    /* range query, count pass                         */
-#define RHG_STAGE_SCAN 5u     /* exclusive scan of the counts                    */
-#define RHG_STAGE_EMIT 6u     /* range query, emit pass                          */
-#define RHG_STAGE_CSR 7u      /* CSR sort and row pointers                       */
-#define RHG_NUM_STAGES 8u
+#define RHG_STAGE_PLAN 0u     /* R solve and band boundaries                      */
+#define RHG_STAGE_SAMPLE 1u   /* Philox sampling / point load and band histogram  */
+#define RHG_STAGE_SORT 2u     /* band offsets and radix sort by (band, angle)     */
+#define RHG_STAGE_GATHER 3u   /* sorted structure-of-arrays                       */
+#define RHG_STAGE_QUERY 4u    /* range query: windows, search, test, emit, recheck */
+#define RHG_STAGE_CSR 5u      /* CSR sort and row pointers                        */
+#define RHG_NUM_STAGES 6u
 int rhg_set_stage_events(void *const *events, uint32_t count);
 uint64_t rhg_launch_count(void);
 

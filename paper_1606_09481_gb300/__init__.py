@@ -22,6 +22,7 @@ __all__ = [
 
 OK, INVALID_ARG, NO_SOLUTION, OOM, CUDA_ERROR, TIMEOUT, OVERFLOW = range(7)
 FLAG_FP64_ONLY = 0x1
+FLAG_VERIFY = 0x2
 MAX_BANDS = 64
 DM_FUNCS = {"exp": 0, "log": 1, "cos": 2, "cosh": 3, "sinh": 4}
 
@@ -37,7 +38,8 @@ class Params(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("m", _c_u64), ("R", _c_dbl), ("num_bands", _c_u32), ("cuda_error", ctypes.c_int32),
-                ("candidates", _c_u64), ("near_threshold", _c_u64), ("rechecks", _c_u64)]
+                ("candidates", _c_u64), ("near_threshold", _c_u64), ("rechecks", _c_u64),
+                ("verify_failures", _c_u64), ("mode", _c_u32), ("reserved", _c_u32)]
 
     def asdict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -88,7 +90,7 @@ def load() -> ctypes.CDLL:
     return L
 
 
-STAGES = ("plan", "sample", "sort", "gather", "count", "scan", "emit", "csr")
+STAGES = ("plan", "sample", "sort", "gather", "query", "csr")
 
 
 class StageTimer:

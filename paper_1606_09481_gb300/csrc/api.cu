@@ -32,8 +32,9 @@ size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // Byte offsets of every buffer inside the caller's workspace.
 struct Layout {
-    size_t meta, keys0, keys1, ids0, ids1, r_by_id, phi, r, ch, sh, akey, id, counts, offsets, sort_tmp,
-        scan_tmp, csr0, csr1, total;
+    size_t meta, keys0, keys1, ids0, ids1, r_by_id, akey, id, ang, pms, phi, r, ch, sh, heavy, recheck, sort_tmp,
+        csr0, csr1, total;
+    uint32_t heavy_cap, recheck_cap;
 };
 
 Layout make_layout(uint64_t n, uint64_t csr_entries)
@@ -45,24 +46,27 @@ Layout make_layout(uint64_t n, uint64_t csr_entries)
         o = align_up(o + bytes);
         return at;
     };
+    L.heavy_cap = static_cast<uint32_t>(n / 16 + 4096);
+    L.recheck_cap = static_cast<uint32_t>(n / 4 + 4096);
     L.meta = take(sizeof(Meta));
     L.keys0 = take(n * 8);
     L.keys1 = take(n * 8);
     L.ids0 = take(n * 4);
     L.ids1 = take(n * 4);
     L.r_by_id = take(n * 8);
+    L.akey = take(n * 4);
+    L.id = take(n * 4);
+    L.ang = take(n * 8);
+    L.pms = take(n * 16);
     L.phi = take(n * 8);
     L.r = take(n * 8);
     L.ch = take(n * 8);
     L.sh = take(n * 8);
-    L.akey = take(n * 4);
-    L.id = take(n * 4);
-    L.counts = take(n * 4);
-    L.offsets = take((n + 1) * 8);
+    L.heavy = take(static_cast<size_t>(L.heavy_cap) * 16);
+    L.recheck = take(static_cast<size_t>(L.recheck_cap) * 8);
     const size_t sort_points = radix_temp_bytes(n);
     const size_t sort_csr = csr_entries ? radix_temp_bytes(csr_entries) : 0;
     L.sort_tmp = take(sort_points > sort_csr ? sort_points : sort_csr);
-    L.scan_tmp = take(scan_temp_bytes(n));
     L.csr0 = take(csr_entries * 8);
     L.csr1 = take(csr_entries * 8);
     L.total = o;
@@ -82,6 +86,8 @@ uint32_t default_bands(uint64_t n)
     return B < 1 ? 1 : B;
 }
 
+constexpr uint32_t kKnownFlags = RHG_FLAG_FP64_ONLY | RHG_FLAG_VERIFY;
+
 // Host-side validation of rhg_params; fills B and p.
 int check_params(const rhg_params *p, uint32_t *B, double *ratio)
 {
@@ -93,7 +99,7 @@ int check_params(const rhg_params *p, uint32_t *B, double *ratio)
     if (!has_R && !(p->k > 0.0 && p->k < 1e300)) return RHG_ERR_INVALID_ARG;
     if (p->num_bands > RHG_MAX_BANDS) return RHG_ERR_INVALID_ARG;
     if (p->band_ratio < 0.0 || !std::isfinite(p->band_ratio)) return RHG_ERR_INVALID_ARG;
-    if (p->flags & ~RHG_FLAG_FP64_ONLY) return RHG_ERR_INVALID_ARG;
+    if (p->flags & ~kKnownFlags) return RHG_ERR_INVALID_ARG;
     *B = p->num_bands ? p->num_bands : default_bands(p->n);
     *ratio = p->band_ratio > 0.0 ? p->band_ratio : 0.9;
     return RHG_OK;
@@ -116,38 +122,25 @@ int error_from_meta(uint32_t e)
     }
 }
 
-// The scalars of Meta the host reads back after a run.
-struct MetaTail {
-    double R;
-    uint32_t B, error;
-    uint64_t m, candidates, near_threshold, rechecks;
-};
-
-Status read_meta(const Meta *d_meta, MetaTail *t, cudaStream_t stream)
+Status read_meta(const Meta *d_meta, Meta *h, cudaStream_t stream)
 {
     Status st;
-    Meta h;
-    RHG_CUDA_TRY(cudaMemcpyAsync(&h, d_meta, sizeof(Meta), cudaMemcpyDeviceToHost, stream));
+    RHG_CUDA_TRY(cudaMemcpyAsync(h, d_meta, sizeof(Meta), cudaMemcpyDeviceToHost, stream));
     RHG_CUDA_TRY(cudaStreamSynchronize(stream));
-    t->R = h.R;
-    t->B = h.B;
-    t->error = h.error;
-    t->m = h.m;
-    t->candidates = h.candidates;
-    t->near_threshold = h.near_threshold;
-    t->rechecks = h.rechecks;
     return st;
 }
 
-void fill_result(rhg_result *res, const MetaTail &t)
+void fill_result(rhg_result *res, const Meta &h)
 {
     if (!res) return;
-    res->m = t.m;
-    res->R = t.R;
-    res->num_bands = t.B;
-    res->candidates = t.candidates;
-    res->near_threshold = t.near_threshold;
-    res->rechecks = t.rechecks;
+    res->m = h.m;
+    res->R = h.R;
+    res->num_bands = h.B;
+    res->candidates = h.candidates;
+    res->near_threshold = h.near_threshold;
+    res->rechecks = h.rechecks;
+    res->verify_failures = h.verify_failures;
+    res->mode = h.filter ? 1u : 0u;
 }
 
 struct Pipeline {
@@ -160,28 +153,44 @@ struct Pipeline {
         SortedPoints P;
         P.n = n;
         P.key = sorted_keys;
+        P.akey = at<uint32_t>(ws, L.akey);
+        P.id = at<uint32_t>(ws, L.id);
+        P.ang = at<float2>(ws, L.ang);
+        P.pms = at<float4>(ws, L.pms);
         P.phi = at<double>(ws, L.phi);
         P.r = at<double>(ws, L.r);
         P.ch = at<double>(ws, L.ch);
         P.sh = at<double>(ws, L.sh);
-        P.akey = at<uint32_t>(ws, L.akey);
-        P.id = at<uint32_t>(ws, L.id);
         return P;
     }
 };
 
-// Points, bands, sort and gather; leaves the sorted SoA in the workspace.
-Status build_points(const Pipeline &pl, uint64_t seed, const double *phi_in, const double *r_in,
-                    const uint64_t **sorted_keys, cudaStream_t stream)
+int bits_for(uint64_t v)
+{
+    int b = 0;
+    while (b < 64 && (v >> b)) ++b;
+    return b;
+}
+
+enum class Output { Pairs, Csr };
+
+// One full pass of the hot path on the stream: plan, points, bands, sort, gather,
+// range query (+ heavy chunks + FP64 rechecks).  No host synchronisation.
+Status enqueue(const Pipeline &pl, const PlanArgs &pa, const double *phi_in, const double *r_in, Output kind,
+               uint32_t *d_pairs, uint64_t capacity_edges, uint32_t heavy_min, cudaStream_t stream)
 {
     Status st;
     Meta *M = pl.meta();
+    mark(RHG_STAGE_PLAN, false, stream);
+    st = launch_plan(M, pa, stream);
+    if (st.code) return st;
+    mark(RHG_STAGE_PLAN, true, stream);
     uint64_t *k0 = at<uint64_t>(pl.ws, pl.L.keys0), *k1 = at<uint64_t>(pl.ws, pl.L.keys1);
     uint32_t *i0 = at<uint32_t>(pl.ws, pl.L.ids0), *i1 = at<uint32_t>(pl.ws, pl.L.ids1);
     double *rid = at<double>(pl.ws, pl.L.r_by_id);
     mark(RHG_STAGE_SAMPLE, false, stream);
     if (phi_in) st = launch_load_points(M, pl.n, phi_in, r_in, k0, i0, stream);
-    else st = launch_sample(M, pl.n, seed, k0, i0, rid, stream);
+    else st = launch_sample(M, pl.n, pa.seed, k0, i0, rid, stream);
     if (st.code) return st;
     mark(RHG_STAGE_SAMPLE, true, stream);
     mark(RHG_STAGE_SORT, false, stream);
@@ -195,84 +204,53 @@ Status build_points(const Pipeline &pl, uint64_t seed, const double *phi_in, con
     if (st.code) return st;
     mark(RHG_STAGE_SORT, true, stream);
     mark(RHG_STAGE_GATHER, false, stream);
-    st = launch_gather(M, pl.n, seed, ks, is, phi_in, phi_in ? r_in : rid, pl.sorted(ks), stream);
+    const SortedPoints P = pl.sorted(ks);
+    st = launch_gather(M, pl.n, pa.seed, ks, is, phi_in, r_in, phi_in ? r_in : rid, P, stream);
+    if (st.code) return st;
     mark(RHG_STAGE_GATHER, true, stream);
-    *sorted_keys = ks;
+    QueryArgs q{};
+    q.M = M;
+    q.P = P;
+    q.src_phi = phi_in;
+    q.src_r = r_in;
+    q.pairs = kind == Output::Pairs ? d_pairs : nullptr;
+    q.csr_keys = kind == Output::Csr ? at<uint64_t>(pl.ws, pl.L.csr0) : nullptr;
+    q.capacity = capacity_edges;
+    q.heavy = at<uint4>(pl.ws, pl.L.heavy);
+    q.heavy_cap = pl.L.heavy_cap;
+    q.recheck = at<uint2>(pl.ws, pl.L.recheck);
+    q.recheck_cap = pl.L.recheck_cap;
+    q.heavy_min = heavy_min;
+    mark(RHG_STAGE_QUERY, false, stream);
+    st = launch_query(q, kind == Output::Csr, stream);
+    if (st.code) return st;
+    mark(RHG_STAGE_QUERY, true, stream);
     return st;
 }
 
-int bits_for(uint64_t v)
-{
-    int b = 0;
-    while (b < 64 && (v >> b)) ++b;
-    return b;
-}
+constexpr uint32_t kHeavyMin = 1024;
 
-enum class Output { Pairs, Csr };
-
-// The query, scan and emit stages shared by every generate entry point.
-Status run_query(const Pipeline &pl, const uint64_t *sorted_keys, Output kind, uint32_t *d_pairs,
-                 uint64_t capacity, uint64_t *d_row_ptr, uint32_t *d_col, MetaTail *tail, int *status,
-                 cudaStream_t stream)
+// Runs the pipeline and reads the metadata back (one synchronisation).  If a
+// work list overflowed (only for extremely dense graphs) it runs again in FP64
+// mode without heavy chunks, which needs no list.
+Status run_pipeline(const Pipeline &pl, PlanArgs pa, const double *phi_in, const double *r_in, Output kind,
+                    uint32_t *d_pairs, uint64_t capacity_edges, Meta *h, cudaStream_t stream)
 {
-    Status st;
-    Meta *M = pl.meta();
-    const SortedPoints P = pl.sorted(sorted_keys);
-    uint32_t *counts = at<uint32_t>(pl.ws, pl.L.counts);
-    uint64_t *offsets = at<uint64_t>(pl.ws, pl.L.offsets);
-    mark(RHG_STAGE_COUNT, false, stream);
-    st = launch_query_count(M, P, counts, stream);
+    Status st = enqueue(pl, pa, phi_in, r_in, kind, d_pairs, capacity_edges, kHeavyMin, stream);
     if (st.code) return st;
-    mark(RHG_STAGE_COUNT, true, stream);
-    mark(RHG_STAGE_SCAN, false, stream);
-    st = exclusive_scan_u32(counts, offsets, pl.n, &M->m, at<void>(pl.ws, pl.L.scan_tmp), stream);
+    st = read_meta(pl.meta(), h, stream);
     if (st.code) return st;
-    mark(RHG_STAGE_SCAN, true, stream);
-    st = read_meta(M, tail, stream);
-    if (st.code) return st;
-    *status = error_from_meta(tail->error);
-    if (*status != RHG_OK) return st;
-    const uint64_t need = kind == Output::Pairs ? tail->m : 2 * tail->m;
-    if (need > capacity) {
-        *status = RHG_ERR_OVERFLOW;
-        return st;
+    if (h->error == kErrListFull) {
+        pa.allow_filter = 0;
+        st = enqueue(pl, pa, phi_in, r_in, kind, d_pairs, capacity_edges, 0xFFFFFFFFu, stream);
+        if (st.code) return st;
+        st = read_meta(pl.meta(), h, stream);
     }
-    if (kind == Output::Pairs) {
-        mark(RHG_STAGE_EMIT, false, stream);
-        if (tail->m) st = launch_query_emit(M, P, offsets, d_pairs, nullptr, stream);
-        if (st.code) return st;
-        mark(RHG_STAGE_EMIT, true, stream);
-    } else {
-        uint64_t *c0 = at<uint64_t>(pl.ws, pl.L.csr0), *c1 = at<uint64_t>(pl.ws, pl.L.csr1);
-        mark(RHG_STAGE_EMIT, false, stream);
-        if (tail->m) {
-            st = launch_query_emit(M, P, offsets, nullptr, c0, stream);
-            if (st.code) return st;
-        }
-        mark(RHG_STAGE_EMIT, true, stream);
-        mark(RHG_STAGE_CSR, false, stream);
-        const int nb = bits_for(pl.n - 1);
-        int shifts[16];
-        int ns = 0;
-        for (int s = 0; s < nb; s += 8) shifts[ns++] = s;
-        for (int s = 0; s < nb; s += 8) shifts[ns++] = 32 + s;
-        uint64_t *sorted = nullptr;
-        st = radix_sort(need, c0, c1, nullptr, nullptr, shifts, ns, at<void>(pl.ws, pl.L.sort_tmp), &sorted,
-                        nullptr, stream);
-        if (st.code) return st;
-        st = launch_csr_finish(sorted, need, pl.n, d_row_ptr, d_col, stream);
-        if (st.code) return st;
-        mark(RHG_STAGE_CSR, true, stream);
-    }
-    Meta h;
-    RHG_CUDA_TRY(cudaMemcpyAsync(&h, M, sizeof(Meta), cudaMemcpyDeviceToHost, stream));
-    RHG_CUDA_TRY(cudaStreamSynchronize(stream));
-    *status = error_from_meta(h.error);
     return st;
 }
 
-int generate(const rhg_params *p, void *d_ws, size_t ws_bytes, Output kind, uint32_t *d_pairs,
-             uint64_t capacity, uint64_t *d_row_ptr, uint32_t *d_col, cudaStream_t stream, rhg_result *res)
+int generate(const rhg_params *p, void *d_ws, size_t ws_bytes, Output kind, uint32_t *d_pairs, uint64_t capacity,
+             uint64_t *d_row_ptr, uint32_t *d_col, cudaStream_t stream, rhg_result *res)
 {
     if (res) std::memset(res, 0, sizeof(*res));
     uint32_t B;
@@ -280,24 +258,46 @@ int generate(const rhg_params *p, void *d_ws, size_t ws_bytes, Output kind, uint
     int rc = check_params(p, &B, &ratio);
     if (rc) return rc;
     if (!d_ws) return RHG_ERR_INVALID_ARG;
-    if (kind == Output::Pairs && capacity && !d_pairs) return RHG_ERR_INVALID_ARG;
+    if (kind == Output::Pairs && capacity && (!d_pairs || (reinterpret_cast<uintptr_t>(d_pairs) & 7)))
+        return RHG_ERR_INVALID_ARG;
     if (kind == Output::Csr && (!d_row_ptr || (capacity && !d_col))) return RHG_ERR_INVALID_ARG;
     const Layout L = make_layout(p->n, kind == Output::Csr ? capacity : 0);
     if (ws_bytes < L.total) return RHG_ERR_OOM;
+    if (reinterpret_cast<uintptr_t>(d_ws) & 255) return RHG_ERR_INVALID_ARG;
     Pipeline pl{d_ws, L, p->n};
-    mark(RHG_STAGE_PLAN, false, stream);
-    Status st = launch_plan(pl.meta(), p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override, stream);
+    PlanArgs pa{p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override,
+                (p->flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u, (p->flags & RHG_FLAG_VERIFY) ? 1u : 0u};
+    const uint64_t cap_edges = kind == Output::Pairs ? capacity : capacity / 2;
+    Meta h;
+    Status st = run_pipeline(pl, pa, nullptr, nullptr, kind, d_pairs, cap_edges, &h, stream);
     if (st.code) return finish(st, res);
-    mark(RHG_STAGE_PLAN, true, stream);
-    const uint64_t *sk = nullptr;
-    st = build_points(pl, p->seed, nullptr, nullptr, &sk, stream);
-    if (st.code) return finish(st, res);
-    MetaTail tail{};
-    int status = RHG_OK;
-    st = run_query(pl, sk, kind, d_pairs, capacity, d_row_ptr, d_col, &tail, &status, stream);
-    if (st.code) return finish(st, res);
-    fill_result(res, tail);
-    return status;
+    fill_result(res, h);
+    if (h.error) return error_from_meta(h.error);
+    if (h.m > cap_edges) return RHG_ERR_OVERFLOW;
+    if (kind == Output::Csr) {
+        const uint64_t entries = 2 * h.m;
+        uint64_t *c0 = at<uint64_t>(pl.ws, pl.L.csr0), *c1 = at<uint64_t>(pl.ws, pl.L.csr1);
+        const int nb = bits_for(p->n - 1);
+        int shifts[16];
+        int ns = 0;
+        for (int s = 0; s < nb; s += 8) shifts[ns++] = s;
+        for (int s = 0; s < nb; s += 8) shifts[ns++] = 32 + s;
+        uint64_t *sorted = nullptr;
+        mark(RHG_STAGE_CSR, false, stream);
+        st = radix_sort(entries, c0, c1, nullptr, nullptr, shifts, ns, at<void>(pl.ws, pl.L.sort_tmp), &sorted,
+                        nullptr, stream);
+        if (st.code) return finish(st, res);
+        st = launch_csr_finish(sorted, entries, p->n, d_row_ptr, d_col, stream);
+        if (st.code) return finish(st, res);
+        mark(RHG_STAGE_CSR, true, stream);
+        const cudaError_t e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) {
+            st.code = RHG_ERR_CUDA;
+            st.cuda = e;
+            return finish(st, res);
+        }
+    }
+    return RHG_OK;
 }
 
 }  // namespace
@@ -363,7 +363,8 @@ int rhg_plan(const rhg_params *p, void *d_workspace, size_t workspace_bytes, voi
     if (workspace_bytes < sizeof(Meta)) return RHG_ERR_OOM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Meta *d = static_cast<Meta *>(d_workspace);
-    const Status st = launch_plan(d, p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override, s);
+    const PlanArgs pa{p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override, 1u, 0u};
+    const Status st = launch_plan(d, pa, s);
     if (st.code) return st.code;
     Meta h;
     if (cudaMemcpyAsync(&h, d, sizeof(Meta), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RHG_ERR_CUDA;
@@ -399,7 +400,8 @@ int rhg_sample_points(const rhg_params *p, void *d_workspace, size_t workspace_b
     if (workspace_bytes < sizeof(Meta)) return RHG_ERR_OOM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Meta *M = static_cast<Meta *>(d_workspace);
-    Status st = launch_plan(M, p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override, s);
+    const PlanArgs pa{p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override, 1u, 0u};
+    Status st = launch_plan(M, pa, s);
     if (st.code) return st.code;
     st = launch_points_by_id(M, p->n, p->seed, d_phi, d_r, s);
     if (st.code) return st.code;
@@ -459,26 +461,25 @@ int rhg_edges_from_points(const double *d_phi, const double *d_r, uint64_t n, do
     if (result) std::memset(result, 0, sizeof(*result));
     if (n < 1 || n > 0xFFFFFFFFull || !d_phi || !d_r || !d_workspace) return RHG_ERR_INVALID_ARG;
     if (!(R > 0.0) || !(R <= 700.0) || num_bands > RHG_MAX_BANDS) return RHG_ERR_INVALID_ARG;
-    if (band_ratio < 0.0 || !std::isfinite(band_ratio) || (flags & ~RHG_FLAG_FP64_ONLY)) return RHG_ERR_INVALID_ARG;
-    if (capacity_edges && !d_pairs) return RHG_ERR_INVALID_ARG;
+    if (band_ratio < 0.0 || !std::isfinite(band_ratio) || (flags & ~kKnownFlags)) return RHG_ERR_INVALID_ARG;
+    if (capacity_edges && (!d_pairs || (reinterpret_cast<uintptr_t>(d_pairs) & 7))) return RHG_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_workspace) & 255) return RHG_ERR_INVALID_ARG;
     const uint32_t B = num_bands ? num_bands : default_bands(n < 2 ? 2 : n);
     const double ratio = band_ratio > 0.0 ? band_ratio : 0.9;
     const Layout L = make_layout(n, 0);
     if (workspace_bytes < L.total) return RHG_ERR_OOM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Pipeline pl{d_workspace, L, n};
-    // alpha only enters the sampler, which is not used here
-    Status st = launch_plan(pl.meta(), n, 1.0, 1.0, 0, B, ratio, R, s);
+    // alpha and k only enter the sampler and the R solve, which are not used here
+    const PlanArgs pa{n, 1.0, 1.0, 0, B, ratio, R, (flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u,
+                      (flags & RHG_FLAG_VERIFY) ? 1u : 0u};
+    Meta h;
+    const Status st = run_pipeline(pl, pa, d_phi, d_r, Output::Pairs, d_pairs, capacity_edges, &h, s);
     if (st.code) return finish(st, result);
-    const uint64_t *sk = nullptr;
-    st = build_points(pl, 0, d_phi, d_r, &sk, s);
-    if (st.code) return finish(st, result);
-    MetaTail tail{};
-    int status = RHG_OK;
-    st = run_query(pl, sk, Output::Pairs, d_pairs, capacity_edges, nullptr, nullptr, &tail, &status, s);
-    if (st.code) return finish(st, result);
-    fill_result(result, tail);
-    return status;
+    fill_result(result, h);
+    if (h.error) return error_from_meta(h.error);
+    if (h.m > capacity_edges) return RHG_ERR_OVERFLOW;
+    return RHG_OK;
 }
 
 int rhg_dm_eval(int fn, const double *d_in, double *d_out, uint64_t count, void *stream)

@@ -12,6 +12,23 @@
 namespace rhg {
 
 constexpr int kMaxBands = static_cast<int>(RHG_MAX_BANDS);
+constexpr int kExpTab = 64;  // e^k table for k = -64..64 (FP32 filter values)
+
+// ---------------------------------------------------------------------------
+// FP32 filter: error model.  The filter evaluates X = L / cosh R in the
+// cancellation-free form X = P_v M_w + M_v P_w + 2 S_v S_w sin^2(d/2) with
+// P = e^{r - G}, M = e^{-r - G}, S = sinh(r) e^{-G} sqrt 2, G = ln(2 cosh R)/2,
+// all FP32, and decides only when |X - 1| exceeds a bound on every error
+// between X and the rounded FP64 predicate (Eq. 3); other pairs are rechecked
+// with the FP64 predicate itself.
+constexpr double kDeltaR = 1e-6;        // |r_approx - r| (FP32-assisted radius, proven <= 5.4e-7)
+constexpr float kEpsPM = 2e-6f;          // relative error of stored P and M (analysis: <= 8.4e-7)
+constexpr float kEps32 = 5.9604645e-8f;  // 2^-24
+constexpr float kCBase = 6e-6f;          // 2 kEpsPM + 8 eps32 + 2 eps_sin, rounded up
+constexpr float kAngAbs = 2e-13f;        // absolute error of |phi_v - phi_w| from the hi/lo split, x2
+constexpr float kC64 = 3.56e-15f;        // 32 u (1 + 1e-3): |L - X H| / H <= kC64 (P_v+M_v)(P_w+M_w)
+constexpr double kFilterMaxR = 32.0;     // above this the FP64 noise of Eq. 3 makes the filter useless
+constexpr double kFilterMaxAlphaR = 80.0;  // FP32 range of cosh(alpha R) in the approximate radius
 
 // Per-graph metadata, written by the plan kernel and read by all later stages.
 struct Meta {
@@ -20,22 +37,30 @@ struct Meta {
     double alpha;
     double inv_alpha;  // 1 / alpha
     double cm1;        // dm::cosh(alpha R) - 1 (inverse CDF of Eq. 1)
+    double G;          // ln(2 cosh R) / 2 (FP32 filter scaling)
     double c[kMaxBands + 1];        // band boundaries c_0 = 0 .. c_B = R
-    double cosh_c[kMaxBands + 1];   // cosh / sinh of the boundaries (windows only)
+    double cosh_c[kMaxBands + 1];   // cosh / sinh of the boundaries (FP64 windows)
     double sinh_c[kMaxBands + 1];
     uint64_t band_start[kMaxBands + 1];  // sorted position of each band's first point
     uint32_t band_count[kMaxBands];
+    // FP32 window constants of band i: inner radius c_i - kDeltaR, outer c_{i+1} + kDeltaR
+    float band_P[kMaxBands + 1], band_M[kMaxBands + 1], band_S[kMaxBands + 1];
+    float band_PMn[kMaxBands + 1];  // P + M at the outer radius
+    float etab[2 * kExpTab + 1];    // e^k rounded to float
     uint32_t B;
     uint32_t error;          // nonzero: a device-side check failed (see kErr*)
+    uint32_t filter;         // 1: FP32 filter + FP64 recheck; 0: FP64 predicate per candidate
+    uint32_t verify;         // 1: check every filter decision against the FP64 predicate
     uint64_t n;
     uint64_t seed;
     double k;
-    uint64_t m;              // edges found (exact)
+    uint64_t m;              // edges found (exact), also the output cursor
     uint64_t candidates;
     uint64_t near_threshold;
     uint64_t rechecks;
-    uint64_t work_counter;   // dynamic work distribution
-    uint64_t emit_cursor;    // output reservation
+    uint64_t verify_failures;
+    uint32_t heavy_n, heavy_next;      // heavy-range chunk list
+    uint32_t recheck_n, pad0;          // FP64 recheck list
 };
 
 // device-side error codes (Meta::error)
@@ -44,6 +69,7 @@ constexpr uint32_t kErrNoSolution = 1;
 constexpr uint32_t kErrBadPoint = 2;
 constexpr uint32_t kErrTimeout = 3;
 constexpr uint32_t kErrInternal = 4;
+constexpr uint32_t kErrListFull = 5;  // heavy or recheck list overflowed: rerun in FP64 mode
 
 // ----------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 64x64->128
@@ -97,6 +123,49 @@ __device__ __forceinline__ double radius_from_u53(uint64_t u53, double R, double
     const double y = __dadd_rn(__dadd_rn(1.0, w), sq);
     const double r = __dmul_rn(dm::log(y), inv_alpha);
     return r > R ? R : r;
+}
+
+__device__ __forceinline__ double phi_from_u53(uint64_t u53)
+{
+    const double ph = __dmul_rn(static_cast<double>(u53), kPhiScale);
+    return ph < dm::kTwoPi ? ph : 0x1.921fb54442d17p+2;  // largest double below 2pi
+}
+
+// Philox block of point `id`: word 0 -> angle, word 1 -> radius.
+__device__ __forceinline__ U64x4 draw(uint64_t id, uint64_t seed)
+{
+    return philox4x64_10(U64x4{id, 0, 0, 0}, seed, 0);
+}
+
+// Radius for band assignment and the FP32 filter, without FP64 transcendentals:
+// y = 1 + w + sqrt(w (w + 2)) in FP32 from the FP64 w = U (cosh(alpha R) - 1)
+// (relative error <= 4 * 2^-24), ln y = e ln 2 + ln m with m in [sqrt(1/2),
+// sqrt(2)) (logf: 1 ulp, <= 3e-8 here), assembled in FP64:
+// |r_approx - r| <= (2.4e-7 + 3e-8) / alpha <= 5.4e-7 < kDeltaR for alpha > 1/2.
+// Requires alpha R <= kFilterMaxAlphaR (w must be finite in FP32).
+__device__ __forceinline__ double radius_approx(uint64_t u53, double R, double cm1, double inv_alpha)
+{
+    const double U = static_cast<double>(u53) * kU53;
+    const float wf = static_cast<float>(U * cm1);
+    const float y = (1.0f + wf) + sqrtf(wf * (wf + 2.0f));
+    int e;
+    float m = frexpf(y, &e);
+    if (m < 0.70710678f) {
+        m *= 2.0f;
+        e -= 1;
+    }
+    const double lg = static_cast<double>(e) * 0.69314718055994530942 + static_cast<double>(logf(m));
+    const double r = lg * inv_alpha;
+    return r < R ? (r > 0.0 ? r : 0.0) : R;
+}
+
+// The sampler's FP64 angle and radius of point `id` (Alg. 1, Eq. 1).
+__device__ __forceinline__ void point_fp64(uint64_t id, uint64_t seed, double R, double cm1, double inv_alpha,
+                                           double *ph, double *r)
+{
+    const U64x4 x = draw(id, seed);
+    *ph = phi_from_u53(x.x0 >> 11);
+    *r = radius_from_u53(x.x1 >> 11, R, cm1, inv_alpha);
 }
 
 // Canonical edge predicate (Eq. 3, threshold test of Alg. 1): returns L; the

@@ -5,38 +5,63 @@
 
 namespace rhg {
 
+struct PlanArgs {
+    uint64_t n;
+    double k, alpha;
+    uint64_t seed;
+    uint32_t B;
+    double p;
+    double R_override;
+    uint32_t allow_filter;  // FP32 filter permitted (the plan still requires R, alpha R in range)
+    uint32_t verify;        // check every filter decision against the FP64 predicate
+};
+
 // Sorted, structure-of-arrays view of the points: position p is the p-th point in
-// (band, angle) order.
+// (band, angle key) order.  Filter mode fills akey/ang/pms/id; FP64 mode fills
+// akey/id and phi/r/ch/sh.
 struct SortedPoints {
     uint64_t n;
     const uint64_t *key;  // (band << 32) | angle key, ascending
+    uint32_t *akey;       // angle key (low 32 bits of key)
+    uint32_t *id;         // vertex id
+    float2 *ang;          // filter: angle as hi + lo floats
+    float4 *pms;          // filter: P, M, S, relative error of S
     double *phi;          // FP64 angle
     double *r;            // FP64 radius
     double *ch;           // dm::cosh(r)
     double *sh;           // dm::sinh(r)
-    uint32_t *akey;       // angle key (low 32 bits of key)
-    uint32_t *id;         // vertex id
+};
+
+// Everything the range query kernels read and write.
+struct QueryArgs {
+    Meta *M;
+    SortedPoints P;
+    const double *src_phi;  // caller points by id (rhg_edges_from_points), else NULL
+    const double *src_r;
+    uint32_t *pairs;        // output: pairs (u < v), or
+    uint64_t *csr_keys;     // output: directed (row << 32 | col) keys, two per edge
+    uint64_t capacity;      // output capacity in edges
+    uint4 *heavy;           // heavy-range chunks {owner position, lo, hi, 0}
+    uint32_t heavy_cap;
+    uint2 *recheck;         // uncertain pairs {owner position, candidate position}
+    uint32_t recheck_cap;
+    uint32_t heavy_min;     // ranges longer than this go to the heavy chunks (UINT32_MAX: never)
 };
 
 // ---- points.cu ----
-// Plan: R (Eq. 22 solve, or R_override > 0), boundaries, constants; zeroes counters.
-Status launch_plan(Meta *d_meta, uint64_t n, double k, double alpha, uint64_t seed, uint32_t B,
-                   double p, double R_override, cudaStream_t stream);
-// Sample: Philox points by id, band of each, sort keys; band histogram.
+Status launch_plan(Meta *d_meta, const PlanArgs &a, cudaStream_t stream);
 Status launch_sample(Meta *d_meta, uint64_t n, uint64_t seed, uint64_t *keys, uint32_t *ids,
                      double *r_by_id, cudaStream_t stream);
-// Load caller points (validates 0 <= phi < 2pi, 0 <= r <= R).
 Status launch_load_points(Meta *d_meta, uint64_t n, const double *phi, const double *r,
                           uint64_t *keys, uint32_t *ids, cudaStream_t stream);
-// Band offsets from the histogram.
 Status launch_band_offsets(Meta *d_meta, cudaStream_t stream);
-// Gather the sorted SoA (phi recomputed from Philox when phi_by_id is NULL).
+// Both gathers are launched; the one Meta::filter does not select returns at once.
+// Filter: FP32 arrays (phi_src/r_src: caller points, else Philox).  FP64 mode:
+// phi/r/ch/sh (r64_src: the sampled FP64 radii by id, or the caller radii).
 Status launch_gather(const Meta *d_meta, uint64_t n, uint64_t seed, const uint64_t *sorted_keys,
-                     const uint32_t *sorted_ids, const double *phi_by_id, const double *r_by_id,
-                     SortedPoints P, cudaStream_t stream);
-// rhg_dm_eval
+                     const uint32_t *sorted_ids, const double *phi_src, const double *r_src,
+                     const double *r64_src, SortedPoints P, cudaStream_t stream);
 Status launch_dm_eval(int fn, const double *in, double *out, uint64_t count, cudaStream_t stream);
-// Sampled points by id (phi, r), for rhg_sample_points.
 Status launch_points_by_id(const Meta *d_meta, uint64_t n, uint64_t seed, double *phi, double *r,
                            cudaStream_t stream);
 
@@ -50,15 +75,11 @@ Status radix_sort(uint64_t n, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals
                   uint64_t **keys_out, uint32_t **vals_out, cudaStream_t stream);
 
 // ---- query.cu ----
-size_t scan_temp_bytes(uint64_t n);
-// Exclusive scan of counts into offsets[0..n]; the total goes to *total_dst.
-Status exclusive_scan_u32(const uint32_t *counts, uint64_t *offsets, uint64_t n, uint64_t *total_dst,
-                          void *temp, cudaStream_t stream);
-// Range query, count pass (per sorted position: edges reported from it).
-Status launch_query_count(Meta *d_meta, SortedPoints P, uint32_t *counts, cudaStream_t stream);
-// Range query, emit pass: pairs (u < v) at offsets, or directed CSR keys when csr != 0.
-Status launch_query_emit(Meta *d_meta, SortedPoints P, const uint64_t *offsets, uint32_t *pairs,
-                         uint64_t *csr_keys, cudaStream_t stream);
+// Range query (Alg. 1): windows, search, candidate test, output; then the heavy
+// chunks and the FP64 rechecks.  Output positions are reserved per warp batch,
+// so the pair order is unspecified; Meta::m is the exact edge count.  The kernels
+// of both modes are launched; each returns at once unless Meta::filter selects it.
+Status launch_query(const QueryArgs &a, bool csr, cudaStream_t stream);
 // CSR row pointers from directed keys sorted by (row, col); col = low words.
 Status launch_csr_finish(const uint64_t *sorted_keys, uint64_t entries, uint64_t n, uint64_t *row_ptr,
                          uint32_t *col, cudaStream_t stream);

@@ -31,22 +31,21 @@ __device__ double kbar(double R, double nd, double alpha)
 
 constexpr int kPlanThreads = 256;  // grid points j = 0..255 of the bracket search
 
-__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, uint64_t n, double k,
-                                                            double alpha, uint64_t seed, uint32_t B,
-                                                            double p, double R_override)
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, PlanArgs a)
 {
     __shared__ int jstar;
     __shared__ double R_sh;
     __shared__ int fail;
     const int t = threadIdx.x;
-    const double nd = static_cast<double>(n);
+    const double nd = static_cast<double>(a.n);
+    const double alpha = a.alpha, k = a.k;
     if (t == 0) {
         jstar = -1;
         fail = 0;
-        R_sh = R_override;
+        R_sh = a.R_override;
     }
     __syncthreads();
-    if (!(R_override > 0.0)) {
+    if (!(a.R_override > 0.0)) {
         // bracket: the largest integer grid point j with kbar(j) > k
         if (kbar(static_cast<double>(t), nd, alpha) > k) atomicMax(&jstar, t);
         __syncthreads();
@@ -67,18 +66,27 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, uint64_t n,
         }
     }
     __syncthreads();
+    const double R = fail ? 1.0 : R_sh;
+    const double coshR = dm::cosh(R);
+    const double G = 0.5 * ::log(2.0 * coshR);
+    // e^k table (threads 0..128)
+    if (t <= 2 * kExpTab) M->etab[t] = static_cast<float>(::exp(static_cast<double>(t - kExpTab)));
     if (t != 0) return;
     M->error = fail ? kErrNoSolution : kErrNone;
-    const double R = fail ? 1.0 : R_sh;
     M->R = R;
-    M->coshR = dm::cosh(R);
+    M->coshR = coshR;
+    M->G = G;
     M->alpha = alpha;
     M->inv_alpha = div(1.0, alpha);
     M->cm1 = sub(dm::cosh(mul(alpha, R)), 1.0);
+    const uint32_t B = a.B;
+    const double p = a.p;
     M->B = B;
-    M->n = n;
-    M->seed = seed;
+    M->n = a.n;
+    M->seed = a.seed;
     M->k = k;
+    M->filter = (a.allow_filter && R <= kFilterMaxR && alpha * R <= kFilterMaxAlphaR) ? 1u : 0u;
+    M->verify = a.verify;
     // Sec. III-A: c_0 = 0, c_{j+1} - c_j = c_1 p^j, c_1 = (1-p) R / (1 - p^B), c_B = R
     M->c[0] = 0.0;
     if (p == 1.0) {
@@ -95,32 +103,35 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, uint64_t n,
         }
     }
     M->c[B] = R;
+    // FP32 window constants: the filter's radii carry an error up to kDeltaR, so
+    // band i is bounded by c_i - kDeltaR (inner) and c_{i+1} + kDeltaR (outer)
+    const double sq = ::exp(-G);
     for (uint32_t j = 0; j <= B; ++j) {
         M->cosh_c[j] = ::cosh(M->c[j]);
         M->sinh_c[j] = ::sinh(M->c[j]);
+        const double ci = M->c[j] - kDeltaR > 0.0 ? M->c[j] - kDeltaR : 0.0;
+        M->band_P[j] = static_cast<float>(::exp(ci) * sq);
+        M->band_M[j] = static_cast<float>(::exp(-ci) * sq);
+        M->band_S[j] = static_cast<float>(::sinh(ci) * sq * 1.4142135623730951);
+        const double co = (j < B ? M->c[j + 1] : R) + kDeltaR;
+        M->band_PMn[j] = static_cast<float>(2.0 * ::cosh(co) * sq * (1.0 + 1e-6));
     }
     for (uint32_t j = 0; j < static_cast<uint32_t>(kMaxBands); ++j) M->band_count[j] = 0;
     M->m = 0;
     M->candidates = 0;
     M->near_threshold = 0;
     M->rechecks = 0;
-    M->work_counter = 0;
-    M->emit_cursor = 0;
-}
-
-__device__ __forceinline__ double phi_from_u53(uint64_t u53)
-{
-    double ph = mul(static_cast<double>(u53), kPhiScale);
-    return ph < dm::kTwoPi ? ph : 0x1.921fb54442d17p+2;  // largest double below 2pi
-}
-
-__device__ __forceinline__ U64x4 draw(uint64_t id, uint64_t seed)
-{
-    return philox4x64_10(U64x4{id, 0, 0, 0}, seed, 0);
+    M->verify_failures = 0;
+    M->heavy_n = 0;
+    M->heavy_next = 0;
+    M->recheck_n = 0;
 }
 
 constexpr int kSampleThreads = 256;
 
+// Points by id: sort key (band << 32 | angle key) and id.  In filter mode the band
+// comes from the approximate radius (bands are then bounded by c_i -+ kDeltaR);
+// otherwise from the FP64 radius, which is also stored by id for the gather.
 __global__ void __launch_bounds__(kSampleThreads) sample_kernel(Meta *M, uint64_t n, uint64_t seed,
                                                                 uint64_t *keys, uint32_t *ids,
                                                                 double *r_by_id)
@@ -128,19 +139,25 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(Meta *M, uint64_
     __shared__ double c[kMaxBands + 1];
     __shared__ unsigned int hist[kMaxBands];
     const uint32_t B = M->B;
+    const bool filter = M->filter != 0;
     const double R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
     if (threadIdx.x <= B) c[threadIdx.x] = M->c[threadIdx.x];
     if (threadIdx.x < kMaxBands) hist[threadIdx.x] = 0;
     __syncthreads();
+    if (M->error) return;
     for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
         const U64x4 x = draw(i, seed);
-        const double ph = phi_from_u53(x.x0 >> 11);
-        const double r = radius_from_u53(x.x1 >> 11, R, cm1, inv_alpha);
+        double r;
+        if (filter) {
+            r = radius_approx(x.x1 >> 11, R, cm1, inv_alpha);
+        } else {
+            r = radius_from_u53(x.x1 >> 11, R, cm1, inv_alpha);
+            r_by_id[i] = r;
+        }
         const uint32_t b = band_of(r, c, B);
-        keys[i] = (static_cast<uint64_t>(b) << 32) | angle_key(ph);
+        keys[i] = (static_cast<uint64_t>(b) << 32) | static_cast<uint32_t>(x.x0 >> 32);
         ids[i] = static_cast<uint32_t>(i);
-        r_by_id[i] = r;
         atomicAdd(&hist[b], 1u);
     }
     __syncthreads();
@@ -185,14 +202,81 @@ __global__ void band_offsets_kernel(Meta *M)
     M->band_start[M->B] = s;
 }
 
-__global__ void __launch_bounds__(256) gather_kernel(uint64_t n, uint64_t seed, const uint64_t *keys,
-                                                     const uint32_t *sids, const double *phi_by_id,
-                                                     const double *r_by_id, SortedPoints P)
+// e^x in FP32 with relative error <= 4 * 2^-24 for |x| <= kExpTab + 1/2:
+// x = k + f with integer k, |f| <= 1/2 exact in FP64, e^k from the table.
+__device__ __forceinline__ float exp_split(double x, const float *etab)
 {
+    const double kd = rint(x);
+    const int k = static_cast<int>(kd);
+    const float f = static_cast<float>(x - kd);
+    return etab[k + kExpTab] * expf(f);
+}
+
+// Filter-mode values of a point from its FP64 angle and (approximate) radius.
+__device__ __forceinline__ void filter_values(double ph, double r, double G, const float *etab, float2 *ang,
+                                              float4 *pms)
+{
+    const float hi = static_cast<float>(ph);
+    const float lo = static_cast<float>(ph - static_cast<double>(hi));
+    *ang = make_float2(hi, lo);
+    const float P = exp_split(r - G, etab);
+    const float Mv = exp_split(-r - G, etab);
+    float S, gam;
+    if (r >= 1.0) {
+        S = (P - Mv) * 0.70710678118654752f;
+        gam = kEpsPM * ((P + Mv) / (P - Mv)) + 2.0f * kEps32;
+    } else if (r > 0.0) {
+        S = static_cast<float>(::sinh(r) * ::exp(-G) * 1.4142135623730951);
+        gam = kEpsPM * static_cast<float>(::cosh(r) / ::sinh(r)) + 2.0f * kEps32;
+    } else {
+        S = 0.0f;
+        gam = 0.0f;
+    }
+    *pms = make_float4(P, Mv, S, gam);
+}
+
+__global__ void __launch_bounds__(256) gather_filter_kernel(const Meta *M, uint64_t n, uint64_t seed,
+                                                            const uint64_t *keys, const uint32_t *sids,
+                                                            const double *phi_src, const double *r_src,
+                                                            SortedPoints P)
+{
+    __shared__ float etab[2 * kExpTab + 1];
+    for (int j = threadIdx.x; j <= 2 * kExpTab; j += blockDim.x) etab[j] = M->etab[j];
+    __syncthreads();
+    if (M->error || !M->filter) return;
+    const double G = M->G, R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
     for (uint64_t p = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; p < n;
          p += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
         const uint32_t id = sids[p];
-        const double ph = phi_by_id ? phi_by_id[id] : phi_from_u53(draw(id, seed).x0 >> 11);
+        double ph, r;
+        if (phi_src) {
+            ph = phi_src[id];
+            r = r_src[id];
+        } else {
+            const U64x4 x = draw(id, seed);
+            ph = phi_from_u53(x.x0 >> 11);
+            r = radius_approx(x.x1 >> 11, R, cm1, inv_alpha);
+        }
+        float2 a;
+        float4 q;
+        filter_values(ph, r, G, etab, &a, &q);
+        P.akey[p] = static_cast<uint32_t>(keys[p]);
+        P.ang[p] = a;
+        P.pms[p] = q;
+        P.id[p] = id;
+    }
+}
+
+__global__ void __launch_bounds__(256) gather_fp64_kernel(const Meta *M, uint64_t n, uint64_t seed,
+                                                          const uint64_t *keys, const uint32_t *sids,
+                                                          const double *phi_src, const double *r_by_id,
+                                                          SortedPoints P)
+{
+    if (M->error || M->filter) return;
+    for (uint64_t p = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t id = sids[p];
+        const double ph = phi_src ? phi_src[id] : phi_from_u53(draw(id, seed).x0 >> 11);
         const double r = r_by_id[id];
         P.phi[p] = ph;
         P.r[p] = r;
@@ -240,11 +324,10 @@ unsigned grid_for(uint64_t n, int threads, int per_sm)
 
 }  // namespace
 
-Status launch_plan(Meta *d_meta, uint64_t n, double k, double alpha, uint64_t seed, uint32_t B,
-                   double p, double R_override, cudaStream_t stream)
+Status launch_plan(Meta *d_meta, const PlanArgs &a, cudaStream_t stream)
 {
     Status st;
-    plan_kernel<<<1, kPlanThreads, 0, stream>>>(d_meta, n, k, alpha, seed, B, p, R_override);
+    plan_kernel<<<1, kPlanThreads, 0, stream>>>(d_meta, a);
     RHG_LAUNCH_CHECK();
     return st;
 }
@@ -278,13 +361,15 @@ Status launch_band_offsets(Meta *d_meta, cudaStream_t stream)
 }
 
 Status launch_gather(const Meta *d_meta, uint64_t n, uint64_t seed, const uint64_t *sorted_keys,
-                     const uint32_t *sorted_ids, const double *phi_by_id, const double *r_by_id,
-                     SortedPoints P, cudaStream_t stream)
+                     const uint32_t *sorted_ids, const double *phi_src, const double *r_src,
+                     const double *r64_src, SortedPoints P, cudaStream_t stream)
 {
-    (void)d_meta;
     Status st;
-    gather_kernel<<<grid_for(n, 256, 8), 256, 0, stream>>>(n, seed, sorted_keys, sorted_ids, phi_by_id,
-                                                         r_by_id, P);
+    gather_filter_kernel<<<grid_for(n, 256, 8), 256, 0, stream>>>(d_meta, n, seed, sorted_keys, sorted_ids,
+                                                                phi_src, r_src, P);
+    RHG_LAUNCH_CHECK();
+    gather_fp64_kernel<<<grid_for(n, 256, 8), 256, 0, stream>>>(d_meta, n, seed, sorted_keys, sorted_ids,
+                                                              phi_src, r64_src, P);
     RHG_LAUNCH_CHECK();
     return st;
 }

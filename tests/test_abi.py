@@ -44,7 +44,7 @@ def test_status_strings_and_version(rhg):
 
 def test_params_layout_matches_header(rhg):
     assert ctypes.sizeof(rhg.Params) == 56
-    assert ctypes.sizeof(rhg.Result) == 48
+    assert ctypes.sizeof(rhg.Result) == 64
 
 
 def _ws_status(rhg, **kw):
@@ -59,7 +59,7 @@ def test_host_validation(rhg):
     bad = [dict(n=1, k=6, alpha=1.0), dict(n=2**32, k=6, alpha=1.0), dict(n=100, k=6, alpha=0.5),
            dict(n=100, k=0, alpha=1.0), dict(n=100, k=-1, alpha=1.0), dict(n=100, k=6, alpha=101.0),
            dict(n=100, k=6, alpha=1.0, num_bands=65), dict(n=100, k=6, alpha=1.0, band_ratio=-0.5),
-           dict(n=100, k=6, alpha=1.0, flags=0x80), dict(n=100, k=6, alpha=float("nan"))]
+           dict(n=100, k=6, alpha=1.0, flags=0x80), dict(n=100, k=6, alpha=1.0, flags=0x4), dict(n=100, k=6, alpha=float("nan"))]
     for kw in bad:
         assert _ws_status(rhg, **kw)[0] == rhg.INVALID_ARG, kw
     # an R given directly replaces k
