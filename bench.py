@@ -286,7 +286,7 @@ def run_ours(args):
                        "l2": "working set ~9 GB > 129 MB L2 (no flush)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "edges": m, "R": res.R, "candidates": int(res.candidates),
-            "near_threshold": int(res.near_threshold), "rechecks": int(res.rechecks),
+            "near_threshold": int(res.near_threshold), "rechecks": int(res.rechecks), "heavy_chunks": int(res.heavy_chunks),
             "mode": "fp32 filter + fp64 recheck" if res.mode else "fp64",
             "stages_ms": stages, "roofline": roofline,
             "gpu_launches": launches, "clocks": clocks.summary()}

@@ -55,7 +55,9 @@ typedef enum rhg_status {
     RHG_OK = 0,
     RHG_ERR_INVALID_ARG = 1,  /* a parameter or buffer is outside its domain          */
     RHG_ERR_NO_SOLUTION = 2,  /* no R gives average degree k (Eq. 22 peaks below k)   */
-    RHG_ERR_OOM = 3,          /* the workspace passed is smaller than required        */
+    RHG_ERR_OOM = 3,          /* the workspace passed is smaller than required, or the
+                                 graph is too dense for the workspace's work lists
+                                 (average degree in the thousands)                    */
     RHG_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed          */
     RHG_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up                   */
     RHG_ERR_OVERFLOW = 6      /* the output buffer holds fewer entries than required;
@@ -96,7 +98,7 @@ typedef struct rhg_result {
     uint64_t verify_failures; /* RHG_FLAG_VERIFY: filter decisions the FP64 predicate
                                  contradicts (0 unless the filter's error bound fails) */
     uint32_t mode;            /* 1: FP32 filter + FP64 recheck; 0: FP64 predicate only */
-    uint32_t reserved;
+    uint32_t heavy_chunks;    /* long candidate ranges split across warps (diagnostic)  */
 } rhg_result;
 
 /* Human-readable name of a status code (static string, never NULL). */

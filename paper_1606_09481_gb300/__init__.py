@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("m", _c_u64), ("R", _c_dbl), ("num_bands", _c_u32), ("cuda_error", ctypes.c_int32),
                 ("candidates", _c_u64), ("near_threshold", _c_u64), ("rechecks", _c_u64),
-                ("verify_failures", _c_u64), ("mode", _c_u32), ("reserved", _c_u32)]
+                ("verify_failures", _c_u64), ("mode", _c_u32), ("heavy_chunks", _c_u32)]
 
     def asdict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -46,8 +46,8 @@ Layout make_layout(uint64_t n, uint64_t csr_entries)
         o = align_up(o + bytes);
         return at;
     };
-    L.heavy_cap = static_cast<uint32_t>(n / 16 + 4096);
-    L.recheck_cap = static_cast<uint32_t>(n / 4 + 4096);
+    L.heavy_cap = static_cast<uint32_t>(n / 4 + 65536);
+    L.recheck_cap = static_cast<uint32_t>(n / 2 + 65536);
     L.meta = take(sizeof(Meta));
     L.keys0 = take(n * 8);
     L.keys1 = take(n * 8);
@@ -118,6 +118,7 @@ int error_from_meta(uint32_t e)
         case kErrNoSolution: return RHG_ERR_NO_SOLUTION;
         case kErrBadPoint: return RHG_ERR_INVALID_ARG;
         case kErrTimeout: return RHG_ERR_TIMEOUT;
+        case kErrListFull: return RHG_ERR_OOM;
         default: return RHG_ERR_CUDA;
     }
 }
@@ -141,6 +142,7 @@ void fill_result(rhg_result *res, const Meta &h)
     res->rechecks = h.rechecks;
     res->verify_failures = h.verify_failures;
     res->mode = h.filter ? 1u : 0u;
+    res->heavy_chunks = h.heavy_n;
 }
 
 struct Pipeline {
@@ -228,11 +230,12 @@ Status enqueue(const Pipeline &pl, const PlanArgs &pa, const double *phi_in, con
     return st;
 }
 
-constexpr uint32_t kHeavyMin = 1024;
+constexpr uint32_t kHeavyMin = 256;
 
-// Runs the pipeline and reads the metadata back (one synchronisation).  If a
-// work list overflowed (only for extremely dense graphs) it runs again in FP64
-// mode without heavy chunks, which needs no list.
+// Runs the pipeline and reads the metadata back (one synchronisation).  If the
+// FP64-recheck list overflowed it runs again in FP64 mode, which needs none; a
+// heavy-chunk list that overflows even then (average degree in the thousands)
+// is reported as RHG_ERR_OOM by the caller.
 Status run_pipeline(const Pipeline &pl, PlanArgs pa, const double *phi_in, const double *r_in, Output kind,
                     uint32_t *d_pairs, uint64_t capacity_edges, Meta *h, cudaStream_t stream)
 {
@@ -240,9 +243,9 @@ Status run_pipeline(const Pipeline &pl, PlanArgs pa, const double *phi_in, const
     if (st.code) return st;
     st = read_meta(pl.meta(), h, stream);
     if (st.code) return st;
-    if (h->error == kErrListFull) {
+    if (h->error == kErrListFull && h->filter) {
         pa.allow_filter = 0;
-        st = enqueue(pl, pa, phi_in, r_in, kind, d_pairs, capacity_edges, 0xFFFFFFFFu, stream);
+        st = enqueue(pl, pa, phi_in, r_in, kind, d_pairs, capacity_edges, kHeavyMin, stream);
         if (st.code) return st;
         st = read_meta(pl.meta(), h, stream);
     }

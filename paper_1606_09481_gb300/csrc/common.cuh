@@ -46,6 +46,7 @@ struct Meta {
     // FP32 window constants of band i: inner radius c_i - kDeltaR, outer c_{i+1} + kDeltaR
     float band_P[kMaxBands + 1], band_M[kMaxBands + 1], band_S[kMaxBands + 1];
     float band_PMn[kMaxBands + 1];  // P + M at the outer radius
+    float band_Po[kMaxBands + 1], band_Mo[kMaxBands + 1], band_So[kMaxBands + 1];  // at the outer radius
     float etab[2 * kExpTab + 1];    // e^k rounded to float
     uint32_t B;
     uint32_t error;          // nonzero: a device-side check failed (see kErr*)
@@ -61,6 +62,7 @@ struct Meta {
     uint64_t verify_failures;
     uint32_t heavy_n, heavy_next;      // heavy-range chunk list
     uint32_t recheck_n, pad0;          // FP64 recheck list
+    uint64_t work_counter;             // next warp batch of the range query
 };
 
 // device-side error codes (Meta::error)

@@ -115,6 +115,9 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, PlanArgs a)
         M->band_S[j] = static_cast<float>(::sinh(ci) * sq * 1.4142135623730951);
         const double co = (j < B ? M->c[j + 1] : R) + kDeltaR;
         M->band_PMn[j] = static_cast<float>(2.0 * ::cosh(co) * sq * (1.0 + 1e-6));
+        M->band_Po[j] = static_cast<float>(::exp(co) * sq);
+        M->band_Mo[j] = static_cast<float>(::exp(-co) * sq);
+        M->band_So[j] = static_cast<float>(::sinh(co) * sq * 1.4142135623730951);
     }
     for (uint32_t j = 0; j < static_cast<uint32_t>(kMaxBands); ++j) M->band_count[j] = 0;
     M->m = 0;
@@ -125,6 +128,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, PlanArgs a)
     M->heavy_n = 0;
     M->heavy_next = 0;
     M->recheck_n = 0;
+    M->work_counter = 0;
 }
 
 constexpr int kSampleThreads = 256;

@@ -4,18 +4,25 @@
 // band's angle-sorted keys, and the distance test of every candidate (Eq. 3).
 //
 // Work decomposition (GB300): a warp takes a batch of 32 consecutive sorted points
-// (lane = point) and walks the bands; each lane computes its window and key range,
-// and the non-empty (owner, range) entries are queued in shared memory.  A flush
-// then lets all 32 lanes test one owner's candidates at a time, writing one
-// decision bit per candidate, reserves the batch's output with one atomic add and
-// replays the bits to write the pairs.  Ranges longer than kHeavy candidates are
-// cut into chunks that a second kernel spreads over all warps (hub vertices).
+// (lane = point) and walks the bands.  For each band every lane computes
+//  - the window of Sec. III-B from the band's inner radius (every neighbour is
+//    inside), and
+//  - a core window from both band radii: X = cosh(r_v - r_w)/cosh R + 2 sinh r_v
+//    sinh r_w sin^2(d/2)/cosh R is convex in r_w, so it is largest at a band
+//    radius, and a pair whose angle is inside the core is an edge for every r_w
+//    of the band, including the rounding of the FP64 predicate;
+// and queues the core range (certain edges, written without a test) and the
+// fringe ranges (window minus core, tested).  A flush streams the core ranges to
+// the output and lets all 32 lanes test the fringe candidates as one flat
+// stream, one decision bit per candidate, reserves the output with one atomic
+// add per segment and replays the bits to write the pairs.  Long ranges go to a
+// chunk list that a second kernel spreads over all warps (hub vertices).
 //
 // Candidate test: in filter mode an FP32 test of X = L / cosh R written without
 // cancellation, X = P_v M_w + M_v P_w + 2 S_v S_w sin^2(d/2), that decides only when
 // |X - 1| exceeds a bound on all errors, including the rounding of the FP64
 // predicate itself; undecided pairs are queued and the third kernel evaluates the
-// FP64 predicate on them.  FP64 mode evaluates the FP64 predicate directly.
+// FP64 predicate on them.  FP64 mode tests every candidate with the FP64 predicate.
 #include "kernels.h"
 
 namespace rhg {
@@ -23,21 +30,27 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr uint32_t kChunk = 4096;  // candidates per heavy chunk
-constexpr int kListCap = 64;       // queued (owner, range) entries per warp (>= 2 per lane)
-constexpr int kBitWords = 128;     // decision words per warp: kChunk / 32
+constexpr uint32_t kChunk = 4096;      // candidates per heavy chunk
+constexpr uint32_t kCoreHeavy = 4096;  // core ranges longer than this become core chunks
+constexpr uint32_t kBatchBudget = 65536;  // candidates a warp batch keeps; beyond, ranges become chunks
+constexpr int kListCap = 64;           // queued fringe entries per warp (>= 2 per lane)
+constexpr int kCoreCap = 32;           // queued core entries per warp (>= 1 per lane)
+constexpr int kBitWords = 128;         // decision words per warp: kChunk / 32
 constexpr uint32_t kFull = 0x80000000u;  // window half-width meaning "whole band"
 
 constexpr float kPiF = 3.14159265f;             // below pi: the unwrapped branch is safe to pi
 constexpr float kTwoPiHiF = 6.28318548202514648f;
 constexpr float kTwoPiLoF = -1.74845553e-07f;    // 2 pi - kTwoPiHiF
-constexpr float kKeyPerRadF = 683565248.0f;      // 2^32 / (2 pi) in FP32
+constexpr float kKeyPerRadF = 683565248.0f;      // 2^32 / (2 pi) in FP32 (slightly low)
 constexpr double kKeyPerRad = 683565275.57643158;
 constexpr float kWinE1 = 5e-6f;                  // window numerator error, relative to 1 + T
+constexpr float kNearMargin = 2e-12f;            // core pairs stay clear of |L/cosh R - 1| <= 1e-12
 
 struct BandShared {
     uint32_t start[kMaxBands + 1];
-    float P[kMaxBands + 1], Mm[kMaxBands + 1], S[kMaxBands + 1], PMn[kMaxBands + 1];
+    float P[kMaxBands + 1], Mm[kMaxBands + 1], S[kMaxBands + 1];     // inner radius c_i - dr
+    float Po[kMaxBands + 1], Mo[kMaxBands + 1], So[kMaxBands + 1];   // outer radius c_{i+1} + dr
+    float PMn[kMaxBands + 1];
     double c[kMaxBands + 1], sinh_c[kMaxBands + 1], cosh_c[kMaxBands + 1];
 };
 
@@ -48,6 +61,9 @@ __device__ __forceinline__ void load_bands(BandShared &S, const Meta *M)
         S.P[j] = M->band_P[j];
         S.Mm[j] = M->band_M[j];
         S.S[j] = M->band_S[j];
+        S.Po[j] = M->band_Po[j];
+        S.Mo[j] = M->band_Mo[j];
+        S.So[j] = M->band_So[j];
         S.PMn[j] = M->band_PMn[j];
         S.c[j] = M->c[j];
         S.sinh_c[j] = M->sinh_c[j];
@@ -55,60 +71,53 @@ __device__ __forceinline__ void load_bands(BandShared &S, const Meta *M)
     }
 }
 
-// The owner of a range: the point whose neighbours are searched.
-struct Owner {
-    uint32_t p, id;
-    // filter mode
-    float ah, al, P, M, S2, PM, crel, gam;
-    // FP64 mode
-    double phi, r, ch, sh;
+// The values of a range's owner (the point whose neighbours are searched) that
+// its lane keeps in registers for the windows.
+struct OwnerRegs {
+    float P, M, S2, PM, gam;  // filter mode
+    double r, ch, sh;         // FP64 mode
 };
 
+// Per-warp shared state.  Queued fringe entries form a flat candidate stream:
+// entry e holds stream positions pre[e] .. pre[e+1]-1 at sorted positions
+// lo[e] + (j - pre[e]); core entries likewise with cpre/clo.  Owners by lane.
+struct WarpSmem {
+    uint32_t lo[kListCap], pre[kListCap + 1];
+    uint32_t clo[kCoreCap], cpre[kCoreCap + 1];
+    uint8_t own[kListCap], cown[kCoreCap];
+    float4 oa[32];      // filter owner: angle hi, angle lo, P, M
+    float4 ob[32];      // filter owner: 2 S, P + M, kCBase + gamma, unused
+    double2 od[32];     // FP64 owner: phi, cosh r
+    double osh[32];     // FP64 owner: sinh r
+    uint32_t opos[32];  // owner sorted position
+    uint32_t oid[32];   // owner vertex id
+    uint32_t bits[kBitWords];
+    uint8_t round_entry[kBitWords];  // entry holding the first candidate of each round
+};
+
+// Load point p as the owner in slot `slot` (and return the window values).
 template <bool kFilter>
-__device__ __forceinline__ Owner load_owner(const SortedPoints &P, uint32_t p)
+__device__ __forceinline__ OwnerRegs load_owner(const SortedPoints &P, WarpSmem &W, int slot, uint32_t p)
 {
-    Owner o;
-    o.p = p;
-    o.id = P.id[p];
+    OwnerRegs o;
+    W.opos[slot] = p;
+    W.oid[slot] = P.id[p];
     if (kFilter) {
         const float2 a = P.ang[p];
         const float4 q = P.pms[p];
-        o.ah = a.x;
-        o.al = a.y;
         o.P = q.x;
         o.M = q.y;
         o.S2 = 2.0f * q.z;
         o.PM = q.x + q.y;
         o.gam = q.w;
-        o.crel = kCBase + q.w;
+        W.oa[slot] = make_float4(a.x, a.y, q.x, q.y);
+        W.ob[slot] = make_float4(o.S2, o.PM, kCBase + q.w, 0.0f);
     } else {
-        o.phi = P.phi[p];
         o.r = P.r[p];
         o.ch = P.ch[p];
         o.sh = P.sh[p];
-    }
-    return o;
-}
-
-template <bool kFilter>
-__device__ __forceinline__ Owner shfl_owner(const Owner &v, int src)
-{
-    Owner o;
-    const unsigned full = 0xffffffffu;
-    o.p = __shfl_sync(full, v.p, src);
-    o.id = __shfl_sync(full, v.id, src);
-    if (kFilter) {
-        o.ah = __shfl_sync(full, v.ah, src);
-        o.al = __shfl_sync(full, v.al, src);
-        o.P = __shfl_sync(full, v.P, src);
-        o.M = __shfl_sync(full, v.M, src);
-        o.S2 = __shfl_sync(full, v.S2, src);
-        o.PM = __shfl_sync(full, v.PM, src);
-        o.crel = __shfl_sync(full, v.crel, src);
-    } else {
-        o.phi = __shfl_sync(full, v.phi, src);
-        o.ch = __shfl_sync(full, v.ch, src);
-        o.sh = __shfl_sync(full, v.sh, src);
+        W.od[slot] = make_double2(P.phi[p], o.ch);
+        W.osh[slot] = o.sh;
     }
     return o;
 }
@@ -116,38 +125,58 @@ __device__ __forceinline__ Owner shfl_owner(const Owner &v, int src)
 // FP32 filter: 1 = edge, 0 = no edge, 2 = undecided (FP64 recheck).
 //   d    circular |phi_v - phi_w| from hi/lo floats (relative error ~2^-23 plus an
 //        absolute error < kAngAbs / 2 from the hi/lo representation)
-//   t    sin(d/2), odd Taylor polynomial to x^11 on [0, pi/2] (rel. error ~3 ulp)
+//   t    sin(d/2): x - x^3/6 below x = 2^-7 (relative error < x^4/120 < 4e-11),
+//        else the odd Taylor polynomial to x^11 on [0, pi/2] (~3 ulp)
 //   X    P_v M_w + M_v P_w + 2 S_v S_w t^2
-//   err  X (kCBase + gamma_v + gamma_w + kAngAbs / d) + kC64 (P_v + M_v)(P_w + M_w)
-__device__ __forceinline__ int filter_decide(const Owner &v, float2 aw, float4 w)
+//   err  X (kCBase + gamma_v + gamma_w) + kC64 (P_v + M_v)(P_w + M_w)
+//        + 2 S_v S_w t kAngAbs (the absolute angle error)
+__device__ __forceinline__ int filter_decide(float4 va, float4 vb, float2 aw, float4 w)
 {
-    const float dh = v.ah - aw.x;  // correctly rounded: relative error <= 2^-24
+    const float dh = va.x - aw.x;  // correctly rounded: relative error <= 2^-24
     float d;
     if (fabsf(dh) > kPiF) {
         // across 0 / 2 pi: 2 pi - (big - small) = (2 pi_hi - big_hi) + small_hi + lo parts;
         // 2 pi_hi - big_hi is exact (Sterbenz, big > pi), so no absolute error of
         // order ulp(2 pi) enters the small result
         const bool vbig = dh > 0.0f;
-        const float bh = vbig ? v.ah : aw.x, bl = vbig ? v.al : aw.y;
-        const float sh = vbig ? aw.x : v.ah, sl = vbig ? aw.y : v.al;
+        const float bh = vbig ? va.x : aw.x, bl = vbig ? va.y : aw.y;
+        const float sh = vbig ? aw.x : va.x, sl = vbig ? aw.y : va.y;
         d = ((kTwoPiHiF - bh) + sh) + ((kTwoPiLoF - bl) + sl);
     } else {
-        d = fabsf(dh + (v.al - aw.y));
+        d = fabsf(dh + (va.y - aw.y));
     }
     const float x = 0.5f * d;
     const float z = x * x;
-    float t = fmaf(z, -2.50521079e-08f, 2.75573188e-06f);
-    t = fmaf(z, t, -1.98412701e-04f);
-    t = fmaf(z, t, 8.33333377e-03f);
-    t = fmaf(z, t, -1.66666672e-01f);
-    t = fmaf(z * x, t, x);
-    const float X = fmaf(v.S2 * w.z, t * t, fmaf(v.P, w.y, v.M * w.x));
-    const float Q = v.PM * (w.x + w.y);
-    const float rel = v.crel + w.w + __fdividef(kAngAbs, d);
-    const float err = fmaf(X, rel, kC64 * Q);
+    float t;
+    if (x < 0.0078125f) {
+        t = fmaf(z * x, -0.166666672f, x);
+    } else {
+        t = fmaf(z, -2.50521079e-08f, 2.75573188e-06f);
+        t = fmaf(z, t, -1.98412701e-04f);
+        t = fmaf(z, t, 8.33333377e-03f);
+        t = fmaf(z, t, -1.66666672e-01f);
+        t = fmaf(z * x, t, x);
+    }
+    const float ss = vb.x * w.z;  // 2 S_v S_w
+    const float X = fmaf(ss * t, t, fmaf(va.z, w.y, va.w * w.x));
+    const float err = fmaf(X, vb.z + w.w, fmaf(kC64 * vb.y, w.x + w.y, ss * t * kAngAbs));
     if (X + err <= 1.0f) return 1;
     if (X - err > 1.0f) return 0;
     return 2;
+}
+
+// asin(sqrt(Q)) for 0 <= Q < 1 (half the window angle), within 1e-6 relative:
+// below sqrt(Q) = 1/8 the series y + y^3/6 + 3 y^5/40 (next term < 1.7e-7 y),
+// else asinf; sqrt(Q) from rsqrtf (2 ulp).
+__device__ __forceinline__ float half_angle(float Q)
+{
+    if (!(Q > 0.0f)) return 0.0f;
+    const float y = Q * rsqrtf(Q);
+    if (y < 0.125f) {
+        const float y2 = y * y;
+        return y * fmaf(y2, fmaf(y2, 0.075f, 0.16666667f), 1.0f);
+    }
+    return asinf(fminf(y, 1.0f));
 }
 
 // Window half-width in angle-key units (kFull: the whole band).  Filter mode,
@@ -155,7 +184,7 @@ __device__ __forceinline__ int filter_decide(const Owner &v, float2 aw, float4 w
 // (beta - cosh(r_v - c')/cosh R) / (2 sinh r_v sinh c' / cosh R), beta = 1 + the
 // FP64 predicate's error bound for r_w < c_{i+1} + kDeltaR, all from the stored
 // P, M, S with their error bounds added.
-__device__ __forceinline__ uint32_t window_filter(const Owner &v, const BandShared &S, uint32_t i)
+__device__ __forceinline__ uint32_t window_filter(const OwnerRegs &v, const BandShared &S, uint32_t i)
 {
     const float Sc = S.S[i];
     if (i == 0 || !(Sc > 0.0f) || !(v.S2 > 0.0f)) return kFull;
@@ -163,16 +192,50 @@ __device__ __forceinline__ uint32_t window_filter(const Owner &v, const BandShar
     const float beta = fmaf(kC64 * v.PM, S.PMn[i], 1.0f);
     const float num = fmaf(1.0f + T, kWinE1, beta - T);
     const float den = v.S2 * Sc * (1.0f - (v.gam + 6.0f * kEps32));
-    const float Q = num / den;
+    const float Q = __fdividef(num, den);  // 2 ulp, inside the final margin
     if (!(Q < 1.0f)) return kFull;
-    const float th = 2.0f * asinf(sqrtf(fmaxf(Q, 0.0f)));
-    const float keys = fmaf(th, kKeyPerRadF * (1.0f + 2e-5f), 3.0f);
+    const float th = half_angle(fmaxf(Q, 0.0f));
+    const float keys = fmaf(th, kKeyPerRadF * (2.0f * (1.0f + 2e-5f)), 3.0f);
     return keys >= 2147483648.0f ? kFull : static_cast<uint32_t>(keys);
+}
+
+// Core half-width in angle-key units: every w of band i whose key is within it
+// is an edge of the FP64 predicate.  X (exact, for the points' FP64 radii) must
+// stay <= 1 - m at both band radii c' = c_i - dr and c'' = c_{i+1} + dr, with m =
+// the predicate's rounding bound (plus kNearMargin); evaluated as lower bounds
+// from the stored values.  Returns -1 for no core, kFull for the whole band.
+__device__ __forceinline__ int64_t window_core(const OwnerRegs &v, const BandShared &S, uint32_t i)
+{
+    const float m = fmaf(kC64 * v.PM, S.PMn[i], kNearMargin);
+    const float S2d = v.S2 * (1.0f + (v.gam + 6.0f * kEps32));
+    float Q = 4.0f;
+    // outer radius c''
+    {
+        const float T = fmaf(v.P, S.Mo[i], v.M * S.Po[i]);
+        const float num = (1.0f - m - T) - (1.0f + T) * kWinE1;
+        if (!(num > 0.0f)) return -1;
+        const float den = S2d * S.So[i];
+        if (den > 0.0f) Q = fminf(Q, __fdividef(num, den));
+    }
+    // inner radius c'
+    {
+        const float T = fmaf(v.P, S.Mm[i], v.M * S.P[i]);
+        const float num = (1.0f - m - T) - (1.0f + T) * kWinE1;
+        if (!(num > 0.0f)) return -1;
+        const float den = S2d * S.S[i];
+        if (den > 0.0f) Q = fminf(Q, __fdividef(num, den));
+    }
+    if (Q >= 1.0f) return kFull;
+    // the series of half_angle is a lower bound of asin; the factor covers the
+    // quotient's 2 ulp, rsqrtf and asinf
+    const float th = half_angle(Q);
+    const float keys = th * (kKeyPerRadF * (2.0f * (1.0f - 4e-5f))) - 4.0f;
+    return keys < 0.0f ? -1 : static_cast<int64_t>(keys);
 }
 
 // FP64 mode window from the FP64 radius (Sec. III-B getMinMaxPhi), conservative
 // for the rounded predicate: threshold (cosh R + 64 u cosh r_v cosh c_{i+1})(1 + 1e-12).
-__device__ __forceinline__ uint32_t window_fp64(const Owner &v, const BandShared &S, uint32_t i, double coshR)
+__device__ __forceinline__ uint32_t window_fp64(const OwnerRegs &v, const BandShared &S, uint32_t i, double coshR)
 {
     const double ci = S.c[i];
     if (ci <= 0.0 || v.r <= 0.0 || v.sh <= 0.0) return kFull;
@@ -227,7 +290,7 @@ __device__ __forceinline__ void key_ranges(const uint32_t *akey, uint32_t s, uin
     }
 }
 
-__device__ __forceinline__ void push_heavy(const QueryArgs &a, uint32_t p, uint32_t lo, uint32_t hi)
+__device__ __forceinline__ void push_heavy(const QueryArgs &a, uint32_t p, uint32_t lo, uint32_t hi, uint32_t type)
 {
     const uint32_t nch = (hi - lo + kChunk - 1) / kChunk;
     const uint32_t at = atomicAdd(&a.M->heavy_n, nch);
@@ -238,7 +301,7 @@ __device__ __forceinline__ void push_heavy(const QueryArgs &a, uint32_t p, uint3
     for (uint32_t j = 0; j < nch; ++j) {
         const uint32_t c0 = lo + j * kChunk;
         const uint32_t c1 = hi - c0 > kChunk ? c0 + kChunk : hi;
-        a.heavy[at + j] = make_uint4(p, c0, c1, 0u);
+        a.heavy[at + j] = make_uint4(p, c0, c1, type);
     }
 }
 
@@ -270,8 +333,9 @@ __device__ __forceinline__ void fp64_point(const QueryArgs &a, const Meta *M, ui
     sh = dm::sinh(r);
 }
 
-// Verification mode: the FP64 predicate for a pair the filter decided; a
-// contradiction, or a decided pair within 1e-12 of the threshold, is counted.
+// Verification mode: the FP64 predicate for a pair the filter or the core
+// decided; a contradiction, or a decided pair within 1e-12 of the threshold, is
+// counted.
 __device__ __noinline__ void verify_pair(const QueryArgs &a, uint32_t idv, uint32_t idw, int dec, double coshR)
 {
     double pv, cv, sv, pw, cw, sw;
@@ -282,16 +346,16 @@ __device__ __noinline__ void verify_pair(const QueryArgs &a, uint32_t idv, uint3
         atomicAdd(reinterpret_cast<unsigned long long *>(&a.M->verify_failures), 1ull);
 }
 
-// Decide candidate q for owner v; queue undecided pairs; in verification mode
+// Decide candidate q (owner slot o); queue undecided pairs; in verification mode
 // compare every decided pair with the FP64 predicate.
 template <bool kFilter>
-__device__ __forceinline__ int decide(const QueryArgs &a, const Owner &v, uint32_t q, bool in, double coshR,
-                                      bool verify, uint32_t &near)
+__device__ __forceinline__ int decide(const QueryArgs &a, const WarpSmem &W, uint32_t o, uint32_t q, bool in,
+                                      double coshR, bool verify, uint32_t &near)
 {
     const unsigned full = 0xffffffffu;
     int dec = 0;
     if (kFilter) {
-        if (in) dec = filter_decide(v, a.P.ang[q], a.P.pms[q]);
+        if (in) dec = filter_decide(W.oa[o], W.ob[o], a.P.ang[q], a.P.pms[q]);
         const uint32_t um = __ballot_sync(full, dec == 2);
         if (um) {
             const int lane = threadIdx.x & 31;
@@ -300,88 +364,142 @@ __device__ __forceinline__ int decide(const QueryArgs &a, const Owner &v, uint32
             base = __shfl_sync(full, base, 0);
             if (dec == 2) {
                 const uint32_t at = base + __popc(um & ((1u << lane) - 1u));
-                if (at < a.recheck_cap) a.recheck[at] = make_uint2(v.p, q);
+                if (at < a.recheck_cap) a.recheck[at] = make_uint2(W.opos[o], q);
                 else atomicMax(&a.M->error, kErrListFull);
             }
         }
-        if (verify && in && dec != 2) verify_pair(a, v.id, a.P.id[q], dec, coshR);
+        if (verify && in && dec != 2) verify_pair(a, W.oid[o], a.P.id[q], dec, coshR);
     } else if (in) {
-        const double L = predicate_L(v.phi, v.ch, v.sh, a.P.phi[q], a.P.ch[q], a.P.sh[q]);
+        const double2 v = W.od[o];
+        const double L = predicate_L(v.x, v.y, W.osh[o], a.P.phi[q], a.P.ch[q], a.P.sh[q]);
         dec = L <= coshR;
         near += fabs(L - coshR) <= 1e-12 * coshR;
     }
     return dec;
 }
 
-struct WarpSmem {
-    uint32_t lo[kListCap], hi[kListCap];
-    uint32_t own[kListCap];
-    uint32_t bits[kBitWords];
-};
+// Write the queued core entries [0, ccount): certain edges, no test.
+template <bool kCsr>
+__device__ __forceinline__ void flush_core(const QueryArgs &a, WarpSmem &W, int ccount, double coshR, bool verify)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t total = W.cpre[ccount];
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(&a.M->m), total);
+    base = __shfl_sync(full, base, 0);
+    if (base + total > a.capacity) return;
+    int e0 = 0;
+    for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+        while (W.cpre[e0 + 1] <= j0) ++e0;
+        const uint32_t j = j0 + lane;
+        if (j < total) {
+            int e = e0;
+            while (W.cpre[e + 1] <= j) ++e;
+            const uint32_t q = W.clo[e] + (j - W.cpre[e]);
+            const uint32_t idv = W.oid[W.cown[e]], idw = a.P.id[q];
+            write_edge<kCsr>(a, base + j, idv, idw);
+            if (verify) verify_pair(a, idv, idw, 1, coshR);
+        }
+    }
+}
 
-// Decide, reserve and write the queued entries [0, count) of this warp, in
-// segments of at most kBitWords decision words; an entry longer than a segment
-// is continued in the next one.
+// Decide, reserve and write the fringe stream of the queued entries [0, count),
+// in segments of kBitWords rounds of 32 candidates: one decision bit per
+// candidate, one output reservation per segment, then a replay of the set bits.
+// The entry of a round's first candidate advances monotonically (warp-uniform);
+// each lane then steps forward over the few entries its round crosses.
 template <bool kFilter, bool kCsr>
-__device__ __forceinline__ void flush(const QueryArgs &a, WarpSmem &W, int count, const Owner &mine, double coshR,
-                                      bool verify, uint32_t &near)
+__device__ __forceinline__ void flush(const QueryArgs &a, WarpSmem &W, int count, double coshR, bool verify,
+                                      uint32_t &near)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    int e = 0;
-    uint32_t qpos = count ? W.lo[0] : 0;  // next candidate of entry e
-    while (e < count) {
-        const int e_start = e;
-        const uint32_t q_start = qpos;
+    const uint32_t total = W.pre[count];
+    int e0 = 0;  // entry holding stream position j0
+    for (uint32_t seg = 0; seg < total; seg += kBitWords * 32) {
+        const uint32_t seg_end = total - seg > kBitWords * 32 ? seg + kBitWords * 32 : total;
         int words = 0;
         uint32_t edges = 0;
-        while (e < count && words < kBitWords) {
-            const uint32_t hi = W.hi[e];
-            const Owner v = shfl_owner<kFilter>(mine, static_cast<int>(W.own[e]));
-            for (; qpos < hi && words < kBitWords; qpos += 32) {
-                const uint32_t q = qpos + lane;
-                const int dec = decide<kFilter>(a, v, q, q < hi, coshR, verify, near);
-                const uint32_t word = __ballot_sync(full, dec == 1);
-                if (lane == 0) W.bits[words] = word;
-                ++words;
-                edges += __popc(word);
+        for (uint32_t j0 = seg; j0 < seg_end; j0 += 32) {
+            while (W.pre[e0 + 1] <= j0) ++e0;
+            const uint32_t j = j0 + lane;
+            const bool in = j < seg_end;
+            int e = e0;
+            if (in)
+                while (W.pre[e + 1] <= j) ++e;
+            const uint32_t q = W.lo[e] + (j - W.pre[e]);
+            const int dec = decide<kFilter>(a, W, W.own[e], q, in, coshR, verify, near);
+            const uint32_t word = __ballot_sync(full, dec == 1);
+            if (lane == 0) {
+                W.bits[words] = word;
+                W.round_entry[words] = static_cast<uint8_t>(e0);
             }
-            if (qpos >= hi) {
-                ++e;
-                if (e < count) qpos = W.lo[e];
-            }
+            ++words;
+            edges += __popc(word);
         }
         __syncwarp();
         unsigned long long base = 0;
         if (lane == 0 && edges) base = atomicAdd(reinterpret_cast<unsigned long long *>(&a.M->m), edges);
         base = __shfl_sync(full, base, 0);
         if (edges && base + edges <= a.capacity) {
-            int wi = 0, ee = e_start;
-            uint32_t qq = q_start, run = 0;
-            while (wi < words) {
-                const uint32_t hi = W.hi[ee];
-                const uint32_t idv = __shfl_sync(full, mine.id, static_cast<int>(W.own[ee]));
-                for (; qq < hi && wi < words; qq += 32) {
-                    const uint32_t word = W.bits[wi++];
-                    if ((word >> lane) & 1u) write_edge<kCsr>(a, base + run + __popc(word & lt), idv, a.P.id[qq + lane]);
-                    run += __popc(word);
+            uint32_t run = 0;
+            for (int wi = 0; wi < words; ++wi) {
+                const uint32_t word = W.bits[wi];
+                if ((word >> lane) & 1u) {
+                    const uint32_t j = seg + static_cast<uint32_t>(wi) * 32 + lane;
+                    int e = W.round_entry[wi];
+                    while (W.pre[e + 1] <= j) ++e;
+                    const uint32_t q = W.lo[e] + (j - W.pre[e]);
+                    write_edge<kCsr>(a, base + run + __popc(word & lt), W.oid[W.own[e]], a.P.id[q]);
                 }
-                if (qq >= hi) {
-                    ++ee;
-                    if (ee < count) qq = W.lo[ee];
-                }
+                run += __popc(word);
             }
         }
         __syncwarp();
     }
 }
 
+// Test one candidate of the lane's own point (owner values in registers):
+// 1 = edge, 0 = no edge, 2 = undecided (queued for the FP64 recheck).
+template <bool kFilter>
+__device__ __forceinline__ int decide_own(const QueryArgs &a, float4 va, float4 vb, const OwnerRegs &v,
+                                          double phv, uint32_t p, uint32_t idv, uint32_t q, bool in, double coshR,
+                                          bool verify, uint32_t &near)
+{
+    const unsigned full = 0xffffffffu;
+    int dec = 0;
+    if (kFilter) {
+        if (in) dec = filter_decide(va, vb, a.P.ang[q], a.P.pms[q]);
+        const uint32_t um = __ballot_sync(full, dec == 2);
+        if (um) {
+            const int lane = threadIdx.x & 31;
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&a.M->recheck_n, static_cast<uint32_t>(__popc(um)));
+            base = __shfl_sync(full, base, 0);
+            if (dec == 2) {
+                const uint32_t at = base + __popc(um & ((1u << lane) - 1u));
+                if (at < a.recheck_cap) a.recheck[at] = make_uint2(p, q);
+                else atomicMax(&a.M->error, kErrListFull);
+            }
+        }
+        if (verify && in && dec != 2) verify_pair(a, idv, a.P.id[q], dec, coshR);
+    } else if (in) {
+        const double L = predicate_L(phv, v.ch, v.sh, a.P.phi[q], a.P.ch[q], a.P.sh[q]);
+        dec = L <= coshR;
+        near += fabs(L - coshR) <= 1e-12 * coshR;
+    }
+    return dec;
+}
+
+// One warp per batch of 32 consecutive sorted points, lane = point; for each band
+// every lane tests its own few fringe candidates (decision bits in a register),
+// then one warp-wide reservation places each lane's core and fringe edges.
 template <bool kFilter, bool kCsr>
-__global__ void __launch_bounds__(kThreads) batch_kernel(QueryArgs a)
+__global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
 {
     __shared__ BandShared S;
-    __shared__ WarpSmem Wsm[kWarps];
     Meta *M = a.M;
     load_bands(S, M);
     __syncthreads();
@@ -390,74 +508,166 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(QueryArgs a)
     const uint32_t n = static_cast<uint32_t>(a.P.n), B = M->B;
     const double coshR = M->coshR;
     const bool verify = M->verify != 0;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpSmem &W = Wsm[warp];
+    const int lane = threadIdx.x & 31;
     const uint32_t nbatch = (n + 31) / 32;
     unsigned long long cand = 0;
     uint32_t near = 0;
-    for (uint32_t batch = blockIdx.x * kWarps + warp; batch < nbatch; batch += gridDim.x * kWarps) {
+    // batches in sorted order from a shared counter: the costly inner-band batches
+    // start first and the rest fill in around them
+    for (;;) {
+        uint32_t batch = 0;
+        if (lane == 0)
+            batch = static_cast<uint32_t>(atomicAdd(reinterpret_cast<unsigned long long *>(&M->work_counter), 1ull));
+        batch = __shfl_sync(full, batch, 0);
+        if (batch >= nbatch) break;
         const uint32_t p = batch * 32 + lane;
         const bool valid = p < n;
-        Owner mine{};
-        uint32_t bv = B, akv = 0;
+        OwnerRegs mine{};
+        float4 va = make_float4(0, 0, 0, 0), vb = va;
+        double phv = 0.0;
+        uint32_t bv = B, akv = 0, idv = 0;
         if (valid) {
-            mine = load_owner<kFilter>(a.P, p);
+            idv = a.P.id[p];
             bv = static_cast<uint32_t>(a.P.key[p] >> 32);
             akv = a.P.akey[p];
+            if (kFilter) {
+                const float2 an = a.P.ang[p];
+                const float4 q = a.P.pms[p];
+                mine.P = q.x;
+                mine.M = q.y;
+                mine.S2 = 2.0f * q.z;
+                mine.PM = q.x + q.y;
+                mine.gam = q.w;
+                va = make_float4(an.x, an.y, q.x, q.y);
+                vb = make_float4(mine.S2, mine.PM, kCBase + q.w, 0.0f);
+            } else {
+                phv = a.P.phi[p];
+                mine.r = a.P.r[p];
+                mine.ch = a.P.ch[p];
+                mine.sh = a.P.sh[p];
+            }
         }
         const uint32_t bmin = __reduce_min_sync(full, bv);
-        int queued = 0;
+        uint32_t kept = 0;  // candidates this batch keeps (warp-uniform)
         for (uint32_t i = bmin; i < B; ++i) {
             const uint32_t s = S.start[i], e = S.start[i + 1];
             if (s == e) continue;
-            uint32_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;
-            if (valid && i >= bv) {
-                const uint32_t Wk = kFilter ? window_filter(mine, S, i) : window_fp64(mine, S, i, coshR);
-                key_ranges(a.P.akey, s, e, akv, Wk, r0, r1, r2, r3);
+            const bool active = valid && i >= bv;
+            uint32_t Wf = 0;
+            int64_t Wc = -1;
+            bool plain = false;  // window lies inside [0, 2^32): union search and core allowed
+            if (active) {
+                Wf = kFilter ? window_filter(mine, S, i) : window_fp64(mine, S, i, coshR);
+                plain = Wf < kFull && Wf <= akv && akv + Wf >= akv;
+                if (kFilter && plain) Wc = window_core(mine, S, i);
+            }
+            // union of the plain windows: one warp-uniform search narrows the lanes'
+            const uint32_t kmin = __reduce_min_sync(full, plain ? akv - Wf : 0xffffffffu);
+            const uint32_t kmax = __reduce_max_sync(full, plain ? akv + Wf : 0u);
+            uint32_t U0 = s, U1 = e;
+            if (kmin <= kmax) {
+                U0 = lower_key(a.P.akey, s, e, kmin);
+                U1 = upper_key(a.P.akey, U0, e, kmax);
+            }
+            // pieces: fringe [f0, f1), core [c0, c1), fringe [f2, f3)
+            uint32_t f0 = 0, f1 = 0, f2 = 0, f3 = 0, c0 = 0, c1 = 0;
+            if (active) {
+                if (plain) {
+                    f0 = lower_key(a.P.akey, U0, U1, akv - Wf);
+                    f3 = upper_key(a.P.akey, f0, U1, akv + Wf);
+                    if (Wc < 0) {  // no core: the fringe is the whole window
+                        f1 = f3;
+                        f2 = f3;
+                    } else if (Wc >= static_cast<int64_t>(Wf)) {
+                        c0 = f0;
+                        c1 = f3;
+                        f1 = f0;
+                        f2 = f3;
+                    } else {
+                        const uint32_t wc = static_cast<uint32_t>(Wc);
+                        c0 = lower_key(a.P.akey, f0, f3, akv - wc);
+                        c1 = upper_key(a.P.akey, c0, f3, akv + wc);
+                        f1 = c0;
+                        f2 = c1;
+                    }
+                } else {
+                    key_ranges(a.P.akey, s, e, akv, Wf, f0, f1, f2, f3);
+                }
                 if (i == bv) {  // same band: each pair once, from the smaller position
-                    r0 = r0 > p + 1 ? r0 : p + 1;
-                    r2 = r2 > p + 1 ? r2 : p + 1;
+                    const uint32_t m1 = p + 1;
+                    f0 = f0 > m1 ? f0 : m1;
+                    f2 = f2 > m1 ? f2 : m1;
+                    c0 = c0 > m1 ? c0 : m1;
                 }
-                if (r1 < r0) r1 = r0;
-                if (r3 < r2) r3 = r2;
-                cand += (r1 - r0) + (r3 - r2);
-                if (r1 - r0 > a.heavy_min) {
-                    push_heavy(a, p, r0, r1);
-                    r1 = r0;
+                if (f1 < f0) f1 = f0;
+                if (f3 < f2) f3 = f2;
+                if (c1 < c0) c1 = c0;
+                cand += (f1 - f0) + (f3 - f2) + (c1 - c0);
+                // a lane tests at most 32 + 32 fringe candidates itself; a batch keeps
+                // about kBatchBudget candidates; longer ranges become chunks that
+                // every warp shares
+                const uint32_t room = kept < kBatchBudget ? (kBatchBudget - kept) / 32 : 0;
+                const uint32_t hc = kCoreHeavy < (room > 64 ? room : 64) ? kCoreHeavy : (room > 64 ? room : 64);
+                if (f1 - f0 > 32) {
+                    push_heavy(a, p, f0, f1, 0);
+                    f1 = f0;
                 }
-                if (r3 - r2 > a.heavy_min) {
-                    push_heavy(a, p, r2, r3);
-                    r3 = r2;
+                if (f3 - f2 > 32) {
+                    push_heavy(a, p, f2, f3, 0);
+                    f3 = f2;
+                }
+                if (c1 - c0 > hc) {
+                    push_heavy(a, p, c0, c1, 1);
+                    c1 = c0;
                 }
             }
-            const int c0 = r1 > r0, c1 = r3 > r2, cnt = c0 + c1;
-            int incl = cnt;
+            const uint32_t nl = f1 - f0, nf = nl + (f3 - f2), nc = c1 - c0;
+            // fringe tests, one candidate per lane per step
+            uint64_t mask = 0;
+            const uint32_t maxf = __reduce_max_sync(full, nf);
+            for (uint32_t t = 0; t < maxf; ++t) {
+                const bool in = t < nf;
+                const uint32_t q = t < nl ? f0 + t : f2 + (t - nl);
+                const int dec = decide_own<kFilter>(a, va, vb, mine, phv, p, idv, q, in, coshR, verify, near);
+                if (dec == 1) mask |= 1ull << t;
+            }
+            // one reservation for the warp's core and fringe edges of this band
+            const uint32_t cnt = nc + static_cast<uint32_t>(__popcll(mask));
+            uint32_t incl = cnt;
             for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_up_sync(full, incl, off);
+                const uint32_t y = __shfl_up_sync(full, incl, off);
                 if (lane >= off) incl += y;
             }
-            const int total = __shfl_sync(full, incl, 31);
+            const uint32_t total = __shfl_sync(full, incl, 31);
+            kept += total;
             if (total == 0) continue;
-            if (queued + total > kListCap) {
-                flush<kFilter, kCsr>(a, W, queued, mine, coshR, verify, near);
-                queued = 0;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(&M->m), total);
+            base = __shfl_sync(full, base, 0);
+            if (base + total > a.capacity) continue;
+            uint64_t pos = base + (incl - cnt);
+            // core edges: owner by owner, all lanes on consecutive positions (coalesced)
+            uint32_t cores = __ballot_sync(full, nc != 0);
+            while (cores) {
+                const int o = __ffs(cores) - 1;
+                cores &= cores - 1;
+                const uint32_t oc0 = __shfl_sync(full, c0, o), onc = __shfl_sync(full, nc, o);
+                const uint32_t oid = __shfl_sync(full, idv, o);
+                const unsigned long long opos = __shfl_sync(full, static_cast<unsigned long long>(pos), o);
+                for (uint32_t t = lane; t < onc; t += 32) {
+                    const uint32_t idw = a.P.id[oc0 + t];
+                    write_edge<kCsr>(a, opos + t, oid, idw);
+                    if (verify) verify_pair(a, oid, idw, 1, coshR);
+                }
             }
-            int at = queued + incl - cnt;
-            if (c0) {
-                W.lo[at] = r0;
-                W.hi[at] = r1;
-                W.own[at] = lane;
-                ++at;
+            pos += nc;
+            while (mask) {
+                const uint32_t t = static_cast<uint32_t>(__ffsll(static_cast<long long>(mask)) - 1);
+                mask &= mask - 1;
+                const uint32_t q = t < nl ? f0 + t : f2 + (t - nl);
+                write_edge<kCsr>(a, pos++, idv, a.P.id[q]);
             }
-            if (c1) {
-                W.lo[at] = r2;
-                W.hi[at] = r3;
-                W.own[at] = lane;
-            }
-            queued += total;
-            __syncwarp();
         }
-        if (queued) flush<kFilter, kCsr>(a, W, queued, mine, coshR, verify, near);
     }
     for (int off = 16; off; off >>= 1) {
         cand += __shfl_down_sync(full, cand, off);
@@ -470,7 +680,8 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(QueryArgs a)
     }
 }
 
-// Heavy chunks: one warp per chunk of at most kChunk candidates of one owner.
+// Heavy chunks: one warp per chunk of at most kChunk candidates of one owner,
+// tested (type 0) or a core chunk of certain edges (type 1).
 template <bool kFilter, bool kCsr>
 __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
 {
@@ -490,15 +701,24 @@ __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
         item = __shfl_sync(full, item, 0);
         if (item >= count) break;
         const uint4 h = a.heavy[item];
-        // every lane holds the owner; the flush broadcasts from lane 0
-        const Owner mine = load_owner<kFilter>(a.P, h.x);
         if (lane == 0) {
-            W.lo[0] = h.y;
-            W.hi[0] = h.z;
-            W.own[0] = 0;
+            load_owner<kFilter>(a.P, W, 0, h.x);
+            if (h.w) {
+                W.clo[0] = h.y;
+                W.cpre[0] = 0;
+                W.cpre[1] = h.z - h.y;
+                W.cown[0] = 0;
+            } else {
+                W.lo[0] = h.y;
+                W.pre[0] = 0;
+                W.pre[1] = h.z - h.y;
+                W.own[0] = 0;
+            }
         }
         __syncwarp();
-        flush<kFilter, kCsr>(a, W, 1, mine, coshR, verify, near);
+        if (h.w) flush_core<kCsr>(a, W, 1, coshR, verify);
+        else flush<kFilter, kCsr>(a, W, 1, coshR, verify, near);
+        __syncwarp();
     }
     for (int off = 16; off; off >>= 1) near += __shfl_down_sync(full, near, off);
     if (lane == 0 && near)
