@@ -33,6 +33,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kChunk = 4096;      // candidates per heavy chunk
 constexpr uint32_t kCoreHeavy = 4096;  // core ranges longer than this become core chunks
 constexpr uint32_t kBatchBudget = 65536;  // candidates a warp batch keeps; beyond, ranges become chunks
+constexpr uint32_t kRun = 4;              // consecutive batches a warp takes at a time
 constexpr int kListCap = 64;           // queued fringe entries per warp (>= 2 per lane)
 constexpr int kCoreCap = 32;           // queued core entries per warp (>= 1 per lane)
 constexpr int kBitWords = 128;         // decision words per warp: kChunk / 32
@@ -267,6 +268,66 @@ __device__ __forceinline__ uint32_t upper_key(const uint32_t *a, uint32_t lo, ui
     return lo;
 }
 
+// First index in [s, e) whose key is >= x (kUpper: > x), searched outward from
+// the hint h by doubling steps, then by bisection: a few nearby, mostly cached
+// loads when h is close to the answer.
+template <bool kUpper>
+__device__ __forceinline__ uint32_t gallop(const uint32_t *a, uint32_t s, uint32_t e, uint32_t h, uint32_t x)
+{
+    auto before = [&](uint32_t i) { return kUpper ? a[i] <= x : a[i] < x; };  // answer > i
+    uint32_t lo, hi;  // the answer lies in [lo, hi]
+    if (h < s) h = s;
+    if (h < e && before(h)) {
+        lo = h + 1;
+        hi = lo;
+        uint32_t step = 1;
+        while (hi < e && before(hi)) {
+            lo = hi + 1;
+            hi = e - lo > step ? lo + step : e;
+            step <<= 1;
+        }
+    } else {
+        hi = h < e ? h : e;
+        lo = hi;
+        uint32_t step = 1;
+        while (lo > s && !before(lo - 1)) {
+            hi = lo - 1;
+            lo = hi - s > step ? hi - step : s;
+            step <<= 1;
+        }
+    }
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (before(mid)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Four independent bisections over [lo, hi) advanced in lock step (memory-level
+// parallelism): r0 = first key >= x0, r1 = first key > x1, r2 = first key >= x2,
+// r3 = first key > x3.
+__device__ __forceinline__ void search4(const uint32_t *a, uint32_t lo, uint32_t hi, uint32_t x0, uint32_t x1,
+                                        uint32_t x2, uint32_t x3, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                        uint32_t &r3)
+{
+    uint32_t l0 = lo, h0 = hi, l1 = lo, h1 = hi, l2 = lo, h2 = hi, l3 = lo, h3 = hi;
+    while (l0 < h0 || l1 < h1 || l2 < h2 || l3 < h3) {
+        const uint32_t m0 = l0 + ((h0 - l0) >> 1), m1 = l1 + ((h1 - l1) >> 1);
+        const uint32_t m2 = l2 + ((h2 - l2) >> 1), m3 = l3 + ((h3 - l3) >> 1);
+        const uint32_t k0 = l0 < h0 ? a[m0] : 0u, k1 = l1 < h1 ? a[m1] : 0u;
+        const uint32_t k2 = l2 < h2 ? a[m2] : 0u, k3 = l3 < h3 ? a[m3] : 0u;
+        if (l0 < h0) { if (k0 < x0) l0 = m0 + 1; else h0 = m0; }
+        if (l1 < h1) { if (k1 <= x1) l1 = m1 + 1; else h1 = m1; }
+        if (l2 < h2) { if (k2 < x2) l2 = m2 + 1; else h2 = m2; }
+        if (l3 < h3) { if (k3 <= x3) l3 = m3 + 1; else h3 = m3; }
+    }
+    r0 = l0;
+    r1 = l1;
+    r2 = l2;
+    r3 = l3;
+}
+
 // Candidate positions in band [s, e) for keys in [a - W, a + W] (mod 2^32): at most
 // two disjoint ranges [r0, r1) and [r2, r3).
 __device__ __forceinline__ void key_ranges(const uint32_t *akey, uint32_t s, uint32_t e, uint32_t a, uint32_t W,
@@ -309,11 +370,13 @@ template <bool kCsr>
 __device__ __forceinline__ void write_edge(const QueryArgs &a, uint64_t pos, uint32_t i1, uint32_t i2)
 {
     const uint32_t u = i1 < i2 ? i1 : i2, v = i1 < i2 ? i2 : i1;
+    // streaming (evict-first) stores: the output must not push the point arrays,
+    // which every warp re-reads, out of L2
     if (kCsr) {
-        a.csr_keys[2 * pos] = (static_cast<uint64_t>(u) << 32) | v;
-        a.csr_keys[2 * pos + 1] = (static_cast<uint64_t>(v) << 32) | u;
+        __stcs(reinterpret_cast<unsigned long long *>(a.csr_keys + 2 * pos), (static_cast<unsigned long long>(u) << 32) | v);
+        __stcs(reinterpret_cast<unsigned long long *>(a.csr_keys + 2 * pos + 1), (static_cast<unsigned long long>(v) << 32) | u);
     } else {
-        reinterpret_cast<uint2 *>(a.pairs)[pos] = make_uint2(u, v);
+        __stcs(reinterpret_cast<uint2 *>(a.pairs) + pos, make_uint2(u, v));
     }
 }
 
@@ -512,13 +575,26 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
     const uint32_t nbatch = (n + 31) / 32;
     unsigned long long cand = 0;
     uint32_t near = 0;
-    // batches in sorted order from a shared counter: the costly inner-band batches
-    // start first and the rest fill in around them
+    // runs of kRun consecutive batches in sorted order from a shared counter: the
+    // costly inner-band batches start first and the rest fill in around them; within
+    // a run each band's search starts from the previous batch's result
+    __shared__ uint32_t hint_sm[kWarps][kMaxBands];
+    uint32_t *hint = hint_sm[threadIdx.x >> 5];
+    uint32_t run_left = 0, batch = 0;
     for (;;) {
-        uint32_t batch = 0;
-        if (lane == 0)
-            batch = static_cast<uint32_t>(atomicAdd(reinterpret_cast<unsigned long long *>(&M->work_counter), 1ull));
-        batch = __shfl_sync(full, batch, 0);
+        if (run_left == 0) {
+            uint32_t first = 0;
+            if (lane == 0)
+                first = static_cast<uint32_t>(
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&M->work_counter), static_cast<unsigned long long>(kRun)));
+            batch = __shfl_sync(full, first, 0);
+            run_left = kRun;
+            for (int j = lane; j < kMaxBands; j += 32) hint[j] = 0xffffffffu;
+            __syncwarp();
+        } else {
+            ++batch;
+        }
+        --run_left;
         if (batch >= nbatch) break;
         const uint32_t p = batch * 32 + lane;
         const bool valid = p < n;
@@ -566,27 +642,22 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
             const uint32_t kmax = __reduce_max_sync(full, plain ? akv + Wf : 0u);
             uint32_t U0 = s, U1 = e;
             if (kmin <= kmax) {
-                U0 = lower_key(a.P.akey, s, e, kmin);
-                U1 = upper_key(a.P.akey, U0, e, kmax);
+                const uint32_t h = hint[i];
+                U0 = (h >= s && h < e) ? gallop<false>(a.P.akey, s, e, h, kmin) : lower_key(a.P.akey, s, e, kmin);
+                U1 = gallop<true>(a.P.akey, U0, e, U0, kmax);
+                if (lane == 0) hint[i] = U0;
             }
             // pieces: fringe [f0, f1), core [c0, c1), fringe [f2, f3)
             uint32_t f0 = 0, f1 = 0, f2 = 0, f3 = 0, c0 = 0, c1 = 0;
             if (active) {
                 if (plain) {
-                    f0 = lower_key(a.P.akey, U0, U1, akv - Wf);
-                    f3 = upper_key(a.P.akey, f0, U1, akv + Wf);
+                    const uint32_t wc = Wc < 0 ? 0u : (Wc >= static_cast<int64_t>(Wf) ? Wf : static_cast<uint32_t>(Wc));
+                    search4(a.P.akey, U0, U1, akv - Wf, akv + Wf, akv - wc, akv + wc, f0, f3, c0, c1);
                     if (Wc < 0) {  // no core: the fringe is the whole window
+                        c0 = c1 = 0;
                         f1 = f3;
                         f2 = f3;
-                    } else if (Wc >= static_cast<int64_t>(Wf)) {
-                        c0 = f0;
-                        c1 = f3;
-                        f1 = f0;
-                        f2 = f3;
                     } else {
-                        const uint32_t wc = static_cast<uint32_t>(Wc);
-                        c0 = lower_key(a.P.akey, f0, f3, akv - wc);
-                        c1 = upper_key(a.P.akey, c0, f3, akv + wc);
                         f1 = c0;
                         f2 = c1;
                     }
@@ -646,18 +717,32 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
             base = __shfl_sync(full, base, 0);
             if (base + total > a.capacity) continue;
             uint64_t pos = base + (incl - cnt);
-            // core edges: owner by owner, all lanes on consecutive positions (coalesced)
+            // core edges: owner by owner, all lanes on consecutive positions
+            // (coalesced); four owners' ids are loaded before they are written
             uint32_t cores = __ballot_sync(full, nc != 0);
             while (cores) {
-                const int o = __ffs(cores) - 1;
-                cores &= cores - 1;
-                const uint32_t oc0 = __shfl_sync(full, c0, o), onc = __shfl_sync(full, nc, o);
-                const uint32_t oid = __shfl_sync(full, idv, o);
-                const unsigned long long opos = __shfl_sync(full, static_cast<unsigned long long>(pos), o);
-                for (uint32_t t = lane; t < onc; t += 32) {
-                    const uint32_t idw = a.P.id[oc0 + t];
-                    write_edge<kCsr>(a, opos + t, oid, idw);
-                    if (verify) verify_pair(a, oid, idw, 1, coshR);
+                uint32_t ow[4], oc[4], on[4], oi[4];
+                unsigned long long op[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int o = cores ? __ffs(cores) - 1 : 0;
+                    const bool has = cores != 0;
+                    cores &= cores ? cores - 1 : 0u;
+                    oc[k] = __shfl_sync(full, c0, o);
+                    on[k] = has ? __shfl_sync(full, nc, o) : 0u;
+                    oi[k] = __shfl_sync(full, idv, o);
+                    op[k] = __shfl_sync(full, static_cast<unsigned long long>(pos), o);
+                }
+                for (uint32_t t = lane; t < on[0] || t < on[1] || t < on[2] || t < on[3]; t += 32) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) ow[k] = t < on[k] ? a.P.id[oc[k] + t] : 0u;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (t < on[k]) {
+                            write_edge<kCsr>(a, op[k] + t, oi[k], ow[k]);
+                            if (verify) verify_pair(a, oi[k], ow[k], 1, coshR);
+                        }
+                    }
                 }
             }
             pos += nc;
