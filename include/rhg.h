@@ -176,6 +176,31 @@ int rhg_generate_pairs_host(const rhg_params *p, void *d_workspace, size_t works
                             uint64_t h_capacity_edges, void *stream, rhg_result *result);
 
 /*
+ * rhg_generate_pairs_static -- rhg_generate_pairs without a caller workspace and
+ * without allocating device memory.  The paper has no counterpart: this is a
+ * library convenience.  It serves callers that cannot allocate device memory,
+ * such as code that runs under a device-memory budget fixed up front, a plugin
+ * whose host program owns every device allocation, or a loop that cannot afford
+ * the device-wide synchronisation a cudaFree implies.
+ *
+ * The scratch is one fixed array of RHG_STATIC_SCRATCH_BYTES in the library's
+ * device image, so p->n is limited to RHG_STATIC_MAX_POINTS; a larger n returns
+ * RHG_ERR_INVALID_ARG before anything is launched.  The array's address is
+ * looked up on the first call on each device (with that device current), so
+ * that first call should come before any stream capture begins.  Nothing in the
+ * scratch has to start at zero: the first kernel of every call resets the
+ * counters it uses.  All calls on one device share the one array, so calls
+ * that overlap in time (other host threads, or other streams before the
+ * previous call returned) race; serialise them.  d_pairs, capacity_edges,
+ * result and the return codes are as in rhg_generate_pairs, and the edges are
+ * the same.
+ */
+#define RHG_STATIC_MAX_POINTS 131072u
+#define RHG_STATIC_SCRATCH_BYTES (16u << 20)
+int rhg_generate_pairs_static(const rhg_params *p, uint32_t *d_pairs, uint64_t capacity_edges,
+                              void *stream, rhg_result *result);
+
+/*
  * rhg_generate_csr -- the same graph as symmetric CSR: d_row_ptr (n + 1 uint64)
  * and d_col (2 m uint32, ascending within each row).  capacity_entries is the
  * number of uint32 d_col holds; the workspace must hold

@@ -76,6 +76,7 @@ def load() -> ctypes.CDLL:
     L.rhg_sample_points.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _p, _p, ctypes.POINTER(_c_dbl)]
     L.rhg_generate_pairs.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _c_u64, _p,
                                      ctypes.POINTER(Result)]
+    L.rhg_generate_pairs_static.argtypes = [ctypes.POINTER(Params), _p, _c_u64, _p, ctypes.POINTER(Result)]
     L.rhg_generate_pairs_host.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _c_u64, _p, _c_u64, _p,
                                           ctypes.POINTER(Result)]
     L.rhg_generate_csr.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _p, _c_u64, _p,
@@ -252,6 +253,23 @@ def generate_pairs(n, k, alpha, seed, num_bands=0, band_ratio=0.0, flags=0, R_ov
                                   wsp.capacity, _stream(stream), ctypes.byref(res))
     _check(rc, "rhg_generate_pairs", res)
     return wsp.out[: 2 * res.m].view(-1, 2), res
+
+
+STATIC_MAX_POINTS = 131072  # RHG_STATIC_MAX_POINTS
+
+
+def generate_pairs_static(n, k, alpha, seed, out, num_bands=0, band_ratio=0.0, flags=0, R_override=0.0,
+                          stream=None):
+    """rhg_generate_pairs_static: the edges into `out` (a CUDA int32 tensor of at
+    least 2 words per edge) with the library's fixed device scratch instead of a
+    workspace; n <= STATIC_MAX_POINTS.  Returns the (m, 2) view of `out` and the
+    Result.  Calls on one device must not overlap in time."""
+    p = make_params(n, k, alpha, seed, num_bands, band_ratio, R_override, flags)
+    res = Result()
+    rc = load().rhg_generate_pairs_static(ctypes.byref(p), out.data_ptr(), out.numel() // 2, _stream(stream),
+                                          ctypes.byref(res))
+    _check(rc, "rhg_generate_pairs_static", res)
+    return out[: 2 * res.m].view(-1, 2), res
 
 
 def generate_pairs_host(n, k, alpha, seed, host_out, workspace: Workspace, num_bands=0, band_ratio=0.0,

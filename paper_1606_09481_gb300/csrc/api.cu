@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "kernels.h"
 
@@ -303,6 +304,30 @@ int generate(const rhg_params *p, void *d_ws, size_t ws_bytes, Output kind, uint
     return RHG_OK;
 }
 
+// Scratch of rhg_generate_pairs_static: one array per device, found by symbol.
+constexpr int kMaxDevices = 64;
+__device__ __align__(256) unsigned char g_static_scratch[RHG_STATIC_SCRATCH_BYTES];
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxDevices] = {};
+
+// The current device's scratch address; the lookup runs once per device.
+int static_scratch(void **ptr, cudaError_t *err)
+{
+    int dev = -1;
+    *err = cudaGetDevice(&dev);
+    if (*err != cudaSuccess) return RHG_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return RHG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *a = nullptr;
+        *err = cudaGetSymbolAddress(&a, g_static_scratch);
+        if (*err != cudaSuccess) return RHG_ERR_CUDA;
+        g_static_ptr[dev] = a;
+    }
+    *ptr = g_static_ptr[dev];
+    return RHG_OK;
+}
+
 }  // namespace
 }  // namespace rhg
 
@@ -483,6 +508,24 @@ int rhg_edges_from_points(const double *d_phi, const double *d_r, uint64_t n, do
     if (h.error) return error_from_meta(h.error);
     if (h.m > capacity_edges) return RHG_ERR_OVERFLOW;
     return RHG_OK;
+}
+
+int rhg_generate_pairs_static(const rhg_params *p, uint32_t *d_pairs, uint64_t capacity_edges, void *stream,
+                              rhg_result *result)
+{
+    if (result) std::memset(result, 0, sizeof(*result));
+    if (!p || p->n > RHG_STATIC_MAX_POINTS) return RHG_ERR_INVALID_ARG;
+    const size_t need = make_layout(p->n, 0).total;
+    if (need > RHG_STATIC_SCRATCH_BYTES) return RHG_ERR_INVALID_ARG;
+    void *ws = nullptr;
+    cudaError_t err = cudaSuccess;
+    const int rc = static_scratch(&ws, &err);
+    if (rc) {
+        if (result) result->cuda_error = static_cast<int32_t>(err);
+        return rc;
+    }
+    return generate(p, ws, RHG_STATIC_SCRATCH_BYTES, Output::Pairs, d_pairs, capacity_edges, nullptr, nullptr,
+                    static_cast<cudaStream_t>(stream), result);
 }
 
 int rhg_dm_eval(int fn, const double *d_in, double *d_out, uint64_t count, void *stream)
