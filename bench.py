@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--k", type=float, default=WORKLOAD["k"])
     ap.add_argument("--alpha", type=float, default=WORKLOAD["alpha"])
     ap.add_argument("--seed", type=int, default=WORKLOAD["seed"])
+    ap.add_argument("--bands", type=int, default=0, help="number of bands (0: ceil(log2 n))")
+    ap.add_argument("--band-ratio", type=float, default=0.0, help="geometric band ratio p (0: 0.9)")
     return ap.parse_args()
 
 
@@ -216,12 +218,12 @@ def run_ours(args):
     rhg.build()
     seed = args.seed + rank
     n, k, alpha = args.n, args.k, args.alpha
-    params = rhg.make_params(n, k, alpha, seed)
+    params = rhg.make_params(n, k, alpha, seed, args.bands, args.band_ratio)
     wsp = rhg.allocate_pairs(params)
     stream = torch.cuda.current_stream()
 
     def step():
-        return rhg.generate_pairs(n, k, alpha, seed, workspace=wsp)
+        return rhg.generate_pairs(n, k, alpha, seed, args.bands, args.band_ratio, workspace=wsp)
 
     pairs, res = step()
     if res.m > wsp.capacity:  # the n k / 2 estimate was short: size the output exactly
@@ -294,13 +296,13 @@ def run_ours(args):
     if not args.no_e2e:
         # end to end through the host-buffer entry point: pairs copied to pinned memory
         host = torch.empty(2 * wsp.capacity, dtype=torch.int32).pin_memory()
-        rhg.generate_pairs_host(n, k, alpha, seed, host, wsp)
+        rhg.generate_pairs_host(n, k, alpha, seed, host, wsp, args.bands, args.band_ratio)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            r2 = rhg.generate_pairs_host(n, k, alpha, seed, host, wsp)
+            r2 = rhg.generate_pairs_host(n, k, alpha, seed, host, wsp, args.bands, args.band_ratio)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
         if world > 1:

@@ -33,8 +33,8 @@ size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // Byte offsets of every buffer inside the caller's workspace.
 struct Layout {
-    size_t meta, keys0, keys1, ids0, ids1, r_by_id, akey, id, ang, pms, phi, r, ch, sh, heavy, recheck, sort_tmp,
-        csr0, csr1, total;
+    size_t meta, keys0, keys1, ids0, ids1, r_by_id, akey, id, ang, pms, phi, r, ch, sh, heavy, recheck, bidx,
+        sort_tmp, csr0, csr1, total;
     uint32_t heavy_cap, recheck_cap;
 };
 
@@ -65,6 +65,7 @@ Layout make_layout(uint64_t n, uint64_t csr_entries)
     L.sh = take(n * 8);
     L.heavy = take(static_cast<size_t>(L.heavy_cap) * 16);
     L.recheck = take(static_cast<size_t>(L.recheck_cap) * 8);
+    L.bidx = take(static_cast<size_t>(index_entries(n)) * 4);
     const size_t sort_points = radix_temp_bytes(n);
     const size_t sort_csr = csr_entries ? radix_temp_bytes(csr_entries) : 0;
     L.sort_tmp = take(sort_points > sort_csr ? sort_points : sort_csr);
@@ -224,6 +225,7 @@ Status enqueue(const Pipeline &pl, const PlanArgs &pa, const double *phi_in, con
     q.recheck = at<uint2>(pl.ws, pl.L.recheck);
     q.recheck_cap = pl.L.recheck_cap;
     q.heavy_min = heavy_min;
+    q.bidx = at<uint32_t>(pl.ws, pl.L.bidx);
     mark(RHG_STAGE_QUERY, false, stream);
     st = launch_query(q, kind == Output::Csr, stream);
     if (st.code) return st;

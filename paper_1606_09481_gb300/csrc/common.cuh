@@ -12,6 +12,10 @@
 namespace rhg {
 
 constexpr int kMaxBands = static_cast<int>(RHG_MAX_BANDS);
+// bucket index: about kBucketPoints..2 kBucketPoints points per bucket, at least
+// two buckets per band; index_entries(n) bounds the entries of all bands
+constexpr uint32_t kBucketPoints = 8;
+__host__ __device__ constexpr uint64_t index_entries(uint64_t n) { return n / kBucketPoints + 3 * kMaxBands + 1; }
 constexpr int kExpTab = 64;  // e^k table for k = -64..64 (FP32 filter values)
 
 // ---------------------------------------------------------------------------
@@ -43,6 +47,11 @@ struct Meta {
     double sinh_c[kMaxBands + 1];
     uint64_t band_start[kMaxBands + 1];  // sorted position of each band's first point
     uint32_t band_count[kMaxBands];
+    // bucket index of band i (range query search): entries idx_off[i] ..
+    // idx_off[i] + 2^(32 - idx_shift[i]); entry j = first position of the band
+    // whose angle key >> idx_shift[i] is >= j
+    uint32_t idx_off[kMaxBands + 1];
+    uint32_t idx_shift[kMaxBands];
     // FP32 window constants of band i: inner radius c_i - kDeltaR, outer c_{i+1} + kDeltaR
     float band_P[kMaxBands + 1], band_M[kMaxBands + 1], band_S[kMaxBands + 1];
     float band_PMn[kMaxBands + 1];  // P + M at the outer radius

@@ -46,6 +46,7 @@ struct QueryArgs {
     uint2 *recheck;         // uncertain pairs {owner position, candidate position}
     uint32_t recheck_cap;
     uint32_t heavy_min;     // ranges longer than this go to the heavy chunks (UINT32_MAX: never)
+    uint32_t *bidx;         // bucket index of the bands, index_entries(n) entries
 };
 
 // ---- points.cu ----

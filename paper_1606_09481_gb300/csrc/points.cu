@@ -199,11 +199,19 @@ __global__ void band_offsets_kernel(Meta *M)
 {
     if (threadIdx.x != 0) return;
     uint64_t s = 0;
+    uint32_t off = 0;
     for (uint32_t j = 0; j < M->B; ++j) {
         M->band_start[j] = s;
         s += M->band_count[j];
+        // 2^b buckets, the largest power of two <= count / kBucketPoints, b >= 1
+        uint32_t b = 1;
+        while (b < 31 && (uint64_t{2} << b) * kBucketPoints <= M->band_count[j]) ++b;
+        M->idx_off[j] = off;
+        M->idx_shift[j] = 32 - b;
+        off += (1u << b) + 1;
     }
     M->band_start[M->B] = s;
+    M->idx_off[M->B] = off;
 }
 
 // e^x in FP32 with relative error <= 4 * 2^-24 for |x| <= kExpTab + 1/2:

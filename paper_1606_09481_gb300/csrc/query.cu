@@ -33,7 +33,6 @@ constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kChunk = 4096;      // candidates per heavy chunk
 constexpr uint32_t kCoreHeavy = 4096;  // core ranges longer than this become core chunks
 constexpr uint32_t kBatchBudget = 65536;  // candidates a warp batch keeps; beyond, ranges become chunks
-constexpr uint32_t kRun = 4;              // consecutive batches a warp takes at a time
 constexpr int kListCap = 64;           // queued fringe entries per warp (>= 2 per lane)
 constexpr int kCoreCap = 32;           // queued core entries per warp (>= 1 per lane)
 constexpr int kBitWords = 128;         // decision words per warp: kChunk / 32
@@ -53,6 +52,7 @@ struct BandShared {
     float Po[kMaxBands + 1], Mo[kMaxBands + 1], So[kMaxBands + 1];   // outer radius c_{i+1} + dr
     float PMn[kMaxBands + 1];
     double c[kMaxBands + 1], sinh_c[kMaxBands + 1], cosh_c[kMaxBands + 1];
+    uint32_t ioff[kMaxBands + 1], ishift[kMaxBands + 1];  // bucket index of each band
 };
 
 __device__ __forceinline__ void load_bands(BandShared &S, const Meta *M)
@@ -69,6 +69,8 @@ __device__ __forceinline__ void load_bands(BandShared &S, const Meta *M)
         S.c[j] = M->c[j];
         S.sinh_c[j] = M->sinh_c[j];
         S.cosh_c[j] = M->cosh_c[j];
+        S.ioff[j] = M->idx_off[j];
+        S.ishift[j] = j < kMaxBands ? M->idx_shift[j] : 32u;
     }
 }
 
@@ -268,55 +270,22 @@ __device__ __forceinline__ uint32_t upper_key(const uint32_t *a, uint32_t lo, ui
     return lo;
 }
 
-// First index in [s, e) whose key is >= x (kUpper: > x), searched outward from
-// the hint h by doubling steps, then by bisection: a few nearby, mostly cached
-// loads when h is close to the answer.
-template <bool kUpper>
-__device__ __forceinline__ uint32_t gallop(const uint32_t *a, uint32_t s, uint32_t e, uint32_t h, uint32_t x)
+// Four searches in one band through its bucket index ix (shift sh): each key's
+// bucket gives the positions [ix[j], ix[j + 1]) that hold every key of that
+// bucket, and a short bisection in lock step finishes.  r0 = first key >= x0,
+// r1 = first key > x1, r2 = first key >= x2, r3 = first key > x3.
+__device__ __forceinline__ void search4_indexed(const uint32_t *a, const uint32_t *ix, uint32_t sh, uint32_t x0,
+                                                uint32_t x1, uint32_t x2, uint32_t x3, uint32_t &r0, uint32_t &r1,
+                                                uint32_t &r2, uint32_t &r3)
 {
-    auto before = [&](uint32_t i) { return kUpper ? a[i] <= x : a[i] < x; };  // answer > i
-    uint32_t lo, hi;  // the answer lies in [lo, hi]
-    if (h < s) h = s;
-    if (h < e && before(h)) {
-        lo = h + 1;
-        hi = lo;
-        uint32_t step = 1;
-        while (hi < e && before(hi)) {
-            lo = hi + 1;
-            hi = e - lo > step ? lo + step : e;
-            step <<= 1;
-        }
-    } else {
-        hi = h < e ? h : e;
-        lo = hi;
-        uint32_t step = 1;
-        while (lo > s && !before(lo - 1)) {
-            hi = lo - 1;
-            lo = hi - s > step ? hi - step : s;
-            step <<= 1;
-        }
-    }
-    while (lo < hi) {
-        const uint32_t mid = lo + ((hi - lo) >> 1);
-        if (before(mid)) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// Four independent bisections over [lo, hi) advanced in lock step (memory-level
-// parallelism): r0 = first key >= x0, r1 = first key > x1, r2 = first key >= x2,
-// r3 = first key > x3.
-__device__ __forceinline__ void search4(const uint32_t *a, uint32_t lo, uint32_t hi, uint32_t x0, uint32_t x1,
-                                        uint32_t x2, uint32_t x3, uint32_t &r0, uint32_t &r1, uint32_t &r2,
-                                        uint32_t &r3)
-{
-    uint32_t l0 = lo, h0 = hi, l1 = lo, h1 = hi, l2 = lo, h2 = hi, l3 = lo, h3 = hi;
+    const uint32_t j0 = x0 >> sh, j1 = x1 >> sh, j2 = x2 >> sh, j3 = x3 >> sh;
+    uint32_t l0 = __ldg(ix + j0), h0 = __ldg(ix + j0 + 1), l1 = __ldg(ix + j1), h1 = __ldg(ix + j1 + 1);
+    uint32_t l2 = __ldg(ix + j2), h2 = __ldg(ix + j2 + 1), l3 = __ldg(ix + j3), h3 = __ldg(ix + j3 + 1);
     while (l0 < h0 || l1 < h1 || l2 < h2 || l3 < h3) {
         const uint32_t m0 = l0 + ((h0 - l0) >> 1), m1 = l1 + ((h1 - l1) >> 1);
         const uint32_t m2 = l2 + ((h2 - l2) >> 1), m3 = l3 + ((h3 - l3) >> 1);
-        const uint32_t k0 = l0 < h0 ? a[m0] : 0u, k1 = l1 < h1 ? a[m1] : 0u;
-        const uint32_t k2 = l2 < h2 ? a[m2] : 0u, k3 = l3 < h3 ? a[m3] : 0u;
+        const uint32_t k0 = l0 < h0 ? __ldg(a + m0) : 0u, k1 = l1 < h1 ? __ldg(a + m1) : 0u;
+        const uint32_t k2 = l2 < h2 ? __ldg(a + m2) : 0u, k3 = l3 < h3 ? __ldg(a + m3) : 0u;
         if (l0 < h0) { if (k0 < x0) l0 = m0 + 1; else h0 = m0; }
         if (l1 < h1) { if (k1 <= x1) l1 = m1 + 1; else h1 = m1; }
         if (l2 < h2) { if (k2 < x2) l2 = m2 + 1; else h2 = m2; }
@@ -575,26 +544,13 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
     const uint32_t nbatch = (n + 31) / 32;
     unsigned long long cand = 0;
     uint32_t near = 0;
-    // runs of kRun consecutive batches in sorted order from a shared counter: the
-    // costly inner-band batches start first and the rest fill in around them; within
-    // a run each band's search starts from the previous batch's result
-    __shared__ uint32_t hint_sm[kWarps][kMaxBands];
-    uint32_t *hint = hint_sm[threadIdx.x >> 5];
-    uint32_t run_left = 0, batch = 0;
+    // batches in sorted order from a shared counter: the costly inner-band batches
+    // start first and the rest fill in around them
     for (;;) {
-        if (run_left == 0) {
-            uint32_t first = 0;
-            if (lane == 0)
-                first = static_cast<uint32_t>(
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&M->work_counter), static_cast<unsigned long long>(kRun)));
-            batch = __shfl_sync(full, first, 0);
-            run_left = kRun;
-            for (int j = lane; j < kMaxBands; j += 32) hint[j] = 0xffffffffu;
-            __syncwarp();
-        } else {
-            ++batch;
-        }
-        --run_left;
+        uint32_t batch = 0;
+        if (lane == 0)
+            batch = static_cast<uint32_t>(atomicAdd(reinterpret_cast<unsigned long long *>(&M->work_counter), 1ull));
+        batch = __shfl_sync(full, batch, 0);
         if (batch >= nbatch) break;
         const uint32_t p = batch * 32 + lane;
         const bool valid = p < n;
@@ -637,22 +593,13 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
                 plain = Wf < kFull && Wf <= akv && akv + Wf >= akv;
                 if (kFilter && plain) Wc = window_core(mine, S, i);
             }
-            // union of the plain windows: one warp-uniform search narrows the lanes'
-            const uint32_t kmin = __reduce_min_sync(full, plain ? akv - Wf : 0xffffffffu);
-            const uint32_t kmax = __reduce_max_sync(full, plain ? akv + Wf : 0u);
-            uint32_t U0 = s, U1 = e;
-            if (kmin <= kmax) {
-                const uint32_t h = hint[i];
-                U0 = (h >= s && h < e) ? gallop<false>(a.P.akey, s, e, h, kmin) : lower_key(a.P.akey, s, e, kmin);
-                U1 = gallop<true>(a.P.akey, U0, e, U0, kmax);
-                if (lane == 0) hint[i] = U0;
-            }
             // pieces: fringe [f0, f1), core [c0, c1), fringe [f2, f3)
             uint32_t f0 = 0, f1 = 0, f2 = 0, f3 = 0, c0 = 0, c1 = 0;
             if (active) {
                 if (plain) {
                     const uint32_t wc = Wc < 0 ? 0u : (Wc >= static_cast<int64_t>(Wf) ? Wf : static_cast<uint32_t>(Wc));
-                    search4(a.P.akey, U0, U1, akv - Wf, akv + Wf, akv - wc, akv + wc, f0, f3, c0, c1);
+                    search4_indexed(a.P.akey, a.bidx + S.ioff[i], S.ishift[i], akv - Wf, akv + Wf, akv - wc, akv + wc,
+                                    f0, f3, c0, c1);
                     if (Wc < 0) {  // no core: the fringe is the whole window
                         c0 = c1 = 0;
                         f1 = f3;
@@ -717,30 +664,43 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
             base = __shfl_sync(full, base, 0);
             if (base + total > a.capacity) continue;
             uint64_t pos = base + (incl - cnt);
-            // core edges: owner by owner, all lanes on consecutive positions
-            // (coalesced); four owners' ids are loaded before they are written
+            // core edges, four owners at a time: their ranges are concatenated and
+            // every lane loads four ids before it writes them (coalesced, with
+            // several loads in flight per lane)
             uint32_t cores = __ballot_sync(full, nc != 0);
             while (cores) {
-                uint32_t ow[4], oc[4], on[4], oi[4];
+                uint32_t oc[4], oi[4], e[4];
                 unsigned long long op[4];
+                uint32_t tot = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int o = cores ? __ffs(cores) - 1 : 0;
                     const bool has = cores != 0;
                     cores &= cores ? cores - 1 : 0u;
-                    oc[k] = __shfl_sync(full, c0, o);
-                    on[k] = has ? __shfl_sync(full, nc, o) : 0u;
+                    const uint32_t on = __shfl_sync(full, nc, o);
+                    e[k] = tot;  // start of owner k in the concatenation
+                    oc[k] = __shfl_sync(full, c0, o) - tot;
                     oi[k] = __shfl_sync(full, idv, o);
-                    op[k] = __shfl_sync(full, static_cast<unsigned long long>(pos), o);
+                    op[k] = __shfl_sync(full, static_cast<unsigned long long>(pos), o) - tot;
+                    tot += has ? on : 0u;
                 }
-                for (uint32_t t = lane; t < on[0] || t < on[1] || t < on[2] || t < on[3]; t += 32) {
+                for (uint32_t j0 = 0; j0 < tot; j0 += 128) {
+                    uint32_t w[4];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) ow[k] = t < on[k] ? a.P.id[oc[k] + t] : 0u;
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t j = j0 + lane + 32 * u;
+                        const uint32_t src = j >= e[3] ? oc[3] : j >= e[2] ? oc[2] : j >= e[1] ? oc[1] : oc[0];
+                        w[u] = j < tot ? a.P.id[src + j] : 0u;
+                    }
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (t < on[k]) {
-                            write_edge<kCsr>(a, op[k] + t, oi[k], ow[k]);
-                            if (verify) verify_pair(a, oi[k], ow[k], 1, coshR);
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t j = j0 + lane + 32 * u;
+                        if (j < tot) {
+                            const int k = j >= e[3] ? 3 : j >= e[2] ? 2 : j >= e[1] ? 1 : 0;
+                            const unsigned long long dst = k == 3 ? op[3] : k == 2 ? op[2] : k == 1 ? op[1] : op[0];
+                            const uint32_t v = k == 3 ? oi[3] : k == 2 ? oi[2] : k == 1 ? oi[1] : oi[0];
+                            write_edge<kCsr>(a, dst + j, v, w[u]);
+                            if (verify) verify_pair(a, v, w[u], 1, coshR);
                         }
                     }
                 }
@@ -876,6 +836,39 @@ __global__ void fill_u64_kernel(uint64_t *a, uint64_t count, uint64_t v)
         a[j] = v;
 }
 
+// Bucket index of every band from the sorted keys ((band << 32) | angle key):
+// position p writes the entries of the buckets from just after its predecessor's
+// bucket up to its own, and the band's last point also the entries after its
+// bucket up to the sentinel.
+__global__ void __launch_bounds__(kThreads) bucket_index_kernel(const Meta *M, const uint64_t *keys, uint64_t n,
+                                                                 uint32_t *idx, uint64_t cap)
+{
+    if (M->error) return;  // an earlier stage failed: the keys may be undefined
+    const uint32_t B = M->B;
+    for (uint64_t p = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t key = keys[p];
+        const uint32_t b = static_cast<uint32_t>(key >> 32);
+        if (b >= B) {  // cannot happen: every key carries its band
+            atomicExch(&const_cast<Meta *>(M)->error, kErrInternal);
+            return;
+        }
+        const uint32_t sh = M->idx_shift[b], off = M->idx_off[b];
+        const uint64_t s = M->band_start[b], e = M->band_start[b + 1];
+        const uint32_t cur = static_cast<uint32_t>(key) >> sh;
+        const uint32_t first = p == s ? 0u : (static_cast<uint32_t>(keys[p - 1]) >> sh) + 1;
+        if (off + (1ull << (32 - sh)) >= cap) {  // cannot happen: the offsets are bounded by index_entries(n)
+            atomicExch(&const_cast<Meta *>(M)->error, kErrInternal);
+            return;
+        }
+        for (uint32_t j = first; j <= cur; ++j) idx[off + j] = static_cast<uint32_t>(p);
+        if (p + 1 == e) {
+            const uint32_t nb = 1u << (32 - sh);
+            for (uint32_t j = cur + 1; j <= nb; ++j) idx[off + j] = static_cast<uint32_t>(e);
+        }
+    }
+}
+
 template <typename K>
 int resident_ctas(K kernel)
 {
@@ -909,7 +902,15 @@ Status run(const QueryArgs &a, cudaStream_t stream)
 
 Status launch_query(const QueryArgs &a, bool csr, cudaStream_t stream)
 {
-    Status st = csr ? run<true, true>(a, stream) : run<true, false>(a, stream);
+    Status st;
+    if (a.P.n) {
+        const uint64_t g = ceil_div(a.P.n, kThreads);
+        const uint64_t cap = static_cast<uint64_t>(num_sms()) * 8;
+        bucket_index_kernel<<<static_cast<unsigned>(g < cap ? g : cap), kThreads, 0, stream>>>(a.M, a.P.key, a.P.n,
+                                                                                                a.bidx, index_entries(a.P.n));
+        RHG_LAUNCH_CHECK();
+    }
+    st = csr ? run<true, true>(a, stream) : run<true, false>(a, stream);
     if (st.code) return st;
     return csr ? run<false, true>(a, stream) : run<false, false>(a, stream);
 }
