@@ -4,11 +4,14 @@
 //
 // One pass per 8-bit digit:
 //   upsweep   each CTA histograms the digit over its contiguous chunk;
-//   scan      one CTA turns the digit-major [digit][cta] counts into offsets;
+//   scan      one CTA per digit turns its row of the digit-major [digit][cta]
+//             counts into an exclusive prefix and a digit total (the downsweep
+//             adds the exclusive scan of the totals);
 //   downsweep each CTA walks its chunk tile by tile; inside a tile every warp
 //             ranks its 32 x kItems keys with __match_any_sync, warps are combined
 //             by a per-digit prefix over warps, so the order of equal digits is the
-//             input order (stable), and keys are scattered to their offsets.
+//             input order (stable); the tile is staged in shared memory in digit
+//             order and written out from there, one contiguous run per digit.
 #include "kernels.h"
 
 namespace rhg {
@@ -48,43 +51,66 @@ __global__ void __launch_bounds__(kThreads) upsweep_kernel(const uint64_t *keys,
     counts[static_cast<uint64_t>(threadIdx.x) * gridDim.x + blockIdx.x] = hist[threadIdx.x];
 }
 
-// exclusive scan over total = kRadix * ctas counts, in place; one CTA of 1024 threads
-__global__ void __launch_bounds__(1024) scan_counts_kernel(uint32_t *counts, uint32_t total)
+// Row d of the digit-major counts (the CTAs' counts of digit d) becomes its
+// exclusive prefix, in place, and totals[d] its sum; one CTA per digit.
+__global__ void __launch_bounds__(kThreads) scan_rows_kernel(uint32_t *counts, uint32_t ctas, uint32_t *totals)
 {
-    __shared__ uint32_t part[1024];
-    const uint32_t per = (total + 1023) / 1024;
-    const uint32_t b = threadIdx.x * per;
-    uint32_t e = b + per;
-    if (e > total) e = total;
-    uint32_t s = 0;
-    for (uint32_t i = b; i < e; ++i) s += counts[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const uint32_t v = threadIdx.x >= static_cast<unsigned>(off) ? part[threadIdx.x - off] : 0u;
+    __shared__ uint32_t warp_sum[kWarps];
+    uint32_t *row = counts + static_cast<uint64_t>(blockIdx.x) * ctas;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < ctas; base += kThreads) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < ctas ? row[i] : 0u;
+        uint32_t incl = v;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
         __syncthreads();
-        part[threadIdx.x] += v;
+        uint32_t before = carry;
+        for (int w = 0; w < warp; ++w) before += warp_sum[w];
+        uint32_t chunk = 0;
+        for (int w = 0; w < kWarps; ++w) chunk += warp_sum[w];
+        if (i < ctas) row[i] = before + incl - v;
+        carry += chunk;
         __syncthreads();
     }
-    uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-    for (uint32_t i = b; i < e; ++i) {
-        const uint32_t c = counts[i];
-        counts[i] = run;
-        run += c;
-    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
 template <bool kValues>
 __global__ void __launch_bounds__(kThreads) downsweep_kernel(const uint64_t *keys_in, uint64_t *keys_out,
                                                              const uint32_t *vals_in, uint32_t *vals_out,
                                                              uint64_t n, int shift, uint64_t tiles_per_cta,
-                                                             const uint32_t *offsets)
+                                                             const uint32_t *offsets, const uint32_t *totals)
 {
     __shared__ uint32_t digit_base[kRadix];
     __shared__ uint32_t warp_count[kWarps][kRadix];
+    __shared__ uint32_t tile_start[kRadix];
+    __shared__ uint32_t warp_sum[kWarps];
+    __shared__ uint64_t skey[kTile];
+    __shared__ uint32_t sval[kValues ? kTile : 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
-    digit_base[threadIdx.x] = offsets[static_cast<uint64_t>(threadIdx.x) * gridDim.x + blockIdx.x];
+    {
+        // this CTA's first position of digit d: keys of smaller digits (exclusive
+        // scan of the digit totals) plus keys of digit d in earlier CTAs
+        const uint32_t t = totals[threadIdx.x];
+        uint32_t incl = t;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += warp_sum[w];
+        digit_base[threadIdx.x] =
+            before + incl - t + offsets[static_cast<uint64_t>(threadIdx.x) * gridDim.x + blockIdx.x];
+        __syncthreads();
+    }
     const uint64_t chunk = blockIdx.x * tiles_per_cta * kTile;
     for (uint64_t t = 0; t < tiles_per_cta; ++t) {
         const uint64_t tile = chunk + t * kTile;
@@ -116,28 +142,49 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const uint64_t *key
             __syncwarp();
         }
         __syncthreads();
-        // per digit: exclusive prefix over warps, then the tile total
-        {
-            const int d = threadIdx.x;
-            uint32_t run = 0;
+        // per digit: exclusive prefix over warps and the tile total; the digits'
+        // starts in the tile are the exclusive scan of the totals
+        const int d = threadIdx.x;
+        uint32_t run = 0;
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const uint32_t c = warp_count[w][d];
-                warp_count[w][d] = run;
-                run += c;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < kItems; ++i) {
-                if (rank[i] != 0xffffffffu) {
-                    const uint32_t pos = digit_base[digit[i]] + warp_count[warp][digit[i]] + rank[i];
-                    keys_out[pos] = key[i];
-                    if (kValues) vals_out[pos] = val[i];
-                }
-            }
-            __syncthreads();
-            digit_base[d] += run;
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = warp_count[w][d];
+            warp_count[w][d] = run;
+            run += c;
         }
+        uint32_t incl = run;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += warp_sum[w];
+        tile_start[d] = before + incl - run;
+        __syncthreads();
+        // the tile in digit order (stable) in shared memory ...
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            if (rank[i] != 0xffffffffu) {
+                const uint32_t local = tile_start[digit[i]] + warp_count[warp][digit[i]] + rank[i];
+                skey[local] = key[i];
+                if (kValues) sval[local] = val[i];
+            }
+        }
+        __syncthreads();
+        // ... then written out in that order: each digit's keys land on consecutive
+        // positions, so neighbouring threads write neighbouring addresses
+        const uint32_t cnt = n - tile < static_cast<uint64_t>(kTile) ? static_cast<uint32_t>(n - tile) : kTile;
+        for (uint32_t j = threadIdx.x; j < cnt; j += kThreads) {
+            const uint64_t k = skey[j];
+            const int dg = static_cast<int>((k >> shift) & (kRadix - 1));
+            const uint32_t pos = digit_base[dg] + (j - tile_start[dg]);
+            keys_out[pos] = k;
+            if (kValues) vals_out[pos] = sval[j];
+        }
+        __syncthreads();
+        digit_base[d] += run;
         __syncthreads();
     }
 }
@@ -147,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const uint64_t *key
 size_t radix_temp_bytes(uint64_t n)
 {
     const Grid g = sort_grid(n);
-    return static_cast<size_t>(kRadix) * g.ctas * sizeof(uint32_t);
+    return static_cast<size_t>(kRadix) * (g.ctas + 1) * sizeof(uint32_t);
 }
 
 Status radix_sort(uint64_t n, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
@@ -160,17 +207,18 @@ Status radix_sort(uint64_t n, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals
     if (n > 1) {
         const Grid g = sort_grid(n);
         uint32_t *counts = static_cast<uint32_t *>(temp);
+        uint32_t *totals = counts + static_cast<size_t>(kRadix) * g.ctas;
         for (int s = 0; s < num_shifts; ++s) {
             upsweep_kernel<<<g.ctas, kThreads, 0, stream>>>(kin, n, shifts[s], g.tiles_per_cta, counts);
             RHG_LAUNCH_CHECK();
-            scan_counts_kernel<<<1, 1024, 0, stream>>>(counts, kRadix * g.ctas);
+            scan_rows_kernel<<<kRadix, kThreads, 0, stream>>>(counts, g.ctas, totals);
             RHG_LAUNCH_CHECK();
             if (vals) {
                 downsweep_kernel<true><<<g.ctas, kThreads, 0, stream>>>(kin, kout, vin, vout, n, shifts[s],
-                                                                       g.tiles_per_cta, counts);
+                                                                       g.tiles_per_cta, counts, totals);
             } else {
                 downsweep_kernel<false><<<g.ctas, kThreads, 0, stream>>>(kin, kout, nullptr, nullptr, n,
-                                                                        shifts[s], g.tiles_per_cta, counts);
+                                                                        shifts[s], g.tiles_per_cta, counts, totals);
             }
             RHG_LAUNCH_CHECK();
             uint64_t *tk = kin;
