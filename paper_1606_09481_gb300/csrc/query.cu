@@ -339,13 +339,11 @@ template <bool kCsr>
 __device__ __forceinline__ void write_edge(const QueryArgs &a, uint64_t pos, uint32_t i1, uint32_t i2)
 {
     const uint32_t u = i1 < i2 ? i1 : i2, v = i1 < i2 ? i2 : i1;
-    // streaming (evict-first) stores: the output must not push the point arrays,
-    // which every warp re-reads, out of L2
     if (kCsr) {
-        __stcs(reinterpret_cast<unsigned long long *>(a.csr_keys + 2 * pos), (static_cast<unsigned long long>(u) << 32) | v);
-        __stcs(reinterpret_cast<unsigned long long *>(a.csr_keys + 2 * pos + 1), (static_cast<unsigned long long>(v) << 32) | u);
+        a.csr_keys[2 * pos] = (static_cast<uint64_t>(u) << 32) | v;
+        a.csr_keys[2 * pos + 1] = (static_cast<uint64_t>(v) << 32) | u;
     } else {
-        __stcs(reinterpret_cast<uint2 *>(a.pairs) + pos, make_uint2(u, v));
+        reinterpret_cast<uint2 *>(a.pairs)[pos] = make_uint2(u, v);
     }
 }
 
@@ -542,6 +540,8 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
     const bool verify = M->verify != 0;
     const int lane = threadIdx.x & 31;
     const uint32_t nbatch = (n + 31) / 32;
+    __shared__ uint8_t own_sm[kWarps][32];
+    uint8_t *own = own_sm[threadIdx.x >> 5];
     unsigned long long cand = 0;
     uint32_t near = 0;
     // batches in sorted order from a shared counter: the costly inner-band batches
@@ -649,63 +649,50 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
                 const int dec = decide_own<kFilter>(a, va, vb, mine, phv, p, idv, q, in, coshR, verify, near);
                 if (dec == 1) mask |= 1ull << t;
             }
-            // one reservation for the warp's core and fringe edges of this band
-            const uint32_t cnt = nc + static_cast<uint32_t>(__popcll(mask));
-            uint32_t incl = cnt;
+            // one reservation for the warp's edges of this band: [base, base + T)
+            // holds the core edges of lanes 0..31 in lane order, then come the
+            // fringe edges
+            const uint32_t nfe = static_cast<uint32_t>(__popcll(mask));
+            uint32_t ci = nc, fi = nfe;  // inclusive scans over the lanes
             for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t y = __shfl_up_sync(full, incl, off);
-                if (lane >= off) incl += y;
+                const uint32_t y = __shfl_up_sync(full, ci, off), z = __shfl_up_sync(full, fi, off);
+                if (lane >= off) {
+                    ci += y;
+                    fi += z;
+                }
             }
-            const uint32_t total = __shfl_sync(full, incl, 31);
+            const uint32_t T = __shfl_sync(full, ci, 31);
+            const uint32_t total = T + __shfl_sync(full, fi, 31);
             kept += total;
             if (total == 0) continue;
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(&M->m), total);
             base = __shfl_sync(full, base, 0);
             if (base + total > a.capacity) continue;
-            uint64_t pos = base + (incl - cnt);
-            // core edges, four owners at a time: their ranges are concatenated and
-            // every lane loads four ids before it writes them (coalesced, with
-            // several loads in flight per lane)
-            uint32_t cores = __ballot_sync(full, nc != 0);
-            while (cores) {
-                uint32_t oc[4], oi[4], e[4];
-                unsigned long long op[4];
-                uint32_t tot = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int o = cores ? __ffs(cores) - 1 : 0;
-                    const bool has = cores != 0;
-                    cores &= cores ? cores - 1 : 0u;
-                    const uint32_t on = __shfl_sync(full, nc, o);
-                    e[k] = tot;  // start of owner k in the concatenation
-                    oc[k] = __shfl_sync(full, c0, o) - tot;
-                    oi[k] = __shfl_sync(full, idv, o);
-                    op[k] = __shfl_sync(full, static_cast<unsigned long long>(pos), o) - tot;
-                    tot += has ? on : 0u;
+            // core edges: element j of the concatenation goes to base + j (coalesced);
+            // its owner is the lane whose segment starts last at or before j: the
+            // segment starts inside each 32-element window are one OR-reduction and
+            // a table of which lane starts where
+            const uint32_t start = ci - nc, delta = c0 - start;  // source position = j + delta
+            uint32_t L = 0;
+            for (uint32_t j0 = 0; j0 < T; j0 += 32) {
+                const bool starts = nc != 0 && start >= j0 && start - j0 < 32;
+                if (starts) own[start - j0] = static_cast<uint8_t>(lane);
+                const uint32_t bits = __reduce_or_sync(full, starts ? 1u << (start - j0) : 0u);
+                __syncwarp();
+                const uint32_t upto = bits & (0xffffffffu >> (31 - lane));  // starts at offsets <= lane
+                if (upto) L = own[31 - __clz(upto)];
+                const uint32_t dl = __shfl_sync(full, delta, L), u = __shfl_sync(full, idv, L);
+                const uint32_t j = j0 + lane;
+                if (j < T) {
+                    const uint32_t w = __ldg(a.P.id + (j + dl));
+                    write_edge<kCsr>(a, base + j, u, w);
+                    if (verify) verify_pair(a, u, w, 1, coshR);
                 }
-                for (uint32_t j0 = 0; j0 < tot; j0 += 128) {
-                    uint32_t w[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint32_t j = j0 + lane + 32 * u;
-                        const uint32_t src = j >= e[3] ? oc[3] : j >= e[2] ? oc[2] : j >= e[1] ? oc[1] : oc[0];
-                        w[u] = j < tot ? a.P.id[src + j] : 0u;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint32_t j = j0 + lane + 32 * u;
-                        if (j < tot) {
-                            const int k = j >= e[3] ? 3 : j >= e[2] ? 2 : j >= e[1] ? 1 : 0;
-                            const unsigned long long dst = k == 3 ? op[3] : k == 2 ? op[2] : k == 1 ? op[1] : op[0];
-                            const uint32_t v = k == 3 ? oi[3] : k == 2 ? oi[2] : k == 1 ? oi[1] : oi[0];
-                            write_edge<kCsr>(a, dst + j, v, w[u]);
-                            if (verify) verify_pair(a, v, w[u], 1, coshR);
-                        }
-                    }
-                }
+                L = __shfl_sync(full, L, 31);  // owner of the window's last element
+                __syncwarp();
             }
-            pos += nc;
+            uint64_t pos = base + T + (fi - nfe);
             while (mask) {
                 const uint32_t t = static_cast<uint32_t>(__ffsll(static_cast<long long>(mask)) - 1);
                 mask &= mask - 1;
