@@ -78,7 +78,7 @@ def measured_peaks():
 def kernel_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source
     has not changed since it was taken (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     with open(path) as f:
@@ -204,6 +204,26 @@ def run_reference(args):
     return 0
 
 
+def replica_seed(seed: int, rank: int) -> int:
+    """Replicas (one per GPU, no exchange) generate independent graphs: rank r
+    uses seed + r."""
+    return seed + rank
+
+
+def combine_ranks(elapsed_ms: float, edges: int, world: int, device: str):
+    """Whole-job figures over the replicas: the slowest rank's time (MAX) and the
+    edges of all ranks (SUM).  A no-op at world size 1."""
+    if world <= 1:
+        return elapsed_ms, edges
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    mm = torch.tensor([edges], dtype=torch.int64, device=device)
+    dist.all_reduce(mm)
+    return float(t.item()), int(mm.item())
+
+
 def run_ours(args):
     import torch
 
@@ -216,7 +236,7 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     rhg.build()
-    seed = args.seed + rank
+    seed = replica_seed(args.seed, rank)
     n, k, alpha = args.n, args.k, args.alpha
     params = rhg.make_params(n, k, alpha, seed, args.bands, args.band_ratio)
     wsp = rhg.allocate_pairs(params)
@@ -257,14 +277,7 @@ def run_ours(args):
     launches = rhg.launch_count() - launches0
     elapsed_ms = ev0.elapsed_time(ev1)
     m = int(res.m)
-    total_m = m
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-        mm = torch.tensor([m], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(mm)
-        total_m = int(mm.item())
+    elapsed_ms, total_m = combine_ranks(elapsed_ms, m, world, "cuda")
     ms_per_step = elapsed_ms / args.steps
     value = total_m / (ms_per_step / 1000.0)
 
@@ -305,10 +318,7 @@ def run_ours(args):
             r2 = rhg.generate_pairs_host(n, k, alpha, seed, host, wsp, args.bands, args.band_ratio)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s, _ = combine_ranks(e2e_s, 0, world, "cuda")
         line["e2e"] = {"value": total_m / e2e_s, "unit": "edges/s", "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": int(r2.m) * 8 + 2 * rhg.plan_workspace_bytes(),
                        "ms_per_step": 1000 * e2e_s,
