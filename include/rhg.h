@@ -224,6 +224,49 @@ int rhg_edges_from_points(const double *d_phi, const double *d_r, uint64_t n, do
                           uint64_t capacity_edges, void *stream, rhg_result *result);
 
 /*
+ * Batches of independent graphs (the batched workload: thousands of small graphs
+ * of uneven size generated together).  Each graph is exactly the graph that
+ * rhg_generate_pairs gives for the same rhg_params (same R, points, bands and
+ * edge set); only the work is shared: one launch of each stage covers every
+ * graph (sampling, a sort segmented by graph, gather, range query).
+ *
+ * rhg_batch_workspace_bytes -- workspace bytes rhg_generate_batch needs for
+ * these `count` graphs (it depends on the n of each graph, not on the output).
+ *
+ * rhg_generate_batch -- graphs[g] (n >= 2, k, alpha, seed, num_bands, band_ratio,
+ * R_override, flags as in rhg_params) for g < count.  Graph g writes its pairs
+ * (u < v, vertex ids 0 .. n_g - 1 of that graph, order unspecified) to
+ * d_pairs[2 pair_offsets[g] ..], with room for pair_offsets[g + 1] -
+ * pair_offsets[g] pairs; pair_offsets is a host array of count + 1
+ * non-decreasing entries and d_pairs holds pair_offsets[count] pairs (8-byte
+ * aligned).  results (host, count entries) receives each graph's exact edge
+ * count, R, band count, mode (1 = FP32 filter + FP64 recheck) and status:
+ * RHG_ERR_OVERFLOW when its edges exceed its room (call again with room for
+ * results[g].m), RHG_ERR_NO_SOLUTION when its k cannot be reached, else RHG_OK.
+ * totals (optional) receives the sum of the edges of the graphs with status
+ * RHG_OK and the batch-wide counters.  Returns RHG_OK when every graph
+ * succeeded, else the status of the first graph that did not; argument errors
+ * (including one invalid graph) return RHG_ERR_INVALID_ARG before any launch.
+ * Limits: count <= 2^20 graphs and fewer than 2^32 points in all.  The tables
+ * of the batch are copied from pageable host memory, and the call synchronises
+ * the stream once at the end (twice when a list overflowed in filter mode and
+ * the batch reran in FP64 mode).
+ */
+typedef struct {
+    uint64_t m;           /* edges of the graph (exact, also on overflow)        */
+    double R;             /* disk radius                                          */
+    uint32_t num_bands;
+    int32_t status;       /* RHG_OK, RHG_ERR_OVERFLOW, RHG_ERR_NO_SOLUTION, ...   */
+    uint32_t mode;        /* 1: FP32 filter + FP64 recheck; 0: FP64 predicate     */
+    uint32_t reserved;
+} rhg_batch_graph;
+
+int rhg_batch_workspace_bytes(const rhg_params *graphs, uint32_t count, size_t *bytes);
+int rhg_generate_batch(const rhg_params *graphs, uint32_t count, void *d_workspace,
+                       size_t workspace_bytes, uint32_t *d_pairs, const uint64_t *pair_offsets,
+                       void *stream, rhg_batch_graph *results, rhg_result *totals);
+
+/*
  * rhg_dm_eval -- the library's deterministic FP64 functions on a device array,
  * for verification against an independent implementation: fn = 0 exp, 1 log,
  * 2 cos, 3 cosh, 4 sinh.  d_out[i] = f(d_in[i]), i < count.

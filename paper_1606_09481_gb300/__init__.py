@@ -45,6 +45,12 @@ class Result(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class BatchGraph(ctypes.Structure):
+    """rhg_batch_graph: one graph's outcome in rhg_generate_batch."""
+    _fields_ = [("m", _c_u64), ("R", _c_dbl), ("num_bands", _c_u32), ("status", ctypes.c_int32),
+                ("mode", _c_u32), ("reserved", _c_u32)]
+
+
 class RhgError(RuntimeError):
     def __init__(self, status: int, where: str, result: Result | None = None):
         self.status = status
@@ -77,6 +83,9 @@ def load() -> ctypes.CDLL:
     L.rhg_generate_pairs.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _c_u64, _p,
                                      ctypes.POINTER(Result)]
     L.rhg_generate_pairs_static.argtypes = [ctypes.POINTER(Params), _p, _c_u64, _p, ctypes.POINTER(Result)]
+    L.rhg_batch_workspace_bytes.argtypes = [ctypes.POINTER(Params), _c_u32, ctypes.POINTER(_c_size)]
+    L.rhg_generate_batch.argtypes = [ctypes.POINTER(Params), _c_u32, _p, _c_size, _p, ctypes.POINTER(_c_u64), _p,
+                                     ctypes.POINTER(BatchGraph), ctypes.POINTER(Result)]
     L.rhg_generate_pairs_host.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _c_u64, _p, _c_u64, _p,
                                           ctypes.POINTER(Result)]
     L.rhg_generate_csr.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _p, _c_u64, _p,
@@ -253,6 +262,68 @@ def generate_pairs(n, k, alpha, seed, num_bands=0, band_ratio=0.0, flags=0, R_ov
                                   wsp.capacity, _stream(stream), ctypes.byref(res))
     _check(rc, "rhg_generate_pairs", res)
     return wsp.out[: 2 * res.m].view(-1, 2), res
+
+
+def batch_params(specs, flags=0, num_bands=0, band_ratio=0.0):
+    """A ctypes array of Params from (n, k, alpha, seed) tuples (or Params)."""
+    ps = [sp if isinstance(sp, Params) else make_params(sp[0], sp[1], sp[2], sp[3], num_bands, band_ratio, 0.0, flags)
+          for sp in specs]
+    return (Params * len(ps))(*ps)
+
+
+def batch_workspace_bytes(params_array) -> int:
+    b = _c_size(0)
+    _check(load().rhg_batch_workspace_bytes(params_array, len(params_array), ctypes.byref(b)),
+           "rhg_batch_workspace_bytes")
+    return int(b.value)
+
+
+@dataclass
+class BatchBuffers:
+    """Device buffers of a batch: workspace, pairs, and the host pair offsets."""
+    params: object
+    ws: object
+    out: object
+    offsets: object  # ctypes uint64 array, count + 1
+
+
+def allocate_batch(params_array, capacities=None) -> BatchBuffers:
+    torch = _torch()
+    caps = capacities or [estimate_capacity(p.n, p.k or 8.0) for p in params_array]
+    offs = (_c_u64 * (len(caps) + 1))()
+    for g, c in enumerate(caps):
+        offs[g + 1] = offs[g] + int(c)
+    ws = _empty_bytes(batch_workspace_bytes(params_array))
+    out = torch.empty(max(2 * int(offs[len(caps)]), 2), dtype=torch.int32, device="cuda")
+    return BatchBuffers(params_array, ws, out, offs)
+
+
+def run_batch(buf: BatchBuffers, stream=None):
+    """One rhg_generate_batch call on prepared buffers: (status, [BatchGraph], totals)."""
+    G = len(buf.params)
+    res = (BatchGraph * G)()
+    tot = Result()
+    rc = load().rhg_generate_batch(buf.params, G, buf.ws.data_ptr(), buf.ws.numel(), buf.out.data_ptr(),
+                                   buf.offsets, _stream(stream), res, ctypes.byref(tot))
+    return rc, res, tot
+
+
+def generate_batch(specs, flags=0, num_bands=0, band_ratio=0.0, stream=None):
+    """Graphs from (n, k, alpha, seed) tuples in one rhg_generate_batch call.
+
+    Returns ([(m_g, 2) int32 CUDA views], [BatchGraph], totals Result).  Graphs
+    that overflowed their estimated room are generated again with exact room."""
+    params = batch_params(specs, flags, num_bands, band_ratio)
+    buf = allocate_batch(params)
+    rc, res, tot = run_batch(buf, stream)
+    if rc == OVERFLOW:
+        caps = [max(int(res[g].m), int(buf.offsets[g + 1] - buf.offsets[g])) for g in range(len(params))]
+        buf = allocate_batch(params, caps)
+        rc, res, tot = run_batch(buf, stream)
+    if rc != OK:
+        raise RhgError(rc, "rhg_generate_batch", tot)
+    views = [buf.out[2 * buf.offsets[g]: 2 * (buf.offsets[g] + res[g].m)].view(-1, 2) for g in range(len(params))]
+    return views, list(res), tot
 
 
 STATIC_MAX_POINTS = 131072  # RHG_STATIC_MAX_POINTS

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "kernels.h"
 
@@ -306,6 +307,211 @@ int generate(const rhg_params *p, void *d_ws, size_t ws_bytes, Output kind, uint
     return RHG_OK;
 }
 
+// ------------------------------------------------------------------ batch
+constexpr uint32_t kMaxBatch = 1u << 20;
+
+// Host-side tables of a batch (uploaded once per call).
+struct BatchHost {
+    uint32_t G = 0;
+    uint64_t N = 0;          // points of all graphs
+    uint64_t idx_total = 0;  // bucket-index entries of all graphs
+    std::vector<PlanArgs> args;
+    std::vector<uint4> tiles;
+    std::vector<uint32_t> tile_first, pt_off, idx_base;
+    std::vector<uint64_t> out_off;
+};
+
+struct BatchLayout {
+    size_t metas, args, tiles, tile_first, pt_off, idx_base, out_off, tables_end, results, keys0, keys1, ids0, ids1,
+        r_by_pos, akey, id, ang, pms, phi, r, ch, sh, bidx, heavy, recheck, sort_tmp, total;
+    uint32_t heavy_cap, recheck_cap;
+};
+
+int batch_host(const rhg_params *graphs, uint32_t count, const uint64_t *pair_offsets, BatchHost &h)
+{
+    if (!graphs || count == 0 || count > kMaxBatch) return RHG_ERR_INVALID_ARG;
+    h.G = count;
+    h.args.resize(count);
+    h.tile_first.assign(count + 1, 0);
+    h.pt_off.assign(count + 1, 0);
+    h.idx_base.assign(count + 1, 0);
+    h.out_off.assign(count + 1, 0);
+    h.tiles.clear();
+    uint64_t pos = 0, idx = 0;
+    for (uint32_t g = 0; g < count; ++g) {
+        const rhg_params &q = graphs[g];
+        uint32_t B;
+        double ratio;
+        const int rc = check_params(&q, &B, &ratio);
+        if (rc) return rc;
+        h.args[g] = PlanArgs{q.n, q.k, q.alpha, q.seed, B, ratio, q.R_override,
+                             (q.flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u, (q.flags & RHG_FLAG_VERIFY) ? 1u : 0u};
+        h.tile_first[g] = static_cast<uint32_t>(h.tiles.size());
+        for (uint64_t s0 = 0; s0 < q.n; s0 += kTilePoints) {
+            const uint64_t c = q.n - s0 < kTilePoints ? q.n - s0 : kTilePoints;
+            h.tiles.push_back(make_uint4(g, static_cast<uint32_t>(pos + s0), static_cast<uint32_t>(c), 0u));
+        }
+        pos += q.n;
+        idx += index_entries(q.n);
+        if (pos >= 0xFFFFFFFFull || idx >= 0xFFFFFFFFull) return RHG_ERR_INVALID_ARG;  // 32-bit positions
+        h.pt_off[g + 1] = static_cast<uint32_t>(pos);
+        h.idx_base[g + 1] = static_cast<uint32_t>(idx);
+    }
+    h.tile_first[count] = static_cast<uint32_t>(h.tiles.size());
+    h.N = pos;
+    h.idx_total = idx;
+    if (pair_offsets) {
+        for (uint32_t g = 0; g <= count; ++g) {
+            if (g && pair_offsets[g] < pair_offsets[g - 1]) return RHG_ERR_INVALID_ARG;
+            h.out_off[g] = pair_offsets[g];
+        }
+    }
+    return RHG_OK;
+}
+
+BatchLayout batch_layout(const BatchHost &h)
+{
+    BatchLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    const uint64_t N = h.N, G = h.G;
+    L.heavy_cap = static_cast<uint32_t>(N / 4 + 65536);
+    L.recheck_cap = static_cast<uint32_t>(N / 2 + 65536);
+    L.metas = take((G + 1) * sizeof(Meta));
+    // the tables are one contiguous upload
+    L.args = o;
+    o += G * sizeof(PlanArgs);
+    o = (o + 15) & ~size_t{15};
+    L.tiles = o;
+    o += h.tiles.size() * sizeof(uint4);
+    L.tile_first = o;
+    o += (G + 1) * 4;
+    L.pt_off = o;
+    o += (G + 1) * 4;
+    L.idx_base = o;
+    o += (G + 1) * 4;
+    o = (o + 7) & ~size_t{7};
+    L.out_off = o;
+    o += (G + 1) * 8;
+    L.tables_end = o;
+    o = align_up(o);
+    L.results = take(2 * G * sizeof(uint4));
+    L.keys0 = take(N * 8);
+    L.keys1 = take(N * 8);
+    L.ids0 = take(N * 4);
+    L.ids1 = take(N * 4);
+    L.r_by_pos = take(N * 8);
+    L.akey = take(N * 4);
+    L.id = take(N * 4);
+    L.ang = take(N * 8);
+    L.pms = take(N * 16);
+    L.phi = take(N * 8);
+    L.r = take(N * 8);
+    L.ch = take(N * 8);
+    L.sh = take(N * 8);
+    L.bidx = take(h.idx_total * 4);
+    L.heavy = take(static_cast<size_t>(L.heavy_cap) * 16);
+    L.recheck = take(static_cast<size_t>(L.recheck_cap) * 8);
+    L.sort_tmp = take(segmented_temp_bytes(static_cast<uint32_t>(h.tiles.size())));
+    L.total = o;
+    return L;
+}
+
+// Copies the tables into the workspace (pageable source: returns when copied).
+Status upload_tables(void *ws, const BatchLayout &L, const BatchHost &h, cudaStream_t stream)
+{
+    Status st;
+    std::vector<unsigned char> buf(L.tables_end - L.args, 0);
+    auto put = [&](size_t off, const void *src, size_t bytes) {
+        if (bytes) std::memcpy(buf.data() + (off - L.args), src, bytes);
+    };
+    put(L.args, h.args.data(), h.args.size() * sizeof(PlanArgs));
+    put(L.tiles, h.tiles.data(), h.tiles.size() * sizeof(uint4));
+    put(L.tile_first, h.tile_first.data(), h.tile_first.size() * 4);
+    put(L.pt_off, h.pt_off.data(), h.pt_off.size() * 4);
+    put(L.idx_base, h.idx_base.data(), h.idx_base.size() * 4);
+    put(L.out_off, h.out_off.data(), h.out_off.size() * 8);
+    RHG_CUDA_TRY(cudaMemcpyAsync(at<char>(ws, L.args), buf.data(), buf.size(), cudaMemcpyHostToDevice, stream));
+    RHG_CUDA_TRY(cudaStreamSynchronize(stream));
+    return st;
+}
+
+BatchTables batch_tables(void *ws, const BatchLayout &L, const BatchHost &h)
+{
+    BatchTables bt;
+    bt.G = h.G;
+    bt.num_tiles = static_cast<uint32_t>(h.tiles.size());
+    bt.tiles = at<uint4>(ws, L.tiles);
+    bt.tile_first = at<uint32_t>(ws, L.tile_first);
+    bt.pt_off = at<uint32_t>(ws, L.pt_off);
+    bt.idx_base = at<uint32_t>(ws, L.idx_base);
+    bt.out_off = at<uint64_t>(ws, L.out_off);
+    return bt;
+}
+
+// Every stage of the batch on the stream: plan (all graphs), sample, band
+// offsets, segmented sort, gather, bucket index and range query, results.
+Status enqueue_batch(void *ws, const BatchLayout &L, const BatchHost &h, uint32_t *d_pairs, cudaStream_t stream)
+{
+    Status st;
+    Meta *metas = at<Meta>(ws, L.metas);
+    const BatchTables bt = batch_tables(ws, L, h);
+    mark(RHG_STAGE_PLAN, false, stream);
+    st = launch_plan_batch(metas, at<PlanArgs>(ws, L.args), h.G, stream);
+    if (st.code) return st;
+    mark(RHG_STAGE_PLAN, true, stream);
+    uint64_t *k0 = at<uint64_t>(ws, L.keys0), *k1 = at<uint64_t>(ws, L.keys1);
+    uint32_t *i0 = at<uint32_t>(ws, L.ids0), *i1 = at<uint32_t>(ws, L.ids1);
+    double *rpos = at<double>(ws, L.r_by_pos);
+    mark(RHG_STAGE_SAMPLE, false, stream);
+    st = launch_sample_batch(metas, bt, k0, i0, rpos, stream);
+    if (st.code) return st;
+    mark(RHG_STAGE_SAMPLE, true, stream);
+    mark(RHG_STAGE_SORT, false, stream);
+    st = launch_band_offsets_batch(metas, bt, stream);
+    if (st.code) return st;
+    const int shifts[5] = {0, 8, 16, 24, 32};
+    uint64_t *ks = nullptr;
+    uint32_t *is = nullptr;
+    st = segmented_radix_sort(bt, k0, k1, i0, i1, shifts, 5, at<void>(ws, L.sort_tmp), &ks, &is, stream);
+    if (st.code) return st;
+    mark(RHG_STAGE_SORT, true, stream);
+    SortedPoints P;
+    P.n = h.N;
+    P.key = ks;
+    P.akey = at<uint32_t>(ws, L.akey);
+    P.id = at<uint32_t>(ws, L.id);
+    P.ang = at<float2>(ws, L.ang);
+    P.pms = at<float4>(ws, L.pms);
+    P.phi = at<double>(ws, L.phi);
+    P.r = at<double>(ws, L.r);
+    P.ch = at<double>(ws, L.ch);
+    P.sh = at<double>(ws, L.sh);
+    mark(RHG_STAGE_GATHER, false, stream);
+    st = launch_gather_batch(metas, bt, ks, is, rpos, P, stream);
+    if (st.code) return st;
+    mark(RHG_STAGE_GATHER, true, stream);
+    QueryArgs q{};
+    q.M = metas;
+    q.bt = bt;
+    q.P = P;
+    q.pairs = d_pairs;
+    q.heavy = at<uint4>(ws, L.heavy);
+    q.heavy_cap = L.heavy_cap;
+    q.recheck = at<uint2>(ws, L.recheck);
+    q.recheck_cap = L.recheck_cap;
+    q.bidx = at<uint32_t>(ws, L.bidx);
+    mark(RHG_STAGE_QUERY, false, stream);
+    st = launch_query_batch(q, stream);
+    if (st.code) return st;
+    mark(RHG_STAGE_QUERY, true, stream);
+    return launch_batch_results(metas, h.G, at<uint4>(ws, L.results), stream);
+}
+
 // Scratch of rhg_generate_pairs_static: one array per device, found by symbol.
 constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_static_scratch[RHG_STATIC_SCRATCH_BYTES];
@@ -528,6 +734,79 @@ int rhg_generate_pairs_static(const rhg_params *p, uint32_t *d_pairs, uint64_t c
     }
     return generate(p, ws, RHG_STATIC_SCRATCH_BYTES, Output::Pairs, d_pairs, capacity_edges, nullptr, nullptr,
                     static_cast<cudaStream_t>(stream), result);
+}
+
+int rhg_batch_workspace_bytes(const rhg_params *graphs, uint32_t count, size_t *bytes)
+{
+    if (!bytes) return RHG_ERR_INVALID_ARG;
+    BatchHost h;
+    const int rc = batch_host(graphs, count, nullptr, h);
+    if (rc) return rc;
+    *bytes = batch_layout(h).total;
+    return RHG_OK;
+}
+
+int rhg_generate_batch(const rhg_params *graphs, uint32_t count, void *d_workspace, size_t workspace_bytes,
+                       uint32_t *d_pairs, const uint64_t *pair_offsets, void *stream, rhg_batch_graph *results,
+                       rhg_result *totals)
+{
+    if (totals) std::memset(totals, 0, sizeof(*totals));
+    if (!d_workspace || !pair_offsets || !results) return RHG_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_workspace) & 255) return RHG_ERR_INVALID_ARG;
+    BatchHost h;
+    int rc = batch_host(graphs, count, pair_offsets, h);
+    if (rc) return rc;
+    if (h.out_off[count] && (!d_pairs || (reinterpret_cast<uintptr_t>(d_pairs) & 7))) return RHG_ERR_INVALID_ARG;
+    const BatchLayout L = batch_layout(h);
+    if (workspace_bytes < L.total) return RHG_ERR_OOM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<uint4> res(2 * static_cast<size_t>(count));
+    Meta ctl;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        Status st = upload_tables(d_workspace, L, h, s);
+        if (st.code) return finish(st, totals);
+        st = enqueue_batch(d_workspace, L, h, d_pairs, s);
+        if (st.code) return finish(st, totals);
+        const cudaError_t e1 = cudaMemcpyAsync(res.data(), at<uint4>(d_workspace, L.results),
+                                               res.size() * sizeof(uint4), cudaMemcpyDeviceToHost, s);
+        const cudaError_t e2 = cudaMemcpyAsync(&ctl, at<Meta>(d_workspace, L.metas) + count, sizeof(Meta),
+                                               cudaMemcpyDeviceToHost, s);
+        const cudaError_t e3 = cudaStreamSynchronize(s);
+        const cudaError_t e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
+        if (e != cudaSuccess) {
+            if (totals) totals->cuda_error = static_cast<int32_t>(e);
+            return RHG_ERR_CUDA;
+        }
+        if (ctl.error != kErrListFull || attempt) break;
+        for (auto &a : h.args) a.allow_filter = 0;  // the FP64 mode needs no recheck list
+    }
+    rc = RHG_OK;
+    uint64_t total_m = 0;
+    uint32_t all_filter = 1;
+    for (uint32_t g = 0; g < count; ++g) {
+        const uint4 a = res[2 * g], b = res[2 * g + 1];
+        rhg_batch_graph &r = results[g];
+        r.m = static_cast<uint64_t>(a.x) | (static_cast<uint64_t>(a.y) << 32);
+        const uint64_t Rb = static_cast<uint64_t>(a.z) | (static_cast<uint64_t>(a.w) << 32);
+        std::memcpy(&r.R, &Rb, sizeof(double));
+        r.num_bands = b.x;
+        r.mode = b.z ? 1u : 0u;
+        r.status = ctl.error ? error_from_meta(ctl.error) : error_from_meta(b.y);
+        if (r.status == RHG_OK && r.m > h.out_off[g + 1] - h.out_off[g]) r.status = RHG_ERR_OVERFLOW;
+        if (r.status == RHG_OK) total_m += r.m;
+        if (!r.mode) all_filter = 0;
+        if (rc == RHG_OK && r.status != RHG_OK) rc = r.status;
+    }
+    if (totals) {
+        totals->m = total_m;
+        totals->candidates = ctl.candidates;
+        totals->near_threshold = ctl.near_threshold;
+        totals->rechecks = ctl.rechecks;
+        totals->verify_failures = ctl.verify_failures;
+        totals->heavy_chunks = ctl.heavy_n;
+        totals->mode = all_filter;
+    }
+    return rc;
 }
 
 int rhg_dm_eval(int fn, const double *d_in, double *d_out, uint64_t count, void *stream)

@@ -32,9 +32,28 @@ struct SortedPoints {
     double *sh;           // dm::sinh(r)
 };
 
+// A batch of independent graphs (rhg_generate_batch): graph g owns the global
+// positions [pt_off[g], pt_off[g+1]) of every per-point array, the bucket-index
+// entries [idx_base[g], idx_base[g+1]) and the output pairs [out_off[g],
+// out_off[g+1]).  Work is cut into tiles of at most kTilePoints positions that
+// never cross a graph: tiles[t] = {graph, first position, count, 0}, and graph g's
+// tiles are [tile_first[g], tile_first[g+1]).  Meta blocks: metas[g] per graph and
+// metas[G], the control block holding the batch-wide counters and lists.
+constexpr uint32_t kTilePoints = 2048;
+struct BatchTables {
+    uint32_t G;
+    uint32_t num_tiles;
+    const uint4 *tiles;
+    const uint32_t *tile_first;  // G + 1
+    const uint32_t *pt_off;      // G + 1
+    const uint32_t *idx_base;    // G + 1
+    const uint64_t *out_off;     // G + 1
+};
+
 // Everything the range query kernels read and write.
 struct QueryArgs {
-    Meta *M;
+    Meta *M;                // the graph's Meta; batch: the G + 1 Meta blocks
+    BatchTables bt;         // batch only
     SortedPoints P;
     const double *src_phi;  // caller points by id (rhg_edges_from_points), else NULL
     const double *src_r;
@@ -66,6 +85,16 @@ Status launch_dm_eval(int fn, const double *in, double *out, uint64_t count, cud
 Status launch_points_by_id(const Meta *d_meta, uint64_t n, uint64_t seed, double *phi, double *r,
                            cudaStream_t stream);
 
+// batch versions (rhg_generate_batch): one launch each for all graphs
+Status launch_plan_batch(Meta *metas, const PlanArgs *d_args, uint32_t G, cudaStream_t stream);
+Status launch_sample_batch(Meta *metas, const BatchTables &bt, uint64_t *keys, uint32_t *ids, double *r_by_pos,
+                           cudaStream_t stream);
+Status launch_band_offsets_batch(Meta *metas, const BatchTables &bt, cudaStream_t stream);
+Status launch_gather_batch(const Meta *metas, const BatchTables &bt, const uint64_t *sorted_keys,
+                           const uint32_t *sorted_ids, const double *r_by_pos, SortedPoints P, cudaStream_t stream);
+// per-graph results: {m, R bits, B | error << 32, 0}
+Status launch_batch_results(const Meta *metas, uint32_t G, uint4 *d_out, cudaStream_t stream);
+
 // ---- sort.cu ----
 // LSD radix sort of 64-bit keys (optionally with uint32 values) over the 8-bit
 // digits whose shifts are listed.  Stable.  On return *keys_out / *vals_out point at
@@ -75,12 +104,21 @@ Status radix_sort(uint64_t n, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals
                   uint32_t *vals_alt, const int *shifts, int num_shifts, void *temp,
                   uint64_t **keys_out, uint32_t **vals_out, cudaStream_t stream);
 
+// Segmented version for a batch: every graph's positions are sorted among
+// themselves (tiles of kTilePoints positions, per-tile digit counts).
+size_t segmented_temp_bytes(uint32_t num_tiles);
+Status segmented_radix_sort(const BatchTables &bt, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals,
+                            uint32_t *vals_alt, const int *shifts, int num_shifts, void *temp, uint64_t **keys_out,
+                            uint32_t **vals_out, cudaStream_t stream);
+
 // ---- query.cu ----
 // Range query (Alg. 1): windows, search, candidate test, output; then the heavy
 // chunks and the FP64 rechecks.  Output positions are reserved per warp batch,
 // so the pair order is unspecified; Meta::m is the exact edge count.  The kernels
 // of both modes are launched; each returns at once unless Meta::filter selects it.
 Status launch_query(const QueryArgs &a, bool csr, cudaStream_t stream);
+// The same for a batch (pairs only): per-graph windows, outputs and counters.
+Status launch_query_batch(const QueryArgs &a, cudaStream_t stream);
 // CSR row pointers from directed keys sorted by (row, col); col = low words.
 Status launch_csr_finish(const uint64_t *sorted_keys, uint64_t entries, uint64_t n, uint64_t *row_ptr,
                          uint32_t *col, cudaStream_t stream);

@@ -31,7 +31,8 @@ __device__ double kbar(double R, double nd, double alpha)
 
 constexpr int kPlanThreads = 256;  // grid points j = 0..255 of the bracket search
 
-__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, PlanArgs a)
+// R, boundaries and the band constants of one graph, by one CTA of kPlanThreads.
+__device__ void plan_block(Meta *M, const PlanArgs &a)
 {
     __shared__ int jstar;
     __shared__ double R_sh;
@@ -131,6 +132,32 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, PlanArgs a)
     M->work_counter = 0;
 }
 
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, PlanArgs a) { plan_block(M, a); }
+
+// Batch: CTA g < G plans graph g; CTA G clears the control block's counters.
+__global__ void __launch_bounds__(kPlanThreads) plan_batch_kernel(Meta *metas, const PlanArgs *args, uint32_t G)
+{
+    if (blockIdx.x < G) {
+        const PlanArgs a = args[blockIdx.x];
+        plan_block(metas + blockIdx.x, a);
+        return;
+    }
+    if (threadIdx.x != 0) return;
+    Meta *C = metas + G;
+    C->error = kErrNone;
+    C->filter = 0;
+    C->verify = 0;
+    C->m = 0;
+    C->candidates = 0;
+    C->near_threshold = 0;
+    C->rechecks = 0;
+    C->verify_failures = 0;
+    C->heavy_n = 0;
+    C->heavy_next = 0;
+    C->recheck_n = 0;
+    C->work_counter = 0;
+}
+
 constexpr int kSampleThreads = 256;
 
 // Points by id: sort key (band << 32 | angle key) and id.  In filter mode the band
@@ -195,11 +222,49 @@ __global__ void __launch_bounds__(kSampleThreads) load_points_kernel(Meta *M, ui
     if (threadIdx.x < B && hist[threadIdx.x]) atomicAdd(&M->band_count[threadIdx.x], hist[threadIdx.x]);
 }
 
-__global__ void band_offsets_kernel(Meta *M)
+// Batch: CTA per tile.  Position p of graph g holds vertex p - pt_off[g]; the
+// FP64 radius (FP64 mode) is stored by position.
+__global__ void __launch_bounds__(kSampleThreads) sample_batch_kernel(Meta *metas, BatchTables bt, uint64_t *keys,
+                                                                      uint32_t *ids, double *r_by_pos)
 {
-    if (threadIdx.x != 0) return;
-    uint64_t s = 0;
-    uint32_t off = 0;
+    __shared__ double c[kMaxBands + 1];
+    __shared__ unsigned int hist[kMaxBands];
+    const uint4 T = bt.tiles[blockIdx.x];
+    Meta *M = metas + T.x;
+    const uint32_t B = M->B;
+    const bool filter = M->filter != 0;
+    const double R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
+    const uint64_t seed = M->seed;
+    if (threadIdx.x <= B) c[threadIdx.x] = M->c[threadIdx.x];
+    if (threadIdx.x < kMaxBands) hist[threadIdx.x] = 0;
+    __syncthreads();
+    if (M->error) return;
+    const uint32_t first_id = T.y - bt.pt_off[T.x];
+    for (uint32_t j = threadIdx.x; j < T.z; j += blockDim.x) {
+        const uint32_t id = first_id + j, pos = T.y + j;
+        const U64x4 x = draw(id, seed);
+        double r;
+        if (filter) {
+            r = radius_approx(x.x1 >> 11, R, cm1, inv_alpha);
+        } else {
+            r = radius_from_u53(x.x1 >> 11, R, cm1, inv_alpha);
+            r_by_pos[pos] = r;
+        }
+        const uint32_t b = band_of(r, c, B);
+        keys[pos] = (static_cast<uint64_t>(b) << 32) | static_cast<uint32_t>(x.x0 >> 32);
+        ids[pos] = id;
+        atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < B && hist[threadIdx.x]) atomicAdd(&M->band_count[threadIdx.x], hist[threadIdx.x]);
+}
+
+// Band starts (sorted positions) and bucket-index offsets of one graph whose
+// positions start at pos0 and whose index entries start at idx0.
+__device__ void band_offsets_one(Meta *M, uint64_t pos0, uint32_t idx0)
+{
+    uint64_t s = pos0;
+    uint32_t off = idx0;
     for (uint32_t j = 0; j < M->B; ++j) {
         M->band_start[j] = s;
         s += M->band_count[j];
@@ -212,6 +277,17 @@ __global__ void band_offsets_kernel(Meta *M)
     }
     M->band_start[M->B] = s;
     M->idx_off[M->B] = off;
+}
+
+__global__ void band_offsets_kernel(Meta *M)
+{
+    if (threadIdx.x == 0) band_offsets_one(M, 0, 0);
+}
+
+__global__ void band_offsets_batch_kernel(Meta *metas, BatchTables bt)
+{
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < bt.G) band_offsets_one(metas + g, bt.pt_off[g], bt.idx_base[g]);
 }
 
 // e^x in FP32 with relative error <= 4 * 2^-24 for |x| <= kExpTab + 1/2:
@@ -299,6 +375,71 @@ __global__ void __launch_bounds__(256) gather_fp64_kernel(const Meta *M, uint64_
     }
 }
 
+// Batch gathers: CTA per tile; ids are local, the FP64 radius is by position.
+__global__ void __launch_bounds__(256) gather_filter_batch_kernel(const Meta *metas, BatchTables bt,
+                                                                  const uint64_t *keys, const uint32_t *sids,
+                                                                  SortedPoints P)
+{
+    __shared__ float etab[2 * kExpTab + 1];
+    const uint4 T = bt.tiles[blockIdx.x];
+    const Meta *M = metas + T.x;
+    for (int j = threadIdx.x; j <= 2 * kExpTab; j += blockDim.x) etab[j] = M->etab[j];
+    __syncthreads();
+    if (M->error || !M->filter) return;
+    const double G = M->G, R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
+    const uint64_t seed = M->seed;
+    for (uint32_t j = threadIdx.x; j < T.z; j += blockDim.x) {
+        const uint32_t p = T.y + j;
+        const uint32_t id = sids[p];
+        const U64x4 x = draw(id, seed);
+        const double ph = phi_from_u53(x.x0 >> 11);
+        const double r = radius_approx(x.x1 >> 11, R, cm1, inv_alpha);
+        float2 a;
+        float4 q;
+        filter_values(ph, r, G, etab, &a, &q);
+        P.akey[p] = static_cast<uint32_t>(keys[p]);
+        P.ang[p] = a;
+        P.pms[p] = q;
+        P.id[p] = id;
+    }
+}
+
+__global__ void __launch_bounds__(256) gather_fp64_batch_kernel(const Meta *metas, BatchTables bt,
+                                                                const uint64_t *keys, const uint32_t *sids,
+                                                                const double *r_by_pos, SortedPoints P)
+{
+    const uint4 T = bt.tiles[blockIdx.x];
+    const Meta *M = metas + T.x;
+    if (M->error || M->filter) return;
+    const uint64_t seed = M->seed;
+    const uint32_t pos0 = bt.pt_off[T.x];
+    for (uint32_t j = threadIdx.x; j < T.z; j += blockDim.x) {
+        const uint32_t p = T.y + j;
+        const uint32_t id = sids[p];
+        const double ph = phi_from_u53(draw(id, seed).x0 >> 11);
+        const double r = r_by_pos[pos0 + id];
+        P.phi[p] = ph;
+        P.r[p] = r;
+        P.ch[p] = dm::cosh(r);
+        P.sh[p] = dm::sinh(r);
+        P.akey[p] = static_cast<uint32_t>(keys[p]);
+        P.id[p] = id;
+    }
+}
+
+// Per-graph results of a batch: {m low, m high, R low, R high} and {B, error}.
+__global__ void batch_results_kernel(const Meta *metas, uint32_t G, uint4 *out)
+{
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const Meta *M = metas + g;
+    const uint64_t m = M->m;
+    const uint64_t Rb = static_cast<uint64_t>(__double_as_longlong(M->R));
+    out[2 * g] = make_uint4(static_cast<uint32_t>(m), static_cast<uint32_t>(m >> 32), static_cast<uint32_t>(Rb),
+                            static_cast<uint32_t>(Rb >> 32));
+    out[2 * g + 1] = make_uint4(M->B, M->error, M->filter, 0u);
+}
+
 __global__ void points_by_id_kernel(const Meta *M, uint64_t n, uint64_t seed, double *phi, double *r)
 {
     const double R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
@@ -382,6 +523,52 @@ Status launch_gather(const Meta *d_meta, uint64_t n, uint64_t seed, const uint64
     RHG_LAUNCH_CHECK();
     gather_fp64_kernel<<<grid_for(n, 256, 8), 256, 0, stream>>>(d_meta, n, seed, sorted_keys, sorted_ids,
                                                               phi_src, r64_src, P);
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+Status launch_plan_batch(Meta *metas, const PlanArgs *d_args, uint32_t G, cudaStream_t stream)
+{
+    Status st;
+    plan_batch_kernel<<<G + 1, kPlanThreads, 0, stream>>>(metas, d_args, G);
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+Status launch_sample_batch(Meta *metas, const BatchTables &bt, uint64_t *keys, uint32_t *ids, double *r_by_pos,
+                           cudaStream_t stream)
+{
+    Status st;
+    if (!bt.num_tiles) return st;
+    sample_batch_kernel<<<bt.num_tiles, kSampleThreads, 0, stream>>>(metas, bt, keys, ids, r_by_pos);
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+Status launch_band_offsets_batch(Meta *metas, const BatchTables &bt, cudaStream_t stream)
+{
+    Status st;
+    band_offsets_batch_kernel<<<static_cast<unsigned>(ceil_div(bt.G, 128u)), 128, 0, stream>>>(metas, bt);
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+Status launch_gather_batch(const Meta *metas, const BatchTables &bt, const uint64_t *sorted_keys,
+                           const uint32_t *sorted_ids, const double *r_by_pos, SortedPoints P, cudaStream_t stream)
+{
+    Status st;
+    if (!bt.num_tiles) return st;
+    gather_filter_batch_kernel<<<bt.num_tiles, 256, 0, stream>>>(metas, bt, sorted_keys, sorted_ids, P);
+    RHG_LAUNCH_CHECK();
+    gather_fp64_batch_kernel<<<bt.num_tiles, 256, 0, stream>>>(metas, bt, sorted_keys, sorted_ids, r_by_pos, P);
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+Status launch_batch_results(const Meta *metas, uint32_t G, uint4 *d_out, cudaStream_t stream)
+{
+    Status st;
+    batch_results_kernel<<<static_cast<unsigned>(ceil_div(G, 128u)), 128, 0, stream>>>(metas, G, d_out);
     RHG_LAUNCH_CHECK();
     return st;
 }

@@ -55,9 +55,9 @@ struct BandShared {
     uint32_t ioff[kMaxBands + 1], ishift[kMaxBands + 1];  // bucket index of each band
 };
 
-__device__ __forceinline__ void load_bands(BandShared &S, const Meta *M)
+__device__ __forceinline__ void load_bands_from(BandShared &S, const Meta *M, int first, int stride)
 {
-    for (int j = threadIdx.x; j <= kMaxBands; j += blockDim.x) {
+    for (int j = first; j <= kMaxBands; j += stride) {
         S.start[j] = static_cast<uint32_t>(M->band_start[j]);
         S.P[j] = M->band_P[j];
         S.Mm[j] = M->band_M[j];
@@ -73,6 +73,8 @@ __device__ __forceinline__ void load_bands(BandShared &S, const Meta *M)
         S.ishift[j] = j < kMaxBands ? M->idx_shift[j] : 32u;
     }
 }
+
+__device__ __forceinline__ void load_bands(BandShared &S, const Meta *M) { load_bands_from(S, M, threadIdx.x, blockDim.x); }
 
 // The values of a range's owner (the point whose neighbours are searched) that
 // its lane keeps in registers for the windows.
@@ -320,18 +322,20 @@ __device__ __forceinline__ void key_ranges(const uint32_t *akey, uint32_t s, uin
     }
 }
 
-__device__ __forceinline__ void push_heavy(const QueryArgs &a, uint32_t p, uint32_t lo, uint32_t hi, uint32_t type)
+// tag = type (0 fringe, 1 core) | graph << 1 (batch)
+__device__ __forceinline__ void push_heavy(const QueryArgs &a, Meta *C, uint32_t p, uint32_t lo, uint32_t hi,
+                                           uint32_t tag)
 {
     const uint32_t nch = (hi - lo + kChunk - 1) / kChunk;
-    const uint32_t at = atomicAdd(&a.M->heavy_n, nch);
+    const uint32_t at = atomicAdd(&C->heavy_n, nch);
     if (at + nch > a.heavy_cap || at + nch < at) {
-        atomicMax(&a.M->error, kErrListFull);
+        atomicMax(&C->error, kErrListFull);
         return;
     }
     for (uint32_t j = 0; j < nch; ++j) {
         const uint32_t c0 = lo + j * kChunk;
         const uint32_t c1 = hi - c0 > kChunk ? c0 + kChunk : hi;
-        a.heavy[at + j] = make_uint4(p, c0, c1, type);
+        a.heavy[at + j] = make_uint4(p, c0, c1, tag);
     }
 }
 
@@ -366,21 +370,22 @@ __device__ __forceinline__ void fp64_point(const QueryArgs &a, const Meta *M, ui
 // Verification mode: the FP64 predicate for a pair the filter or the core
 // decided; a contradiction, or a decided pair within 1e-12 of the threshold, is
 // counted.
-__device__ __noinline__ void verify_pair(const QueryArgs &a, uint32_t idv, uint32_t idw, int dec, double coshR)
+__device__ __noinline__ void verify_pair(const QueryArgs &a, const Meta *Mg, Meta *C, uint32_t idv, uint32_t idw,
+                                         int dec, double coshR)
 {
     double pv, cv, sv, pw, cw, sw;
-    fp64_point(a, a.M, idv, pv, cv, sv);
-    fp64_point(a, a.M, idw, pw, cw, sw);
+    fp64_point(a, Mg, idv, pv, cv, sv);
+    fp64_point(a, Mg, idw, pw, cw, sw);
     const double L = predicate_L(pv, cv, sv, pw, cw, sw);
     if ((L <= coshR) != (dec == 1) || fabs(L - coshR) <= 1e-12 * coshR)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&a.M->verify_failures), 1ull);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&C->verify_failures), 1ull);
 }
 
 // Decide candidate q (owner slot o); queue undecided pairs; in verification mode
 // compare every decided pair with the FP64 predicate.
 template <bool kFilter>
-__device__ __forceinline__ int decide(const QueryArgs &a, const WarpSmem &W, uint32_t o, uint32_t q, bool in,
-                                      double coshR, bool verify, uint32_t &near)
+__device__ __forceinline__ int decide(const QueryArgs &a, const Meta *Mg, Meta *C, const WarpSmem &W, uint32_t o,
+                                      uint32_t q, bool in, double coshR, bool verify, uint32_t &near)
 {
     const unsigned full = 0xffffffffu;
     int dec = 0;
@@ -390,15 +395,15 @@ __device__ __forceinline__ int decide(const QueryArgs &a, const WarpSmem &W, uin
         if (um) {
             const int lane = threadIdx.x & 31;
             uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&a.M->recheck_n, static_cast<uint32_t>(__popc(um)));
+            if (lane == 0) base = atomicAdd(&C->recheck_n, static_cast<uint32_t>(__popc(um)));
             base = __shfl_sync(full, base, 0);
             if (dec == 2) {
                 const uint32_t at = base + __popc(um & ((1u << lane) - 1u));
                 if (at < a.recheck_cap) a.recheck[at] = make_uint2(W.opos[o], q);
-                else atomicMax(&a.M->error, kErrListFull);
+                else atomicMax(&C->error, kErrListFull);
             }
         }
-        if (verify && in && dec != 2) verify_pair(a, W.oid[o], a.P.id[q], dec, coshR);
+        if (verify && in && dec != 2) verify_pair(a, Mg, C, W.oid[o], a.P.id[q], dec, coshR);
     } else if (in) {
         const double2 v = W.od[o];
         const double L = predicate_L(v.x, v.y, W.osh[o], a.P.phi[q], a.P.ch[q], a.P.sh[q]);
@@ -409,16 +414,19 @@ __device__ __forceinline__ int decide(const QueryArgs &a, const WarpSmem &W, uin
 }
 
 // Write the queued core entries [0, ccount): certain edges, no test.
+// Output: graph Mg's edge counter, its region starting at obase with room for cap pairs.
 template <bool kCsr>
-__device__ __forceinline__ void flush_core(const QueryArgs &a, WarpSmem &W, int ccount, double coshR, bool verify)
+__device__ __forceinline__ void flush_core(const QueryArgs &a, Meta *Mg, Meta *C, uint64_t obase, uint64_t cap,
+                                           WarpSmem &W, int ccount, double coshR, bool verify)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint32_t total = W.cpre[ccount];
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(&a.M->m), total);
+    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(&Mg->m), total);
     base = __shfl_sync(full, base, 0);
-    if (base + total > a.capacity) return;
+    if (base + total > cap) return;
+    base += obase;
     int e0 = 0;
     for (uint32_t j0 = 0; j0 < total; j0 += 32) {
         while (W.cpre[e0 + 1] <= j0) ++e0;
@@ -429,7 +437,7 @@ __device__ __forceinline__ void flush_core(const QueryArgs &a, WarpSmem &W, int 
             const uint32_t q = W.clo[e] + (j - W.cpre[e]);
             const uint32_t idv = W.oid[W.cown[e]], idw = a.P.id[q];
             write_edge<kCsr>(a, base + j, idv, idw);
-            if (verify) verify_pair(a, idv, idw, 1, coshR);
+            if (verify) verify_pair(a, Mg, C, idv, idw, 1, coshR);
         }
     }
 }
@@ -440,8 +448,8 @@ __device__ __forceinline__ void flush_core(const QueryArgs &a, WarpSmem &W, int 
 // The entry of a round's first candidate advances monotonically (warp-uniform);
 // each lane then steps forward over the few entries its round crosses.
 template <bool kFilter, bool kCsr>
-__device__ __forceinline__ void flush(const QueryArgs &a, WarpSmem &W, int count, double coshR, bool verify,
-                                      uint32_t &near)
+__device__ __forceinline__ void flush(const QueryArgs &a, Meta *Mg, Meta *C, uint64_t obase, uint64_t cap,
+                                      WarpSmem &W, int count, double coshR, bool verify, uint32_t &near)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -460,7 +468,7 @@ __device__ __forceinline__ void flush(const QueryArgs &a, WarpSmem &W, int count
             if (in)
                 while (W.pre[e + 1] <= j) ++e;
             const uint32_t q = W.lo[e] + (j - W.pre[e]);
-            const int dec = decide<kFilter>(a, W, W.own[e], q, in, coshR, verify, near);
+            const int dec = decide<kFilter>(a, Mg, C, W, W.own[e], q, in, coshR, verify, near);
             const uint32_t word = __ballot_sync(full, dec == 1);
             if (lane == 0) {
                 W.bits[words] = word;
@@ -471,9 +479,10 @@ __device__ __forceinline__ void flush(const QueryArgs &a, WarpSmem &W, int count
         }
         __syncwarp();
         unsigned long long base = 0;
-        if (lane == 0 && edges) base = atomicAdd(reinterpret_cast<unsigned long long *>(&a.M->m), edges);
+        if (lane == 0 && edges) base = atomicAdd(reinterpret_cast<unsigned long long *>(&Mg->m), edges);
         base = __shfl_sync(full, base, 0);
-        if (edges && base + edges <= a.capacity) {
+        if (edges && base + edges <= cap) {
+            base += obase;
             uint32_t run = 0;
             for (int wi = 0; wi < words; ++wi) {
                 const uint32_t word = W.bits[wi];
@@ -494,9 +503,9 @@ __device__ __forceinline__ void flush(const QueryArgs &a, WarpSmem &W, int count
 // Test one candidate of the lane's own point (owner values in registers):
 // 1 = edge, 0 = no edge, 2 = undecided (queued for the FP64 recheck).
 template <bool kFilter>
-__device__ __forceinline__ int decide_own(const QueryArgs &a, float4 va, float4 vb, const OwnerRegs &v,
-                                          double phv, uint32_t p, uint32_t idv, uint32_t q, bool in, double coshR,
-                                          bool verify, uint32_t &near)
+__device__ __forceinline__ int decide_own(const QueryArgs &a, const Meta *Mg, Meta *C, float4 va, float4 vb,
+                                          const OwnerRegs &v, double phv, uint32_t p, uint32_t idv, uint32_t q,
+                                          bool in, double coshR, bool verify, uint32_t &near)
 {
     const unsigned full = 0xffffffffu;
     int dec = 0;
@@ -506,15 +515,15 @@ __device__ __forceinline__ int decide_own(const QueryArgs &a, float4 va, float4 
         if (um) {
             const int lane = threadIdx.x & 31;
             uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&a.M->recheck_n, static_cast<uint32_t>(__popc(um)));
+            if (lane == 0) base = atomicAdd(&C->recheck_n, static_cast<uint32_t>(__popc(um)));
             base = __shfl_sync(full, base, 0);
             if (dec == 2) {
                 const uint32_t at = base + __popc(um & ((1u << lane) - 1u));
                 if (at < a.recheck_cap) a.recheck[at] = make_uint2(p, q);
-                else atomicMax(&a.M->error, kErrListFull);
+                else atomicMax(&C->error, kErrListFull);
             }
         }
-        if (verify && in && dec != 2) verify_pair(a, idv, a.P.id[q], dec, coshR);
+        if (verify && in && dec != 2) verify_pair(a, Mg, C, idv, a.P.id[q], dec, coshR);
     } else if (in) {
         const double L = predicate_L(phv, v.ch, v.sh, a.P.phi[q], a.P.ch[q], a.P.sh[q]);
         dec = L <= coshR;
@@ -526,20 +535,34 @@ __device__ __forceinline__ int decide_own(const QueryArgs &a, float4 va, float4 
 // One warp per batch of 32 consecutive sorted points, lane = point; for each band
 // every lane tests its own few fringe candidates (decision bits in a register),
 // then one warp-wide reservation places each lane's core and fringe edges.
-template <bool kFilter, bool kCsr>
+// kMulti (a batch of graphs): batches are 32-point slices of the tiles, each warp
+// keeps the band table of its current graph in its own shared memory, and edges
+// go to the graph's output region and counter; lists and work counters live in
+// the control block.
+template <bool kFilter, bool kCsr, bool kMulti>
 __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
 {
-    __shared__ BandShared S;
-    Meta *M = a.M;
-    load_bands(S, M);
-    __syncthreads();
-    if (M->error || (M->filter != 0) != kFilter) return;
-    const unsigned full = 0xffffffffu;
-    const uint32_t n = static_cast<uint32_t>(a.P.n), B = M->B;
-    const double coshR = M->coshR;
-    const bool verify = M->verify != 0;
+    __shared__ BandShared Sm[kMulti ? kWarps : 1];
     const int lane = threadIdx.x & 31;
-    const uint32_t nbatch = (n + 31) / 32;
+    BandShared &S = Sm[kMulti ? (threadIdx.x >> 5) : 0];
+    Meta *C = kMulti ? a.M + a.bt.G : a.M;  // counters and lists
+    Meta *M = a.M;                          // the current graph
+    if (!kMulti) {
+        load_bands(S, M);
+        __syncthreads();
+        if (M->error || (M->filter != 0) != kFilter) return;
+    } else if (C->error) {
+        return;
+    }
+    const unsigned full = 0xffffffffu;
+    const uint32_t n = static_cast<uint32_t>(a.P.n);
+    uint32_t B = M->B;
+    double coshR = M->coshR;
+    bool verify = M->verify != 0;
+    uint64_t obase = 0, cap = a.capacity;  // output region of the current graph
+    uint32_t cur_g = 0xffffffffu;
+    bool skip = false;
+    const uint32_t nbatch = kMulti ? a.bt.num_tiles * (kTilePoints / 32) : (n + 31) / 32;
     __shared__ uint8_t own_sm[kWarps][32];
     uint8_t *own = own_sm[threadIdx.x >> 5];
     unsigned long long cand = 0;
@@ -549,11 +572,36 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
     for (;;) {
         uint32_t batch = 0;
         if (lane == 0)
-            batch = static_cast<uint32_t>(atomicAdd(reinterpret_cast<unsigned long long *>(&M->work_counter), 1ull));
+            batch = static_cast<uint32_t>(atomicAdd(reinterpret_cast<unsigned long long *>(&C->work_counter), 1ull));
         batch = __shfl_sync(full, batch, 0);
         if (batch >= nbatch) break;
-        const uint32_t p = batch * 32 + lane;
-        const bool valid = p < n;
+        uint32_t p0, cnt;  // first sorted position and points of this batch
+        if (kMulti) {
+            const uint4 T = a.bt.tiles[batch / (kTilePoints / 32)];
+            const uint32_t sub = (batch % (kTilePoints / 32)) * 32;
+            if (sub >= T.z) continue;
+            if (T.x != cur_g) {
+                cur_g = T.x;
+                M = a.M + cur_g;
+                __syncwarp();
+                load_bands_from(S, M, lane, 32);
+                __syncwarp();
+                B = M->B;
+                coshR = M->coshR;
+                verify = M->verify != 0;
+                obase = a.bt.out_off[cur_g];
+                cap = a.bt.out_off[cur_g + 1] - obase;
+                skip = M->error || (M->filter != 0) != kFilter;
+            }
+            if (skip) continue;
+            p0 = T.y + sub;
+            cnt = T.z - sub < 32 ? T.z - sub : 32;
+        } else {
+            p0 = batch * 32;
+            cnt = n - p0 < 32 ? n - p0 : 32;
+        }
+        const uint32_t p = p0 + lane;
+        const bool valid = static_cast<uint32_t>(lane) < cnt;
         OwnerRegs mine{};
         float4 va = make_float4(0, 0, 0, 0), vb = va;
         double phv = 0.0;
@@ -626,16 +674,17 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
                 // every warp shares
                 const uint32_t room = kept < kBatchBudget ? (kBatchBudget - kept) / 32 : 0;
                 const uint32_t hc = kCoreHeavy < (room > 64 ? room : 64) ? kCoreHeavy : (room > 64 ? room : 64);
+                const uint32_t gtag = kMulti ? cur_g << 1 : 0u;
                 if (f1 - f0 > 32) {
-                    push_heavy(a, p, f0, f1, 0);
+                    push_heavy(a, C, p, f0, f1, gtag);
                     f1 = f0;
                 }
                 if (f3 - f2 > 32) {
-                    push_heavy(a, p, f2, f3, 0);
+                    push_heavy(a, C, p, f2, f3, gtag);
                     f3 = f2;
                 }
                 if (c1 - c0 > hc) {
-                    push_heavy(a, p, c0, c1, 1);
+                    push_heavy(a, C, p, c0, c1, gtag | 1u);
                     c1 = c0;
                 }
             }
@@ -646,7 +695,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
             for (uint32_t t = 0; t < maxf; ++t) {
                 const bool in = t < nf;
                 const uint32_t q = t < nl ? f0 + t : f2 + (t - nl);
-                const int dec = decide_own<kFilter>(a, va, vb, mine, phv, p, idv, q, in, coshR, verify, near);
+                const int dec = decide_own<kFilter>(a, M, C, va, vb, mine, phv, p, idv, q, in, coshR, verify, near);
                 if (dec == 1) mask |= 1ull << t;
             }
             // one reservation for the warp's edges of this band: [base, base + T)
@@ -668,7 +717,8 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(&M->m), total);
             base = __shfl_sync(full, base, 0);
-            if (base + total > a.capacity) continue;
+            if (base + total > cap) continue;
+            base += obase;
             // core edges: element j of the concatenation goes to base + j (coalesced);
             // its owner is the lane whose segment starts last at or before j: the
             // segment starts inside each 32-element window are one OR-reduction and
@@ -687,7 +737,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
                 if (j < T) {
                     const uint32_t w = __ldg(a.P.id + (j + dl));
                     write_edge<kCsr>(a, base + j, u, w);
-                    if (verify) verify_pair(a, u, w, 1, coshR);
+                    if (verify) verify_pair(a, M, C, u, w, 1, coshR);
                 }
                 L = __shfl_sync(full, L, 31);  // owner of the window's last element
                 __syncwarp();
@@ -706,36 +756,42 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
         near += __shfl_down_sync(full, near, off);
     }
     if (lane == 0) {
-        if (cand) atomicAdd(reinterpret_cast<unsigned long long *>(&M->candidates), cand);
-        if (near) atomicAdd(reinterpret_cast<unsigned long long *>(&M->near_threshold),
+        if (cand) atomicAdd(reinterpret_cast<unsigned long long *>(&C->candidates), cand);
+        if (near) atomicAdd(reinterpret_cast<unsigned long long *>(&C->near_threshold),
                             static_cast<unsigned long long>(near));
     }
 }
 
 // Heavy chunks: one warp per chunk of at most kChunk candidates of one owner,
 // tested (type 0) or a core chunk of certain edges (type 1).
-template <bool kFilter, bool kCsr>
+template <bool kFilter, bool kCsr, bool kMulti>
 __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
 {
     __shared__ WarpSmem Wsm[kWarps];
-    Meta *M = a.M;
-    if (M->error || (M->filter != 0) != kFilter) return;
+    Meta *C = kMulti ? a.M + a.bt.G : a.M;
+    if (C->error || (!kMulti && (C->filter != 0) != kFilter)) return;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmem &W = Wsm[warp];
-    const double coshR = M->coshR;
-    const bool verify = M->verify != 0;
-    const uint32_t count = M->heavy_n < a.heavy_cap ? M->heavy_n : a.heavy_cap;
+    const uint32_t count = C->heavy_n < a.heavy_cap ? C->heavy_n : a.heavy_cap;
     uint32_t near = 0;
     for (;;) {
         uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(&M->heavy_next, 1u);
+        if (lane == 0) item = atomicAdd(&C->heavy_next, 1u);
         item = __shfl_sync(full, item, 0);
         if (item >= count) break;
         const uint4 h = a.heavy[item];
+        const uint32_t g = h.w >> 1;
+        Meta *Mg = kMulti ? a.M + g : a.M;
+        if (kMulti && (Mg->error || (Mg->filter != 0) != kFilter)) continue;
+        const double coshR = Mg->coshR;
+        const bool verify = Mg->verify != 0;
+        const uint64_t obase = kMulti ? a.bt.out_off[g] : 0;
+        const uint64_t cap = kMulti ? a.bt.out_off[g + 1] - obase : a.capacity;
+        const bool core = (h.w & 1u) != 0;
         if (lane == 0) {
             load_owner<kFilter>(a.P, W, 0, h.x);
-            if (h.w) {
+            if (core) {
                 W.clo[0] = h.y;
                 W.cpre[0] = 0;
                 W.cpre[1] = h.z - h.y;
@@ -748,13 +804,13 @@ __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
             }
         }
         __syncwarp();
-        if (h.w) flush_core<kCsr>(a, W, 1, coshR, verify);
-        else flush<kFilter, kCsr>(a, W, 1, coshR, verify, near);
+        if (core) flush_core<kCsr>(a, Mg, C, obase, cap, W, 1, coshR, verify);
+        else flush<kFilter, kCsr>(a, Mg, C, obase, cap, W, 1, coshR, verify, near);
         __syncwarp();
     }
     for (int off = 16; off; off >>= 1) near += __shfl_down_sync(full, near, off);
     if (lane == 0 && near)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&M->near_threshold), static_cast<unsigned long long>(near));
+        atomicAdd(reinterpret_cast<unsigned long long *>(&C->near_threshold), static_cast<unsigned long long>(near));
 }
 
 // FP64 recheck of the pairs the filter left undecided: the predicate of Eq. 3 on
@@ -797,6 +853,54 @@ __global__ void __launch_bounds__(kThreads) recheck_kernel(QueryArgs a)
     if (lane == 0 && near)
         atomicAdd(reinterpret_cast<unsigned long long *>(&M->near_threshold), static_cast<unsigned long long>(near));
     if (blockIdx.x == 0 && threadIdx.x == 0) M->rechecks = count;
+}
+
+// Batch recheck: each pair's graph from the owner position; one output slot per
+// edge from the graph's counter (the pairs are few).
+__global__ void __launch_bounds__(kThreads) recheck_batch_kernel(QueryArgs a)
+{
+    Meta *C = a.M + a.bt.G;
+    if (C->error) return;
+    const uint32_t count = C->recheck_n < a.recheck_cap ? C->recheck_n : a.recheck_cap;
+    uint32_t near = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += stride) {
+        const uint2 pq = a.recheck[idx];
+        uint32_t lo = 0, hi = a.bt.G;  // graph g: pt_off[g] <= pq.x < pt_off[g + 1]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.bt.pt_off[mid] <= pq.x) lo = mid;
+            else hi = mid;
+        }
+        Meta *Mg = a.M + lo;
+        const uint32_t idv = a.P.id[pq.x], idw = a.P.id[pq.y];
+        double pv, cv, sv, pw, cw, sw;
+        fp64_point(a, Mg, idv, pv, cv, sv);
+        fp64_point(a, Mg, idw, pw, cw, sw);
+        const double coshR = Mg->coshR;
+        const double L = predicate_L(pv, cv, sv, pw, cw, sw);
+        near += fabs(L - coshR) <= 1e-12 * coshR;
+        if (L <= coshR) {
+            const unsigned long long at = atomicAdd(reinterpret_cast<unsigned long long *>(&Mg->m), 1ull);
+            const uint64_t obase = a.bt.out_off[lo];
+            if (at < a.bt.out_off[lo + 1] - obase) write_edge<false>(a, obase + at, idv, idw);
+        }
+    }
+    for (int off = 16; off; off >>= 1) near += __shfl_down_sync(0xffffffffu, near, off);
+    if ((threadIdx.x & 31) == 0 && near)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&C->near_threshold), static_cast<unsigned long long>(near));
+    if (blockIdx.x == 0 && threadIdx.x == 0) C->rechecks = count;
+}
+
+// Between the filter and the FP64 phase of a batch: the work counters and the
+// heavy list start again (the recheck list and the statistics carry over).
+__global__ void reset_phase_kernel(Meta *C)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        C->work_counter = 0;
+        C->heavy_n = 0;
+        C->heavy_next = 0;
+    }
 }
 
 // --------------------------------------------------------------------- CSR finish
@@ -856,6 +960,39 @@ __global__ void __launch_bounds__(kThreads) bucket_index_kernel(const Meta *M, c
     }
 }
 
+// Batch: CTA per tile, the tile's graph's bands and index region.
+__global__ void __launch_bounds__(kThreads) bucket_index_batch_kernel(const Meta *metas, BatchTables bt,
+                                                                       const uint64_t *keys, uint32_t *idx)
+{
+    const uint4 T = bt.tiles[blockIdx.x];
+    const Meta *M = metas + T.x;
+    if (M->error || metas[bt.G].error) return;
+    const uint32_t B = M->B;
+    const uint64_t cap = bt.idx_base[T.x + 1];
+    for (uint32_t jj = threadIdx.x; jj < T.z; jj += blockDim.x) {
+        const uint64_t p = T.y + jj;
+        const uint64_t key = keys[p];
+        const uint32_t b = static_cast<uint32_t>(key >> 32);
+        if (b >= B) {  // cannot happen: every key carries its band
+            atomicExch(const_cast<uint32_t *>(&metas[bt.G].error), kErrInternal);
+            return;
+        }
+        const uint32_t sh = M->idx_shift[b], off = M->idx_off[b];
+        const uint64_t s = M->band_start[b], e = M->band_start[b + 1];
+        const uint32_t cur = static_cast<uint32_t>(key) >> sh;
+        const uint32_t first = p == s ? 0u : (static_cast<uint32_t>(keys[p - 1]) >> sh) + 1;
+        if (off + (1ull << (32 - sh)) >= cap) {  // cannot happen: bounded by index_entries(n_g)
+            atomicExch(const_cast<uint32_t *>(&metas[bt.G].error), kErrInternal);
+            return;
+        }
+        for (uint32_t j = first; j <= cur; ++j) idx[off + j] = static_cast<uint32_t>(p);
+        if (p + 1 == e) {
+            const uint32_t nb = 1u << (32 - sh);
+            for (uint32_t j = cur + 1; j <= nb; ++j) idx[off + j] = static_cast<uint32_t>(e);
+        }
+    }
+}
+
 template <typename K>
 int resident_ctas(K kernel)
 {
@@ -864,22 +1001,23 @@ int resident_ctas(K kernel)
     return (per_sm > 0 ? per_sm : 1) * num_sms();
 }
 
-template <bool kFilter, bool kCsr>
+template <bool kFilter, bool kCsr, bool kMulti>
 Status run(const QueryArgs &a, cudaStream_t stream)
 {
     Status st;
-    const uint64_t nbatch = (a.P.n + 31) / 32;
+    const uint64_t nbatch = kMulti ? static_cast<uint64_t>(a.bt.num_tiles) * (kTilePoints / 32) : (a.P.n + 31) / 32;
     const uint64_t need = ceil_div(nbatch ? nbatch : 1, kWarps);
     static int grid_b = 0, grid_h = 0;
-    if (!grid_b) grid_b = resident_ctas(batch_kernel<kFilter, kCsr>);
-    if (!grid_h) grid_h = resident_ctas(heavy_kernel<kFilter, kCsr>);
+    if (!grid_b) grid_b = resident_ctas(batch_kernel<kFilter, kCsr, kMulti>);
+    if (!grid_h) grid_h = resident_ctas(heavy_kernel<kFilter, kCsr, kMulti>);
     const unsigned gb = static_cast<unsigned>(need < static_cast<uint64_t>(grid_b) ? need : grid_b);
-    batch_kernel<kFilter, kCsr><<<gb, kThreads, 0, stream>>>(a);
+    batch_kernel<kFilter, kCsr, kMulti><<<gb, kThreads, 0, stream>>>(a);
     RHG_LAUNCH_CHECK();
-    heavy_kernel<kFilter, kCsr><<<static_cast<unsigned>(grid_h), kThreads, 0, stream>>>(a);
+    heavy_kernel<kFilter, kCsr, kMulti><<<static_cast<unsigned>(grid_h), kThreads, 0, stream>>>(a);
     RHG_LAUNCH_CHECK();
     if (kFilter) {
-        recheck_kernel<kCsr><<<static_cast<unsigned>(num_sms() * 4), kThreads, 0, stream>>>(a);
+        if (kMulti) recheck_batch_kernel<<<static_cast<unsigned>(num_sms() * 4), kThreads, 0, stream>>>(a);
+        else recheck_kernel<kCsr><<<static_cast<unsigned>(num_sms() * 4), kThreads, 0, stream>>>(a);
         RHG_LAUNCH_CHECK();
     }
     return st;
@@ -897,9 +1035,22 @@ Status launch_query(const QueryArgs &a, bool csr, cudaStream_t stream)
                                                                                                 a.bidx, index_entries(a.P.n));
         RHG_LAUNCH_CHECK();
     }
-    st = csr ? run<true, true>(a, stream) : run<true, false>(a, stream);
+    st = csr ? run<true, true, false>(a, stream) : run<true, false, false>(a, stream);
     if (st.code) return st;
-    return csr ? run<false, true>(a, stream) : run<false, false>(a, stream);
+    return csr ? run<false, true, false>(a, stream) : run<false, false, false>(a, stream);
+}
+
+Status launch_query_batch(const QueryArgs &a, cudaStream_t stream)
+{
+    Status st;
+    if (!a.bt.num_tiles) return st;
+    bucket_index_batch_kernel<<<a.bt.num_tiles, kThreads, 0, stream>>>(a.M, a.bt, a.P.key, a.bidx);
+    RHG_LAUNCH_CHECK();
+    st = run<true, false, true>(a, stream);
+    if (st.code) return st;
+    reset_phase_kernel<<<1, 32, 0, stream>>>(a.M + a.bt.G);
+    RHG_LAUNCH_CHECK();
+    return run<false, false, true>(a, stream);
 }
 
 Status launch_csr_finish(const uint64_t *sorted_keys, uint64_t entries, uint64_t n, uint64_t *row_ptr,
