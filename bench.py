@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload measurement")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
     ap.add_argument("--k", type=float, default=WORKLOAD["k"])
     ap.add_argument("--alpha", type=float, default=WORKLOAD["alpha"])
@@ -204,6 +206,74 @@ def run_reference(args):
     return 0
 
 
+def batched_specs(count: int = 4096):
+    """The batched workload: graph j has seed 1000 + j, n = floor(10^U(3, 5)),
+    k uniform in 6..32, alpha uniform in [0.55, 1.5], drawn by numpy's PCG64 with
+    seed 4096 (the same list on every run)."""
+    import numpy as np
+    rng = np.random.default_rng(4096)
+    return [(int(10 ** rng.uniform(3, 5)), int(rng.integers(6, 33)), float(rng.uniform(0.55, 1.5)), 1000 + j)
+            for j in range(count)]
+
+
+def bench_batched(args, rhg, torch, stream):
+    """Edges/s of the batched path (one rhg_generate_batch call per step for all
+    graphs) against the plain path called once per graph on the same graphs."""
+    specs = batched_specs(args.batch_graphs)
+    params = rhg.batch_params(specs)
+    buf = rhg.allocate_batch(params)
+    rc, res, tot = rhg.run_batch(buf, stream)
+    if rc == rhg.OVERFLOW:
+        caps = [max(int(res[g].m), int(buf.offsets[g + 1] - buf.offsets[g])) for g in range(len(params))]
+        del buf
+        buf = rhg.allocate_batch(params, caps)
+        rc, res, tot = rhg.run_batch(buf, stream)
+    if rc != rhg.OK:
+        raise rhg.RhgError(rc, "rhg_generate_batch", tot)
+    for _ in range(max(args.warmup - 1, 0)):
+        rhg.run_batch(buf, stream)
+    timer = rhg.StageTimer()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with timer:
+        e0.record(stream)
+        for _ in range(args.steps):
+            timer.reset_marks()
+            rc, res, tot = rhg.run_batch(buf, stream)
+            timer.accumulate()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    m = int(tot.m)
+    points = sum(sp[0] for sp in specs)
+    del buf
+    # the plain path, one call per graph, reusing one workspace sized for the largest graph
+    big = max(specs, key=lambda sp: sp[0])
+    cap = max(int(r.m) for r in res) + 4096
+    wsp = rhg.allocate_pairs(rhg.make_params(*big), cap)
+    for sp in specs[:64]:
+        rhg.generate_pairs(*sp, workspace=wsp)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plain_m = 0
+    for sp in specs:
+        _, r = rhg.generate_pairs(*sp, workspace=wsp)
+        plain_m += int(r.m)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    del wsp
+    value = m / (ms / 1000.0)
+    plain = plain_m / (plain_ms / 1000.0)
+    return {"value": value, "unit": "edges/s", "ms_per_step": ms, "graphs": len(specs), "points": points,
+            "edges": m, "exact_edges_equal_plain": plain_m == m, "plain_per_graph_value": plain,
+            "plain_per_graph_ms": plain_ms, "speedup_vs_plain": value / plain,
+            "stages_ms": {s: timer.totals[s] / max(args.steps, 1) for s in rhg.STAGES if s != "csr"},
+            "workload": "batched: 4096 graphs, n log-uniform in [1e3, 1e5], k uniform in 6..32, alpha uniform "
+                        "in [0.55, 1.5], seeds 1000..5095 (numpy PCG64 seed 4096), FP32 filter + FP64 recheck, "
+                        "B = ceil(log2 n) per graph"}
+
+
 def replica_seed(seed: int, rank: int) -> int:
     """Replicas (one per GPU, no exchange) generate independent graphs: rank r
     uses seed + r."""
@@ -324,6 +394,11 @@ def run_ours(args):
                        "ms_per_step": 1000 * e2e_s,
                        "note": "parameters in, pairs out to pinned host memory; two metadata reads per call"}
         del host
+
+    if not args.no_batched:
+        del pairs
+        pairs = None
+        line["batched"] = bench_batched(args, rhg, torch, stream)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         del pairs
