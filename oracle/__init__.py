@@ -90,6 +90,10 @@ def lib() -> ctypes.CDLL:
             L.ro_prepared_count.argtypes = [_p, _p, _u64, _p]
             L.ro_prepared_count.restype = _i64
             L.ro_prepared_free.argtypes = [_p]
+            L.ro_asinh.restype = _dbl
+            L.ro_asinh.argtypes = [_dbl]
+            L.ro_draw_movement.argtypes = [_u64, _u64, _dbl, _dbl, _dbl, _dbl, _p, _p]
+            L.ro_move.argtypes = [_u64, _p, _p, _p, _p, _p, _dbl, _dbl]
             _lib = L
     return _lib
 
@@ -169,6 +173,33 @@ def sample_points(n: int, alpha: float, R: float, seed: int, first: int = 0):
     r = np.zeros(n, dtype=np.float64)
     lib().ro_sample_points(n, alpha, R, seed, first, _ptr(phi), _ptr(r))
     return phi, r
+
+
+def asinh(y: float) -> float:
+    """The dynamic model's deterministic asinh (y >= 0)."""
+    return lib().ro_asinh(float(y))
+
+
+def draw_movement(n: int, seed: int, phi_range=(-1.0, 1.0), r_range=(-10.0, 1.0)):
+    """Step values (tau_phi, tau_r) of nodes 0..n-1 (Sec. III-C); the default
+    ranges are those of the paper's experiment."""
+    tphi = np.zeros(n, dtype=np.float64)
+    tr = np.zeros(n, dtype=np.float64)
+    lib().ro_draw_movement(n, seed, float(phi_range[0]), float(phi_range[1]), float(r_range[0]),
+                           float(r_range[1]), _ptr(tphi), _ptr(tr))
+    return tphi, tr
+
+
+def move(ids, phi, r, tau_phi, tau_r, R: float, alpha: float):
+    """One movement step (rotation + Algorithm 2 radial movement with reflection)
+    of the nodes `ids`; returns new (phi, r, tau_r) arrays, the inputs unchanged."""
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    phi = np.array(phi, dtype=np.float64)
+    r = np.array(r, dtype=np.float64)
+    tau_r = np.array(tau_r, dtype=np.float64)
+    tau_phi = np.ascontiguousarray(tau_phi, dtype=np.float64)
+    lib().ro_move(len(ids), _ptr(ids), _ptr(phi), _ptr(r), _ptr(tau_phi), _ptr(tau_r), float(R), float(alpha))
+    return phi, r, tau_r
 
 
 def band_assign(r: np.ndarray, R: float, B: int, p: float = 0.9) -> np.ndarray:

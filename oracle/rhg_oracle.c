@@ -752,3 +752,84 @@ void ro_prepared_free(void *handle)
     ro_bands_free(&h->S);
     free(h);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Dynamic model (Sec. III-C; Algorithm 2, radial movement).                  */
+/*                                                                            */
+/* Step values of node i: Philox counter (i, 1, 0, 0), key (seed, 0), words    */
+/* x0, x1; U = (x >> 11) * 2^-53; tau_phi = lo_phi + (hi_phi - lo_phi) * U0,   */
+/* tau_r = lo_r + (hi_r - lo_r) * U1.                                         */
+/*                                                                            */
+/* One movement step of node i, in place:                                     */
+/*   rotation   p = phi + tau_phi, brought into [0, 2pi) by subtracting or     */
+/*              adding 2pi (a sum that rounds up to 2pi becomes the largest    */
+/*              double below 2pi);                                            */
+/*   radial     x = sinh(alpha r), y = x + tau_r; while y is outside           */
+/*              [0, sinh(alpha R)] the step is mirrored at the boundary it      */
+/*              crossed (y = 2 sinh(alpha R) - y, or y = -y) and tau_r changes  */
+/*              sign (the node bounces); r = asinh(y) / alpha (times 1/alpha),  */
+/*              at most R.                                                    */
+/*   asinh(y) = log(y + sqrt(y*y + 1)) for y >= 0, each operation rounded.     */
+/* ------------------------------------------------------------------------- */
+double ro_asinh(double y)
+{
+    double yy = y * y;
+    double t = yy + 1.0;
+    double s = sqrt(t);
+    double u = y + s;
+    return ro_log(u);
+}
+
+void ro_draw_movement(uint64_t n, uint64_t seed, double phi_lo, double phi_hi, double r_lo, double r_hi,
+                      double *tau_phi, double *tau_r)
+{
+    const double U53 = 0x1.0p-53;
+    double wphi = phi_hi - phi_lo, wr = r_hi - r_lo;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t ctr[4] = {i, 1, 0, 0}, key[2] = {seed, 0}, x[4];
+        ro_philox4x64(ctr, key, x);
+        double u0 = (double)(x[0] >> 11) * U53;
+        double u1 = (double)(x[1] >> 11) * U53;
+        double a = wphi * u0;
+        double b = wr * u1;
+        tau_phi[i] = phi_lo + a;
+        tau_r[i] = r_lo + b;
+    }
+}
+
+void ro_move(uint64_t count, const uint32_t *ids, double *phi, double *r, const double *tau_phi, double *tau_r,
+             double R, double alpha)
+{
+    double aR = alpha * R;
+    const double top = ro_sinh(aR);
+    const double inv_alpha = 1.0 / alpha;
+    const double below = nextafter(RO_TWO_PI, 0.0);
+    for (uint64_t j = 0; j < count; ++j) {
+        uint32_t i = ids[j];
+        double p = phi[i] + tau_phi[i];
+        for (int it = 0; it < 64 && p >= RO_TWO_PI; ++it) p = p - RO_TWO_PI;
+        for (int it = 0; it < 64 && p < 0.0; ++it) p = p + RO_TWO_PI;
+        if (p >= RO_TWO_PI) p = below;
+        if (p < 0.0) p = 0.0;
+        double tr = tau_r[i];
+        double ar = alpha * r[i];
+        double x = ro_sinh(ar);
+        double y = x + tr;
+        for (int it = 0; it < 64 && (y > top || y < 0.0); ++it) {
+            if (y > top) {
+                double t2 = top + top;
+                y = t2 - y;
+            } else {
+                y = -y;
+            }
+            tr = -tr;
+        }
+        if (y > top) y = top;
+        if (y < 0.0) y = 0.0;
+        double z = ro_asinh(y) * inv_alpha;
+        if (z > R) z = R;
+        phi[i] = p;
+        r[i] = z;
+        tau_r[i] = tr;
+    }
+}
