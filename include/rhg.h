@@ -267,9 +267,50 @@ int rhg_generate_batch(const rhg_params *graphs, uint32_t count, void *d_workspa
                        void *stream, rhg_batch_graph *results, rhg_result *totals);
 
 /*
+ * Dynamic model (Sec. III-C): vertices move in discrete steps, each a rotation
+ * phi + tau_phi (mod 2 pi) and the radial movement of Algorithm 2 in the
+ * coordinate sinh(alpha r): y = sinh(alpha r) + tau_r, mirrored at sinh(alpha R)
+ * or at 0 while outside (tau_r changes sign: the vertex bounces), then
+ * r = asinh(y) / alpha (at most R).  All FP64, in the fixed operation order of
+ * the library's deterministic functions.
+ *
+ * rhg_draw_movement -- step values of vertices 0 .. n-1 from Philox counter
+ * (i, 1, 0, 0), key (seed, 0): tau_phi uniform in [phi_lo, phi_hi), tau_r
+ * uniform in [r_lo, r_hi) (the paper's experiment: (-1, 1) and (-10, 1)).
+ *
+ * rhg_move_points -- one step of the `count` distinct vertices d_ids (ids < n)
+ * on the FP64 coordinates d_phi, d_r (by id, in place; the result of
+ * rhg_sample_points or of earlier steps), with step values d_tau_phi, d_tau_r
+ * (tau_r's sign flips are written back).  INVALID_ARG for count > n or an
+ * unusable R or alpha; ids at or above n are skipped.
+ *
+ * rhg_update_edges -- the edge list after a step, without generating the graph
+ * again: d_old_pairs (m_old pairs u < v, the graph of these points before the
+ * step, e.g. from rhg_edges_from_points or an earlier update) keeps the pairs
+ * whose endpoints both stayed; the moved vertices d_moved_ids (the ids given to
+ * rhg_move_points) are queried against all bands of the moved point set
+ * (d_phi, d_r after the step, disk radius R), and their pairs are added, each
+ * once.  The result in d_new_pairs (room for capacity_edges pairs, must not
+ * overlap d_old_pairs) is, as a set, the graph rhg_edges_from_points gives for
+ * the moved points.  Workspace: rhg_workspace_bytes_update(n, moved_count).
+ * result->m = exact edge count (OVERFLOW when above the capacity); INVALID_ARG
+ * when an id repeats or is out of range (detected on the device).
+ */
+int rhg_draw_movement(uint64_t n, uint64_t seed, double phi_lo, double phi_hi, double r_lo, double r_hi,
+                      double *d_tau_phi, double *d_tau_r, void *stream);
+int rhg_move_points(const uint32_t *d_ids, uint64_t count, uint64_t n, double *d_phi, double *d_r,
+                    const double *d_tau_phi, double *d_tau_r, double R, double alpha, void *stream);
+int rhg_workspace_bytes_update(uint64_t n, uint64_t moved_count, size_t *bytes);
+int rhg_update_edges(const double *d_phi, const double *d_r, uint64_t n, double R, uint32_t num_bands,
+                     double band_ratio, uint32_t flags, const uint32_t *d_moved_ids, uint64_t moved_count,
+                     const uint32_t *d_old_pairs, uint64_t m_old, void *d_workspace, size_t workspace_bytes,
+                     uint32_t *d_new_pairs, uint64_t capacity_edges, void *stream, rhg_result *result);
+
+/*
  * rhg_dm_eval -- the library's deterministic FP64 functions on a device array,
  * for verification against an independent implementation: fn = 0 exp, 1 log,
- * 2 cos, 3 cosh, 4 sinh.  d_out[i] = f(d_in[i]), i < count.
+ * 2 cos, 3 cosh, 4 sinh, 5 asinh (y >= 0; dynamic model).  d_out[i] = f(d_in[i]),
+ * i < count.
  */
 int rhg_dm_eval(int fn, const double *d_in, double *d_out, uint64_t count, void *stream);
 

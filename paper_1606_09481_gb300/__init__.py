@@ -24,7 +24,7 @@ OK, INVALID_ARG, NO_SOLUTION, OOM, CUDA_ERROR, TIMEOUT, OVERFLOW = range(7)
 FLAG_FP64_ONLY = 0x1
 FLAG_VERIFY = 0x2
 MAX_BANDS = 64
-DM_FUNCS = {"exp": 0, "log": 1, "cos": 2, "cosh": 3, "sinh": 4}
+DM_FUNCS = {"exp": 0, "log": 1, "cos": 2, "cosh": 3, "sinh": 4, "asinh": 5}
 
 _c_u64, _c_u32, _c_dbl, _c_size, _p = (ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                        ctypes.c_size_t, ctypes.c_void_p)
@@ -86,6 +86,11 @@ def load() -> ctypes.CDLL:
     L.rhg_batch_workspace_bytes.argtypes = [ctypes.POINTER(Params), _c_u32, ctypes.POINTER(_c_size)]
     L.rhg_generate_batch.argtypes = [ctypes.POINTER(Params), _c_u32, _p, _c_size, _p, ctypes.POINTER(_c_u64), _p,
                                      ctypes.POINTER(BatchGraph), ctypes.POINTER(Result)]
+    L.rhg_draw_movement.argtypes = [_c_u64, _c_u64, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _p, _p, _p]
+    L.rhg_move_points.argtypes = [_p, _c_u64, _c_u64, _p, _p, _p, _p, _c_dbl, _c_dbl, _p]
+    L.rhg_workspace_bytes_update.argtypes = [_c_u64, _c_u64, ctypes.POINTER(_c_size)]
+    L.rhg_update_edges.argtypes = [_p, _p, _c_u64, _c_dbl, _c_u32, _c_dbl, _c_u32, _p, _c_u64, _p, _c_u64, _p, _c_size,
+                                   _p, _c_u64, _p, ctypes.POINTER(Result)]
     L.rhg_generate_pairs_host.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _c_u64, _p, _c_u64, _p,
                                           ctypes.POINTER(Result)]
     L.rhg_generate_csr.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _p, _c_u64, _p,
@@ -398,6 +403,56 @@ def edges_from_points(phi, r, R, num_bands=0, band_ratio=0.0, flags=0, capacity=
             break
         cap = int(res.m)
     _check(rc, "rhg_edges_from_points", res)
+    return out[: 2 * res.m].view(-1, 2), res
+
+
+# ------------------------------------------------------------------- dynamic model
+def draw_movement(n, seed, phi_range=(-1.0, 1.0), r_range=(-10.0, 1.0), stream=None):
+    """Step values (tau_phi, tau_r) of vertices 0..n-1 as float64 CUDA tensors;
+    the default ranges are the paper's experiment."""
+    torch = _torch()
+    tphi = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    tr = torch.empty_like(tphi)
+    _check(load().rhg_draw_movement(n, seed, float(phi_range[0]), float(phi_range[1]), float(r_range[0]),
+                                    float(r_range[1]), tphi.data_ptr(), tr.data_ptr(), _stream(stream)),
+           "rhg_draw_movement")
+    return tphi[:n], tr[:n]
+
+
+def move_points(ids, phi, r, tau_phi, tau_r, R, alpha, stream=None):
+    """One movement step of the vertices `ids` (int32 CUDA tensor of distinct ids),
+    in place on the float64 CUDA tensors phi, r and tau_r."""
+    n = int(phi.numel())
+    _check(load().rhg_move_points(ids.data_ptr(), int(ids.numel()), n, phi.data_ptr(), r.data_ptr(),
+                                  tau_phi.data_ptr(), tau_r.data_ptr(), float(R), float(alpha), _stream(stream)),
+           "rhg_move_points")
+
+
+def update_edges(phi, r, R, moved_ids, old_pairs, num_bands=0, band_ratio=0.0, flags=0, capacity=None,
+                 stream=None):
+    """The edge list after a movement step (rhg_update_edges): old_pairs is the
+    (m, 2) int32 CUDA tensor of the graph before the step, phi / r the positions
+    after it, moved_ids the moved vertices.  Returns ((m', 2) pairs, Result)."""
+    torch = _torch()
+    n = int(phi.numel())
+    cnt = int(moved_ids.numel())
+    nb = _c_size(0)
+    L = load()
+    _check(L.rhg_workspace_bytes_update(n, cnt, ctypes.byref(nb)), "rhg_workspace_bytes_update")
+    ws = _empty_bytes(nb.value)
+    old = old_pairs.contiguous()
+    m_old = int(old.shape[0]) if old.numel() else 0
+    cap = capacity if capacity is not None else m_old + m_old // 4 + 4096
+    for _ in range(2):
+        out = torch.empty(max(2 * cap, 2), dtype=torch.int32, device="cuda")
+        res = Result()
+        rc = L.rhg_update_edges(phi.data_ptr(), r.data_ptr(), n, float(R), num_bands, float(band_ratio), flags,
+                                moved_ids.data_ptr() if cnt else None, cnt, old.data_ptr() if m_old else None, m_old,
+                                ws.data_ptr(), ws.numel(), out.data_ptr(), cap, _stream(stream), ctypes.byref(res))
+        if rc != OVERFLOW:
+            break
+        cap = int(res.m)
+    _check(rc, "rhg_update_edges", res)
     return out[: 2 * res.m].view(-1, 2), res
 
 

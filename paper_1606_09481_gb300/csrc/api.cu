@@ -179,10 +179,9 @@ int bits_for(uint64_t v)
 
 enum class Output { Pairs, Csr };
 
-// One full pass of the hot path on the stream: plan, points, bands, sort, gather,
-// range query (+ heavy chunks + FP64 rechecks).  No host synchronisation.
-Status enqueue(const Pipeline &pl, const PlanArgs &pa, const double *phi_in, const double *r_in, Output kind,
-               uint32_t *d_pairs, uint64_t capacity_edges, uint32_t heavy_min, cudaStream_t stream)
+// The point pipeline on the stream: plan, points, bands, sort, gather.
+Status enqueue_points(const Pipeline &pl, const PlanArgs &pa, const double *phi_in, const double *r_in,
+                      SortedPoints *P_out, cudaStream_t stream)
 {
     Status st;
     Meta *M = pl.meta();
@@ -213,6 +212,19 @@ Status enqueue(const Pipeline &pl, const PlanArgs &pa, const double *phi_in, con
     st = launch_gather(M, pl.n, pa.seed, ks, is, phi_in, r_in, phi_in ? r_in : rid, P, stream);
     if (st.code) return st;
     mark(RHG_STAGE_GATHER, true, stream);
+    *P_out = P;
+    return st;
+}
+
+// One full pass of the hot path on the stream: the point pipeline, then the range
+// query (+ heavy chunks + FP64 rechecks).  No host synchronisation.
+Status enqueue(const Pipeline &pl, const PlanArgs &pa, const double *phi_in, const double *r_in, Output kind,
+               uint32_t *d_pairs, uint64_t capacity_edges, uint32_t heavy_min, cudaStream_t stream)
+{
+    SortedPoints P;
+    Status st = enqueue_points(pl, pa, phi_in, r_in, &P, stream);
+    if (st.code) return st;
+    Meta *M = pl.meta();
     QueryArgs q{};
     q.M = M;
     q.P = P;
@@ -512,6 +524,35 @@ Status enqueue_batch(void *ws, const BatchLayout &L, const BatchHost &h, uint32_
     return launch_batch_results(metas, h.G, at<uint4>(ws, L.results), stream);
 }
 
+// ------------------------------------------------------------------ dynamic
+// Workspace of rhg_update_edges: the point pipeline of the moved points, then
+// the moved flags (by id and by sorted position), the moved vertices' sorted
+// positions, their pair counts, offsets and the scan's block sums.
+struct UpdateLayout {
+    Layout L;
+    size_t moved_id, moved_pos, owners, counts, offsets, scan_tmp, total;
+};
+
+UpdateLayout update_layout(uint64_t n, uint64_t moved)
+{
+    UpdateLayout U{};
+    U.L = make_layout(n, 0);
+    size_t o = U.L.total;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    U.moved_id = take(n);
+    U.moved_pos = take(n);
+    U.owners = take(moved * 4);
+    U.counts = take(moved * 4);
+    U.offsets = take((moved + 1) * 8);
+    U.scan_tmp = take(scan_temp_bytes(moved));
+    U.total = o;
+    return U;
+}
+
 // Scratch of rhg_generate_pairs_static: one array per device, found by symbol.
 constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_static_scratch[RHG_STATIC_SCRATCH_BYTES];
@@ -809,9 +850,102 @@ int rhg_generate_batch(const rhg_params *graphs, uint32_t count, void *d_workspa
     return rc;
 }
 
+int rhg_draw_movement(uint64_t n, uint64_t seed, double phi_lo, double phi_hi, double r_lo, double r_hi,
+                      double *d_tau_phi, double *d_tau_r, void *stream)
+{
+    if (n && (!d_tau_phi || !d_tau_r)) return RHG_ERR_INVALID_ARG;
+    if (!std::isfinite(phi_lo) || !std::isfinite(phi_hi) || !std::isfinite(r_lo) || !std::isfinite(r_hi) ||
+        phi_hi < phi_lo || r_hi < r_lo)
+        return RHG_ERR_INVALID_ARG;
+    return launch_draw_movement(n, seed, phi_lo, phi_hi, r_lo, r_hi, d_tau_phi, d_tau_r,
+                                static_cast<cudaStream_t>(stream))
+        .code;
+}
+
+int rhg_move_points(const uint32_t *d_ids, uint64_t count, uint64_t n, double *d_phi, double *d_r,
+                    const double *d_tau_phi, double *d_tau_r, double R, double alpha, void *stream)
+{
+    if (count && (!d_ids || !d_phi || !d_r || !d_tau_phi || !d_tau_r)) return RHG_ERR_INVALID_ARG;
+    if (count > n || n > 0xFFFFFFFFull) return RHG_ERR_INVALID_ARG;
+    if (!(R > 0.0) || !(R <= 700.0) || !(alpha > 0.5) || !(alpha <= 100.0) || alpha * R > 700.0)
+        return RHG_ERR_INVALID_ARG;
+    return launch_move(d_ids, count, n, d_phi, d_r, d_tau_phi, d_tau_r, R, alpha, static_cast<cudaStream_t>(stream))
+        .code;
+}
+
+int rhg_workspace_bytes_update(uint64_t n, uint64_t moved_count, size_t *bytes)
+{
+    if (!bytes || n < 1 || n > 0xFFFFFFFFull || moved_count > n) return RHG_ERR_INVALID_ARG;
+    *bytes = update_layout(n, moved_count).total;
+    return RHG_OK;
+}
+
+int rhg_update_edges(const double *d_phi, const double *d_r, uint64_t n, double R, uint32_t num_bands,
+                     double band_ratio, uint32_t flags, const uint32_t *d_moved_ids, uint64_t moved_count,
+                     const uint32_t *d_old_pairs, uint64_t m_old, void *d_workspace, size_t workspace_bytes,
+                     uint32_t *d_new_pairs, uint64_t capacity_edges, void *stream, rhg_result *result)
+{
+    if (result) std::memset(result, 0, sizeof(*result));
+    if (n < 1 || n > 0xFFFFFFFFull || !d_phi || !d_r || !d_workspace) return RHG_ERR_INVALID_ARG;
+    if (!(R > 0.0) || !(R <= 700.0) || num_bands > RHG_MAX_BANDS) return RHG_ERR_INVALID_ARG;
+    if (band_ratio < 0.0 || !std::isfinite(band_ratio) || (flags & ~RHG_FLAG_FP64_ONLY)) return RHG_ERR_INVALID_ARG;
+    if (moved_count > n || (moved_count && !d_moved_ids) || (m_old && !d_old_pairs)) return RHG_ERR_INVALID_ARG;
+    if (capacity_edges && (!d_new_pairs || (reinterpret_cast<uintptr_t>(d_new_pairs) & 7))) return RHG_ERR_INVALID_ARG;
+    if (m_old && (reinterpret_cast<uintptr_t>(d_old_pairs) & 7)) return RHG_ERR_INVALID_ARG;
+    if (m_old && capacity_edges && d_new_pairs == d_old_pairs) return RHG_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_workspace) & 255) return RHG_ERR_INVALID_ARG;
+    const UpdateLayout U = update_layout(n, moved_count);
+    if (workspace_bytes < U.total) return RHG_ERR_OOM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint32_t B = num_bands ? num_bands : default_bands(n < 2 ? 2 : n);
+    const double ratio = band_ratio > 0.0 ? band_ratio : 0.9;
+    const PlanArgs pa{n, 1.0, 1.0, 0, B, ratio, R, (flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u, 0u};
+    Pipeline pl{d_workspace, U.L, n};
+    Meta *M = pl.meta();
+    SortedPoints P;
+    Status st = enqueue_points(pl, pa, d_phi, d_r, &P, s);
+    if (st.code) return finish(st, result);
+    QueryArgs q{};
+    q.M = M;
+    q.P = P;
+    q.src_phi = d_phi;
+    q.src_r = d_r;
+    q.pairs = d_new_pairs;
+    q.capacity = capacity_edges;
+    q.bidx = at<uint32_t>(d_workspace, U.L.bidx);
+    uint8_t *moved_id = at<uint8_t>(d_workspace, U.moved_id), *moved_pos = at<uint8_t>(d_workspace, U.moved_pos);
+    uint32_t *owners = at<uint32_t>(d_workspace, U.owners), *counts = at<uint32_t>(d_workspace, U.counts);
+    uint64_t *offsets = at<uint64_t>(d_workspace, U.offsets);
+    // the plan zeroed both counters: work_counter lists the moved vertices, m the kept edges
+    unsigned long long *owner_n = reinterpret_cast<unsigned long long *>(&M->work_counter);
+    unsigned long long *kept = reinterpret_cast<unsigned long long *>(&M->m);
+    mark(RHG_STAGE_QUERY, false, s);
+    if (!st.code) st = launch_bucket_index(q, s);
+    if (!st.code) st = launch_mark_moved(d_moved_ids, moved_count, n, moved_id, s);
+    if (!st.code) st = launch_owners(M, P.id, n, moved_id, moved_pos, owners, moved_count, owner_n, s);
+    if (!st.code)
+        st = launch_subset_query(q, owners, moved_count, owner_n, moved_pos, counts, nullptr, nullptr, 0, false, s);
+    if (!st.code) st = launch_scan(counts, moved_count, offsets, at<void>(d_workspace, U.scan_tmp), s);
+    if (!st.code) st = launch_keep_old(d_old_pairs, m_old, moved_id, n, d_new_pairs, capacity_edges, kept, s);
+    if (!st.code)
+        st = launch_subset_query(q, owners, moved_count, owner_n, moved_pos, counts, offsets, kept, capacity_edges,
+                                 true, s);
+    if (!st.code) st = launch_add_total(kept, offsets + moved_count, s);
+    if (st.code) return finish(st, result);
+    mark(RHG_STAGE_QUERY, true, s);
+    Meta h;
+    st = read_meta(M, &h, s);
+    if (st.code) return finish(st, result);
+    fill_result(result, h);
+    if (h.error) return error_from_meta(h.error);
+    if (h.work_counter != moved_count) return RHG_ERR_INVALID_ARG;  // an id repeated or out of range
+    if (h.m > capacity_edges) return RHG_ERR_OVERFLOW;
+    return RHG_OK;
+}
+
 int rhg_dm_eval(int fn, const double *d_in, double *d_out, uint64_t count, void *stream)
 {
-    if (fn < 0 || fn > 4 || (count && (!d_in || !d_out))) return RHG_ERR_INVALID_ARG;
+    if (fn < 0 || fn > 5 || (count && (!d_in || !d_out))) return RHG_ERR_INVALID_ARG;
     if (!count) return RHG_OK;
     const Status st = launch_dm_eval(fn, d_in, d_out, count, static_cast<cudaStream_t>(stream));
     return st.code;

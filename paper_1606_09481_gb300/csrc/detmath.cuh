@@ -137,5 +137,12 @@ __device__ __forceinline__ double sinh(double x)
     return mul(sub(e, div(1.0, e)), 0.5);
 }
 
+// asinh(y) for y >= 0 (dynamic model, Algorithm 2): log(y + sqrt(y*y + 1)).
+__device__ __forceinline__ double asinh(double y)
+{
+    const double t = add(mul(y, y), 1.0);
+    return log(add(y, __dsqrt_rn(t)));
+}
+
 }  // namespace dm
 }  // namespace rhg

@@ -462,7 +462,8 @@ __global__ void dm_eval_kernel(int fn, const double *in, double *out, uint64_t c
             case 1: y = dm::log(x); break;
             case 2: y = dm::cos(x); break;
             case 3: y = dm::cosh(x); break;
-            default: y = dm::sinh(x); break;
+            case 4: y = dm::sinh(x); break;
+            default: y = dm::asinh(x); break;
         }
         out[i] = y;
     }

@@ -903,6 +903,136 @@ __global__ void reset_phase_kernel(Meta *C)
     }
 }
 
+// ------------------------------------------------------------------ subset query
+// Neighbours of the moved vertices (dynamic model, Sec. III-C), for the update of
+// an edge list: one warp per moved vertex v (sorted position owners[j]) and every
+// band, inward and outward (the window of Sec. III-B at the band's inner radius
+// bounds every band).  A pair (v, w) counts when w is not v and either w did not
+// move or id_v < id_w (a pair of two moved vertices once).  Filter mode decides
+// undecided pairs with the FP64 predicate on the spot; FP64 mode tests every
+// candidate with it.  kEmit = false writes the count of vertex j; kEmit = true
+// writes its pairs from *base + offsets[j] (pairs past the capacity are skipped).
+struct SubsetArgs {
+    const uint32_t *owners;
+    uint64_t count;                          // entries of counts / offsets
+    const unsigned long long *owners_found;  // owners listed on the device (<= count when ids repeat)
+    const uint8_t *moved_by_pos;
+    uint32_t *counts;
+    const uint64_t *offsets;
+    const unsigned long long *base;
+    uint64_t capacity;
+};
+
+template <bool kFilter>
+__device__ __forceinline__ bool subset_test(const QueryArgs &a, const Meta *M, float4 va, float4 vb, double phv,
+                                            double chv, double shv, uint32_t idv, uint32_t q, double coshR)
+{
+    if (kFilter) {
+        const int dec = filter_decide(va, vb, a.P.ang[q], a.P.pms[q]);
+        if (dec != 2) return dec == 1;
+        double pw, cw, sw;
+        fp64_point(a, M, a.P.id[q], pw, cw, sw);
+        return predicate_L(phv, chv, shv, pw, cw, sw) <= coshR;
+    }
+    return predicate_L(phv, chv, shv, a.P.phi[q], a.P.ch[q], a.P.sh[q]) <= coshR;
+}
+
+template <bool kFilter, bool kEmit>
+__global__ void __launch_bounds__(kThreads) subset_kernel(QueryArgs a, SubsetArgs sa)
+{
+    __shared__ BandShared S;
+    Meta *M = a.M;
+    load_bands(S, M);
+    __syncthreads();
+    if (M->error || (M->filter != 0) != kFilter) return;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t B = M->B;
+    const double coshR = M->coshR;
+    const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
+    const uint64_t found_n = *sa.owners_found < sa.count ? *sa.owners_found : sa.count;
+    for (uint64_t j = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32; j < sa.count; j += warps) {
+        if (j >= found_n) {  // not listed: no pairs
+            if (!kEmit && lane == 0) sa.counts[j] = 0;
+            continue;
+        }
+        const uint32_t p = sa.owners[j];
+        const uint32_t idv = a.P.id[p];
+        const uint32_t akv = a.P.akey[p];
+        OwnerRegs mine{};
+        float4 va = make_float4(0, 0, 0, 0), vb = va;
+        double phv, chv, shv;
+        if (kFilter) {
+            const float2 an = a.P.ang[p];
+            const float4 q = a.P.pms[p];
+            mine.P = q.x;
+            mine.M = q.y;
+            mine.S2 = 2.0f * q.z;
+            mine.PM = q.x + q.y;
+            mine.gam = q.w;
+            va = make_float4(an.x, an.y, q.x, q.y);
+            vb = make_float4(mine.S2, mine.PM, kCBase + q.w, 0.0f);
+            fp64_point(a, M, idv, phv, chv, shv);
+        } else {
+            phv = a.P.phi[p];
+            mine.r = a.P.r[p];
+            chv = mine.ch = a.P.ch[p];
+            shv = mine.sh = a.P.sh[p];
+        }
+        uint64_t out = 0;
+        if (kEmit) out = *sa.base + sa.offsets[j];
+        uint32_t found = 0;
+        for (uint32_t i = 0; i < B; ++i) {
+            const uint32_t s = S.start[i], e = S.start[i + 1];
+            if (s == e) continue;
+            const uint32_t Wf = kFilter ? window_filter(mine, S, i) : window_fp64(mine, S, i, coshR);
+            const bool plain = Wf < kFull && Wf <= akv && akv + Wf >= akv;
+            uint32_t f0, f1, f2, f3, c0 = 0, c1 = 0;
+            if (plain) {
+                int64_t Wc = -1;
+                if (kFilter) Wc = window_core(mine, S, i);
+                const uint32_t wc = Wc < 0 ? 0u : (Wc >= static_cast<int64_t>(Wf) ? Wf : static_cast<uint32_t>(Wc));
+                search4_indexed(a.P.akey, a.bidx + S.ioff[i], S.ishift[i], akv - Wf, akv + Wf, akv - wc, akv + wc,
+                                f0, f3, c0, c1);
+                if (Wc < 0) {
+                    c0 = c1 = f3;
+                    f1 = f2 = f3;
+                } else {
+                    f1 = c0;
+                    f2 = c1;
+                }
+            } else {
+                key_ranges(a.P.akey, s, e, akv, Wf, f0, f1, f2, f3);
+            }
+            // three pieces: [f0, f1) and [f2, f3) tested, [c0, c1) certain
+            for (int piece = 0; piece < 3; ++piece) {
+                const uint32_t lo = piece == 0 ? f0 : (piece == 1 ? c0 : f2);
+                const uint32_t hi = piece == 0 ? f1 : (piece == 1 ? c1 : f3);
+                for (uint32_t q0 = lo; q0 < hi; q0 += 32) {
+                    const uint32_t q = q0 + lane;
+                    bool edge = false;
+                    uint32_t idw = 0;
+                    if (q < hi && q != p) {
+                        const bool wm = sa.moved_by_pos[q] != 0;
+                        if (wm || kEmit) idw = a.P.id[q];
+                        if (!wm || idv < idw)
+                            edge = piece == 1 ||
+                                   subset_test<kFilter>(a, M, va, vb, phv, chv, shv, idv, q, coshR);
+                    }
+                    const uint32_t word = __ballot_sync(full, edge);
+                    if (kEmit && edge) {
+                        const uint64_t at = out + found + __popc(word & lt);
+                        if (at < sa.capacity) write_edge<false>(a, at, idv, idw);
+                    }
+                    found += __popc(word);
+                }
+            }
+        }
+        if (!kEmit && lane == 0) sa.counts[j] = found;
+    }
+}
+
 // --------------------------------------------------------------------- CSR finish
 // row_ptr[r] = first entry of row r in keys sorted by (row, col); col = low words.
 __global__ void csr_finish_kernel(const uint64_t *keys, uint64_t entries, uint64_t n, uint64_t *row_ptr,
@@ -1051,6 +1181,43 @@ Status launch_query_batch(const QueryArgs &a, cudaStream_t stream)
     reset_phase_kernel<<<1, 32, 0, stream>>>(a.M + a.bt.G);
     RHG_LAUNCH_CHECK();
     return run<false, false, true>(a, stream);
+}
+
+Status launch_bucket_index(const QueryArgs &a, cudaStream_t stream)
+{
+    Status st;
+    if (a.P.n) {
+        const uint64_t g = ceil_div(a.P.n, kThreads);
+        const uint64_t cap = static_cast<uint64_t>(num_sms()) * 8;
+        bucket_index_kernel<<<static_cast<unsigned>(g < cap ? g : cap), kThreads, 0, stream>>>(a.M, a.P.key, a.P.n,
+                                                                                                a.bidx, index_entries(a.P.n));
+        RHG_LAUNCH_CHECK();
+    }
+    return st;
+}
+
+Status launch_subset_query(const QueryArgs &a, const uint32_t *owners, uint64_t count,
+                           const unsigned long long *owners_found, const uint8_t *moved_by_pos, uint32_t *counts,
+                           const uint64_t *offsets, const unsigned long long *base, uint64_t capacity, bool emit,
+                           cudaStream_t stream)
+{
+    Status st;
+    if (!count) return st;
+    const SubsetArgs sa{owners, count, owners_found, moved_by_pos, counts, offsets, base, capacity};
+    const uint64_t need = ceil_div(count, kWarps);
+    const uint64_t cap = static_cast<uint64_t>(num_sms()) * 8;
+    const unsigned g = static_cast<unsigned>(need < cap ? need : cap);
+    if (emit) {
+        subset_kernel<true, true><<<g, kThreads, 0, stream>>>(a, sa);
+        RHG_LAUNCH_CHECK();
+        subset_kernel<false, true><<<g, kThreads, 0, stream>>>(a, sa);
+    } else {
+        subset_kernel<true, false><<<g, kThreads, 0, stream>>>(a, sa);
+        RHG_LAUNCH_CHECK();
+        subset_kernel<false, false><<<g, kThreads, 0, stream>>>(a, sa);
+    }
+    RHG_LAUNCH_CHECK();
+    return st;
 }
 
 Status launch_csr_finish(const uint64_t *sorted_keys, uint64_t entries, uint64_t n, uint64_t *row_ptr,

@@ -18,10 +18,12 @@ def _inputs(fn, seed=0):
     if fn == "cos":
         return np.concatenate([rng.uniform(0, 2 * np.pi, 50000), rng.uniform(0, 1e-6, 2000),
                                np.linspace(0, 2 * np.pi, 4097)])
+    if fn == "asinh":
+        return np.concatenate([10.0 ** rng.uniform(-8, 35, 40000), rng.uniform(0, 10, 10000), [0.0, 1.0, 1e-300]])
     return np.concatenate([rng.uniform(0, 60, 40000), rng.uniform(0, 0.6, 10000), [0.0, 0.5, 0.4999999999]])
 
 
-@pytest.mark.parametrize("fn", ["exp", "log", "cos", "cosh", "sinh"])
+@pytest.mark.parametrize("fn", ["exp", "log", "cos", "cosh", "sinh", "asinh"])
 def test_dm_bitwise(O, fn):
     rhg = require_gpu()
     import torch
