@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload measurement")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--no-served", action="store_true", help="skip the served-workload measurement")
+    ap.add_argument("--no-dynamic", action="store_true", help="skip the dynamic-model measurement")
+    ap.add_argument("--moved", type=float, default=0.12, help="fraction of vertices moved per dynamic step")
     ap.add_argument("--served-requests", type=int, default=400, help="requests per arrival rate")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
     ap.add_argument("--k", type=float, default=WORKLOAD["k"])
@@ -314,6 +316,78 @@ def bench_served(args, rhg, torch):
                         "seed 5) at 0.25..4x the plain path's capacity; 120 GB admission budget, 4 workers"}
 
 
+def bench_dynamic(args, rhg, torch, stream):
+    """Dynamic model at the plain workload's size: one step = move a fraction of
+    the vertices (rotation + Algorithm 2) and update the edge list from the
+    previous one (rhg_update_edges), against generating the graph of the moved
+    points again (rhg_edges_from_points).  Buffers are allocated once."""
+    L = rhg.load()
+    n, k, alpha = args.n, args.k, args.alpha
+    phi, r, R = rhg.sample_points(n, k, alpha, args.seed)
+    cap = rhg.estimate_capacity(n, k)
+    nb = ctypes.c_size_t(0)
+    L.rhg_workspace_bytes_points(n, 0, ctypes.byref(nb))
+    ws_full = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    cnt = int(args.moved * n)
+    L.rhg_workspace_bytes_update(n, cnt, 0, ctypes.byref(nb))
+    ws_upd = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    bufs = [torch.empty(2 * cap, dtype=torch.int32, device="cuda") for _ in range(2)]
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    res = rhg.Result()
+
+    def full(out):
+        rc = L.rhg_edges_from_points(phi.data_ptr(), r.data_ptr(), n, R, 0, 0.0, 0, ws_full.data_ptr(),
+                                     ws_full.numel(), out.data_ptr(), cap, sptr, ctypes.byref(res))
+        rhg._check(rc, "rhg_edges_from_points", res)
+        return int(res.m)
+
+    m = full(bufs[0])
+    tphi, tr = rhg.draw_movement(n, args.seed)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(args.seed)
+    steps = []
+    for _ in range(args.warmup + args.steps):
+        steps.append(torch.sort(torch.randperm(n, device="cuda", generator=gen)[:cnt]).values.to(torch.int32))
+    cur = 0
+
+    def update(ids, src, dst, m_old):
+        L.rhg_move_points(ids.data_ptr(), cnt, n, phi.data_ptr(), r.data_ptr(), tphi.data_ptr(), tr.data_ptr(), R,
+                          alpha, sptr)
+        rc = L.rhg_update_edges(phi.data_ptr(), r.data_ptr(), n, R, 0, 0.0, 0, ids.data_ptr(), cnt, src.data_ptr(),
+                                m_old, ws_upd.data_ptr(), ws_upd.numel(), dst.data_ptr(), cap, sptr,
+                                ctypes.byref(res))
+        rhg._check(rc, "rhg_update_edges", res)
+        return int(res.m)
+
+    for i in range(args.warmup):
+        m = update(steps[i], bufs[cur], bufs[1 - cur], m)
+        cur = 1 - cur
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        m = update(steps[args.warmup + i], bufs[cur], bufs[1 - cur], m)
+        cur = 1 - cur
+    e1.record(stream)
+    torch.cuda.synchronize()
+    upd_ms = e0.elapsed_time(e1) / args.steps
+    # the same final positions generated from scratch
+    e0.record(stream)
+    for _ in range(args.steps):
+        m_full = full(bufs[1 - cur])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    full_ms = e0.elapsed_time(e1) / args.steps
+    same = m_full == m
+    del ws_full, ws_upd, bufs
+    return {"moved_fraction": args.moved, "moved_per_step": cnt, "edges": m, "update_ms": upd_ms,
+            "regenerate_ms": full_ms, "update_edges_per_s": m / (upd_ms / 1000.0),
+            "speedup_vs_regenerate": full_ms / upd_ms, "edge_count_equals_regeneration": same,
+            "workload": f"dynamic: n={n}, k={k}, alpha={alpha}, seed {args.seed}; per step {args.moved:.0%} of the "
+                        "vertices (uniform random, torch generator) move with tau_phi in (-1, 1), tau_r in (-10, 1) "
+                        "(Philox); step = move + update of the previous edge list"}
+
+
 def replica_seed(seed: int, rank: int) -> int:
     """Replicas (one per GPU, no exchange) generate independent graphs: rank r
     uses seed + r."""
@@ -439,6 +513,10 @@ def run_ours(args):
         del pairs
         pairs = None
         line["batched"] = bench_batched(args, rhg, torch, stream)
+
+    if not args.no_dynamic:
+        pairs = None
+        line["dynamic"] = bench_dynamic(args, rhg, torch, stream)
 
     if not args.no_served:
         pairs = None

@@ -292,7 +292,8 @@ int rhg_generate_batch(const rhg_params *graphs, uint32_t count, void *d_workspa
  * (d_phi, d_r after the step, disk radius R), and their pairs are added, each
  * once.  The result in d_new_pairs (room for capacity_edges pairs, must not
  * overlap d_old_pairs) is, as a set, the graph rhg_edges_from_points gives for
- * the moved points.  Workspace: rhg_workspace_bytes_update(n, moved_count).
+ * the moved points.  Workspace: rhg_workspace_bytes_update(n, moved_count,
+ * num_bands) (num_bands 0: the default, as in rhg_update_edges).
  * result->m = exact edge count (OVERFLOW when above the capacity); INVALID_ARG
  * when an id repeats or is out of range (detected on the device).
  */
@@ -300,7 +301,7 @@ int rhg_draw_movement(uint64_t n, uint64_t seed, double phi_lo, double phi_hi, d
                       double *d_tau_phi, double *d_tau_r, void *stream);
 int rhg_move_points(const uint32_t *d_ids, uint64_t count, uint64_t n, double *d_phi, double *d_r,
                     const double *d_tau_phi, double *d_tau_r, double R, double alpha, void *stream);
-int rhg_workspace_bytes_update(uint64_t n, uint64_t moved_count, size_t *bytes);
+int rhg_workspace_bytes_update(uint64_t n, uint64_t moved_count, uint32_t num_bands, size_t *bytes);
 int rhg_update_edges(const double *d_phi, const double *d_r, uint64_t n, double R, uint32_t num_bands,
                      double band_ratio, uint32_t flags, const uint32_t *d_moved_ids, uint64_t moved_count,
                      const uint32_t *d_old_pairs, uint64_t m_old, void *d_workspace, size_t workspace_bytes,

@@ -88,7 +88,7 @@ def load() -> ctypes.CDLL:
                                      ctypes.POINTER(BatchGraph), ctypes.POINTER(Result)]
     L.rhg_draw_movement.argtypes = [_c_u64, _c_u64, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _p, _p, _p]
     L.rhg_move_points.argtypes = [_p, _c_u64, _c_u64, _p, _p, _p, _p, _c_dbl, _c_dbl, _p]
-    L.rhg_workspace_bytes_update.argtypes = [_c_u64, _c_u64, ctypes.POINTER(_c_size)]
+    L.rhg_workspace_bytes_update.argtypes = [_c_u64, _c_u64, _c_u32, ctypes.POINTER(_c_size)]
     L.rhg_update_edges.argtypes = [_p, _p, _c_u64, _c_dbl, _c_u32, _c_dbl, _c_u32, _p, _c_u64, _p, _c_u64, _p, _c_size,
                                    _p, _c_u64, _p, ctypes.POINTER(Result)]
     L.rhg_generate_pairs_host.argtypes = [ctypes.POINTER(Params), _p, _c_size, _p, _c_u64, _p, _c_u64, _p,
@@ -438,7 +438,7 @@ def update_edges(phi, r, R, moved_ids, old_pairs, num_bands=0, band_ratio=0.0, f
     cnt = int(moved_ids.numel())
     nb = _c_size(0)
     L = load()
-    _check(L.rhg_workspace_bytes_update(n, cnt, ctypes.byref(nb)), "rhg_workspace_bytes_update")
+    _check(L.rhg_workspace_bytes_update(n, cnt, num_bands, ctypes.byref(nb)), "rhg_workspace_bytes_update")
     ws = _empty_bytes(nb.value)
     old = old_pairs.contiguous()
     m_old = int(old.shape[0]) if old.numel() else 0

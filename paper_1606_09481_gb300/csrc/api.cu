@@ -3,6 +3,7 @@
 //   plan -> sample -> band offsets -> radix sort -> gather -> query count ->
 //   scan -> (one 64-byte D2H of the metadata) -> query emit [-> CSR sort/finish].
 #include <atomic>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -530,10 +531,11 @@ Status enqueue_batch(void *ws, const BatchLayout &L, const BatchHost &h, uint32_
 // positions, their pair counts, offsets and the scan's block sums.
 struct UpdateLayout {
     Layout L;
-    size_t moved_id, moved_pos, owners, counts, offsets, scan_tmp, total;
+    size_t moved_id, moved_bits, moved_pos, owners, counts, offsets, scan_tmp, chunks, total;
+    uint64_t chunk_cap;
 };
 
-UpdateLayout update_layout(uint64_t n, uint64_t moved)
+UpdateLayout update_layout(uint64_t n, uint64_t moved, uint32_t B)
 {
     UpdateLayout U{};
     U.L = make_layout(n, 0);
@@ -543,12 +545,16 @@ UpdateLayout update_layout(uint64_t n, uint64_t moved)
         o = align_up(o + bytes);
         return at;
     };
+    U.chunk_cap = 2 * moved + 65536;
+    const uint64_t slots = moved * B + U.chunk_cap;
     U.moved_id = take(n);
+    U.moved_bits = take(ceil_div(n, 32) * 4);
     U.moved_pos = take(n);
     U.owners = take(moved * 4);
-    U.counts = take(moved * 4);
-    U.offsets = take((moved + 1) * 8);
-    U.scan_tmp = take(scan_temp_bytes(moved));
+    U.counts = take(slots * 4);
+    U.offsets = take((slots + 1) * 8);
+    U.scan_tmp = take(scan_temp_bytes(slots));
+    U.chunks = take(U.chunk_cap * 16);
     U.total = o;
     return U;
 }
@@ -873,10 +879,11 @@ int rhg_move_points(const uint32_t *d_ids, uint64_t count, uint64_t n, double *d
         .code;
 }
 
-int rhg_workspace_bytes_update(uint64_t n, uint64_t moved_count, size_t *bytes)
+int rhg_workspace_bytes_update(uint64_t n, uint64_t moved_count, uint32_t num_bands, size_t *bytes)
 {
-    if (!bytes || n < 1 || n > 0xFFFFFFFFull || moved_count > n) return RHG_ERR_INVALID_ARG;
-    *bytes = update_layout(n, moved_count).total;
+    if (!bytes || n < 1 || n > 0xFFFFFFFFull || moved_count > n || num_bands > RHG_MAX_BANDS)
+        return RHG_ERR_INVALID_ARG;
+    *bytes = update_layout(n, moved_count, num_bands ? num_bands : default_bands(n < 2 ? 2 : n)).total;
     return RHG_OK;
 }
 
@@ -894,10 +901,10 @@ int rhg_update_edges(const double *d_phi, const double *d_r, uint64_t n, double 
     if (m_old && (reinterpret_cast<uintptr_t>(d_old_pairs) & 7)) return RHG_ERR_INVALID_ARG;
     if (m_old && capacity_edges && d_new_pairs == d_old_pairs) return RHG_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(d_workspace) & 255) return RHG_ERR_INVALID_ARG;
-    const UpdateLayout U = update_layout(n, moved_count);
+    const uint32_t B = num_bands ? num_bands : default_bands(n < 2 ? 2 : n);
+    const UpdateLayout U = update_layout(n, moved_count, B);
     if (workspace_bytes < U.total) return RHG_ERR_OOM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const uint32_t B = num_bands ? num_bands : default_bands(n < 2 ? 2 : n);
     const double ratio = band_ratio > 0.0 ? band_ratio : 0.9;
     const PlanArgs pa{n, 1.0, 1.0, 0, B, ratio, R, (flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u, 0u};
     Pipeline pl{d_workspace, U.L, n};
@@ -916,21 +923,29 @@ int rhg_update_edges(const double *d_phi, const double *d_r, uint64_t n, double 
     uint8_t *moved_id = at<uint8_t>(d_workspace, U.moved_id), *moved_pos = at<uint8_t>(d_workspace, U.moved_pos);
     uint32_t *owners = at<uint32_t>(d_workspace, U.owners), *counts = at<uint32_t>(d_workspace, U.counts);
     uint64_t *offsets = at<uint64_t>(d_workspace, U.offsets);
-    // the plan zeroed both counters: work_counter lists the moved vertices, m the kept edges
+    // the plan zeroed these counters: work_counter lists the moved vertices, m the
+    // kept edges, and heavy_n with heavy_next (one 64-bit word) the chunks
     unsigned long long *owner_n = reinterpret_cast<unsigned long long *>(&M->work_counter);
     unsigned long long *kept = reinterpret_cast<unsigned long long *>(&M->m);
+    unsigned long long *chunk_n = reinterpret_cast<unsigned long long *>(&M->heavy_n);
+    static_assert(offsetof(Meta, heavy_next) == offsetof(Meta, heavy_n) + 4 && offsetof(Meta, heavy_n) % 8 == 0,
+                  "heavy_n and heavy_next form one aligned 64-bit word");
+    uint4 *chunks = at<uint4>(d_workspace, U.chunks);
+    const uint64_t slots = moved_count * B + U.chunk_cap;
     mark(RHG_STAGE_QUERY, false, s);
     if (!st.code) st = launch_bucket_index(q, s);
-    if (!st.code) st = launch_mark_moved(d_moved_ids, moved_count, n, moved_id, s);
+    uint32_t *moved_bits = at<uint32_t>(d_workspace, U.moved_bits);
+    if (!st.code) st = launch_mark_moved(d_moved_ids, moved_count, n, moved_id, moved_bits, s);
     if (!st.code) st = launch_owners(M, P.id, n, moved_id, moved_pos, owners, moved_count, owner_n, s);
     if (!st.code)
-        st = launch_subset_query(q, owners, moved_count, owner_n, moved_pos, counts, nullptr, nullptr, 0, false, s);
-    if (!st.code) st = launch_scan(counts, moved_count, offsets, at<void>(d_workspace, U.scan_tmp), s);
-    if (!st.code) st = launch_keep_old(d_old_pairs, m_old, moved_id, n, d_new_pairs, capacity_edges, kept, s);
+        st = launch_subset_query(q, owners, moved_count, owner_n, chunks, U.chunk_cap, chunk_n, moved_pos, counts,
+                                 nullptr, nullptr, 0, false, s);
+    if (!st.code) st = launch_scan(counts, slots, offsets, at<void>(d_workspace, U.scan_tmp), s);
+    if (!st.code) st = launch_keep_old(d_old_pairs, m_old, moved_bits, n, d_new_pairs, capacity_edges, kept, s);
     if (!st.code)
-        st = launch_subset_query(q, owners, moved_count, owner_n, moved_pos, counts, offsets, kept, capacity_edges,
-                                 true, s);
-    if (!st.code) st = launch_add_total(kept, offsets + moved_count, s);
+        st = launch_subset_query(q, owners, moved_count, owner_n, chunks, U.chunk_cap, chunk_n, moved_pos, counts,
+                                 offsets, kept, capacity_edges, true, s);
+    if (!st.code) st = launch_add_total(kept, offsets + slots, s);
     if (st.code) return finish(st, result);
     mark(RHG_STAGE_QUERY, true, s);
     Meta h;

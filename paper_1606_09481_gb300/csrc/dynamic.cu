@@ -78,11 +78,24 @@ __global__ void fill_u8_kernel(uint8_t *a, uint64_t count, uint8_t v)
         a[j] = v;
 }
 
-__global__ void mark_kernel(const uint32_t *ids, uint64_t count, uint64_t n, uint8_t *moved_by_id)
+__global__ void mark_kernel(const uint32_t *ids, uint64_t count, uint64_t n, uint8_t *moved_by_id,
+                            uint32_t *moved_bits)
+{
+    for (uint64_t j = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; j < count;
+         j += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t i = ids[j];
+        if (i < n) {
+            moved_by_id[i] = 1;
+            atomicOr(moved_bits + (i >> 5), 1u << (i & 31));
+        }
+    }
+}
+
+__global__ void fill_u32_kernel(uint32_t *a, uint64_t count)
 {
     for (uint64_t j = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; j < count;
          j += static_cast<uint64_t>(gridDim.x) * blockDim.x)
-        if (ids[j] < n) moved_by_id[ids[j]] = 1;
+        a[j] = 0;
 }
 
 // Moved flag by sorted position, and the sorted positions of the moved vertices
@@ -192,37 +205,52 @@ __global__ void __launch_bounds__(kThreads) scan_apply_kernel(const uint32_t *in
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[count] = sums[gridDim.x];
 }
 
-// The old edges whose endpoints both stayed, appended through the counter (one
-// atomic per block); pairs past the capacity are counted but not written.
+// The old edges whose endpoints both stayed (moved ids as a bitset), appended
+// through the counter with one atomic per block and kKeepItems pairs per thread
+// in flight; pairs past the capacity are counted but not written.
+constexpr int kKeepItems = 4;
+
 __global__ void __launch_bounds__(kThreads) keep_old_kernel(const uint2 *old_pairs, uint64_t m_old,
-                                                            const uint8_t *moved_by_id, uint64_t n, uint2 *out,
+                                                            const uint32_t *moved_bits, uint64_t n, uint2 *out,
                                                             uint64_t cap, unsigned long long *counter)
 {
     __shared__ uint32_t warp_cnt[kThreads / 32];
     __shared__ unsigned long long block_base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * kThreads; base < m_old;
-         base += static_cast<uint64_t>(gridDim.x) * kThreads) {
-        const uint64_t j = base + threadIdx.x;
-        uint2 e = make_uint2(0, 0);
-        bool keep = false;
-        if (j < m_old) {
-            e = old_pairs[j];
-            keep = e.x < n && e.y < n && !moved_by_id[e.x] && !moved_by_id[e.y];
+    constexpr uint64_t kSpan = static_cast<uint64_t>(kThreads) * kKeepItems;
+    for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * kSpan; base < m_old;
+         base += static_cast<uint64_t>(gridDim.x) * kSpan) {
+        uint2 e[kKeepItems];
+        bool keep[kKeepItems];
+        uint32_t b[kKeepItems], mine = 0;
+#pragma unroll
+        for (int t = 0; t < kKeepItems; ++t) {  // pair base + t * kThreads + threadIdx.x (coalesced)
+            const uint64_t j = base + static_cast<uint64_t>(t) * kThreads + threadIdx.x;
+            e[t] = j < m_old ? old_pairs[j] : make_uint2(0xffffffffu, 0xffffffffu);
         }
-        const uint32_t b = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) warp_cnt[warp] = __popc(b);
+#pragma unroll
+        for (int t = 0; t < kKeepItems; ++t) {
+            keep[t] = e[t].x < n && e[t].y < n && !((__ldg(moved_bits + (e[t].x >> 5)) >> (e[t].x & 31)) & 1u) &&
+                      !((__ldg(moved_bits + (e[t].y >> 5)) >> (e[t].y & 31)) & 1u);
+            b[t] = __ballot_sync(0xffffffffu, keep[t]);
+            mine += __popc(b[t]);
+        }
+        if (lane == 0) warp_cnt[warp] = mine;
         __syncthreads();
         if (threadIdx.x == 0) {
-            uint32_t t = 0;
-            for (int w = 0; w < kThreads / 32; ++w) t += warp_cnt[w];
-            block_base = t ? atomicAdd(counter, static_cast<unsigned long long>(t)) : 0ull;
+            uint32_t tot = 0;
+            for (int w = 0; w < kThreads / 32; ++w) tot += warp_cnt[w];
+            block_base = tot ? atomicAdd(counter, static_cast<unsigned long long>(tot)) : 0ull;
         }
         __syncthreads();
-        uint32_t before = 0;
-        for (int w = 0; w < warp; ++w) before += warp_cnt[w];
-        const uint64_t at = block_base + before + __popc(b & ((1u << lane) - 1u));
-        if (keep && at < cap) out[at] = e;
+        uint64_t at = block_base;
+        for (int w = 0; w < warp; ++w) at += warp_cnt[w];
+#pragma unroll
+        for (int t = 0; t < kKeepItems; ++t) {
+            const uint64_t pos = at + __popc(b[t] & ((1u << lane) - 1u));
+            if (keep[t] && pos < cap) out[pos] = e[t];
+            at += __popc(b[t]);
+        }
         __syncthreads();
     }
 }
@@ -255,13 +283,16 @@ Status launch_move(const uint32_t *ids, uint64_t count, uint64_t n, double *phi,
     return st;
 }
 
-Status launch_mark_moved(const uint32_t *ids, uint64_t count, uint64_t n, uint8_t *moved_by_id, cudaStream_t stream)
+Status launch_mark_moved(const uint32_t *ids, uint64_t count, uint64_t n, uint8_t *moved_by_id,
+                         uint32_t *moved_bits, cudaStream_t stream)
 {
     Status st;
     fill_u8_kernel<<<grid(n), kThreads, 0, stream>>>(moved_by_id, n, 0);
     RHG_LAUNCH_CHECK();
+    fill_u32_kernel<<<grid(ceil_div(n, 32)), kThreads, 0, stream>>>(moved_bits, ceil_div(n, 32));
+    RHG_LAUNCH_CHECK();
     if (count) {
-        mark_kernel<<<grid(count), kThreads, 0, stream>>>(ids, count, n, moved_by_id);
+        mark_kernel<<<grid(count), kThreads, 0, stream>>>(ids, count, n, moved_by_id, moved_bits);
         RHG_LAUNCH_CHECK();
     }
     return st;
@@ -293,14 +324,14 @@ Status launch_scan(const uint32_t *in, uint64_t count, uint64_t *out, void *temp
     return st;
 }
 
-Status launch_keep_old(const uint32_t *old_pairs, uint64_t m_old, const uint8_t *moved_by_id, uint64_t n,
+Status launch_keep_old(const uint32_t *old_pairs, uint64_t m_old, const uint32_t *moved_bits, uint64_t n,
                        uint32_t *out, uint64_t cap, unsigned long long *counter, cudaStream_t stream)
 {
     Status st;
     if (!m_old) return st;
-    keep_old_kernel<<<grid(m_old, 16), kThreads, 0, stream>>>(reinterpret_cast<const uint2 *>(old_pairs), m_old,
-                                                              moved_by_id, n, reinterpret_cast<uint2 *>(out), cap,
-                                                              counter);
+    keep_old_kernel<<<grid(ceil_div(m_old, kKeepItems), 8), kThreads, 0, stream>>>(
+        reinterpret_cast<const uint2 *>(old_pairs), m_old, moved_bits, n, reinterpret_cast<uint2 *>(out), cap,
+        counter);
     RHG_LAUNCH_CHECK();
     return st;
 }

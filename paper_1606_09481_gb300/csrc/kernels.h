@@ -122,9 +122,11 @@ Status launch_query_batch(const QueryArgs &a, cudaStream_t stream);
 // Bucket index alone (the subset query needs it without the full query).
 Status launch_bucket_index(const QueryArgs &a, cudaStream_t stream);
 // Neighbours of the moved vertices (dynamic model): counts (emit = false) or
-// pairs at *base + offsets[j] (emit = true); see subset_kernel.
+// pairs at *base + offsets[slot] (emit = true); counts / offsets hold count * B
+// (vertex, band) slots, then chunk_cap chunk slots; see subset_kernel.
 Status launch_subset_query(const QueryArgs &a, const uint32_t *owners, uint64_t count,
-                           const unsigned long long *owners_found, const uint8_t *moved_by_pos, uint32_t *counts,
+                           const unsigned long long *owners_found, uint4 *chunks, uint64_t chunk_cap,
+                           unsigned long long *chunk_n, const uint8_t *moved_by_pos, uint32_t *counts,
                            const uint64_t *offsets, const unsigned long long *base, uint64_t capacity, bool emit,
                            cudaStream_t stream);
 // CSR row pointers from directed keys sorted by (row, col); col = low words.
@@ -136,14 +138,15 @@ Status launch_draw_movement(uint64_t n, uint64_t seed, double phi_lo, double phi
                             double *tau_phi, double *tau_r, cudaStream_t stream);
 Status launch_move(const uint32_t *ids, uint64_t count, uint64_t n, double *phi, double *r, const double *tau_phi,
                    double *tau_r, double R, double alpha, cudaStream_t stream);
-Status launch_mark_moved(const uint32_t *ids, uint64_t count, uint64_t n, uint8_t *moved_by_id, cudaStream_t stream);
+Status launch_mark_moved(const uint32_t *ids, uint64_t count, uint64_t n, uint8_t *moved_by_id,
+                         uint32_t *moved_bits, cudaStream_t stream);
 Status launch_owners(const Meta *M, const uint32_t *sorted_ids, uint64_t n, const uint8_t *moved_by_id,
                      uint8_t *moved_by_pos, uint32_t *owners, uint64_t cap, unsigned long long *counter,
                      cudaStream_t stream);
 size_t scan_temp_bytes(uint64_t count);
 // out[0..count) = exclusive prefix sums of in, out[count] = the total
 Status launch_scan(const uint32_t *in, uint64_t count, uint64_t *out, void *temp, cudaStream_t stream);
-Status launch_keep_old(const uint32_t *old_pairs, uint64_t m_old, const uint8_t *moved_by_id, uint64_t n,
+Status launch_keep_old(const uint32_t *old_pairs, uint64_t m_old, const uint32_t *moved_bits, uint64_t n,
                        uint32_t *out, uint64_t cap, unsigned long long *counter, cudaStream_t stream);
 Status launch_add_total(unsigned long long *m, const uint64_t *total, cudaStream_t stream);
 

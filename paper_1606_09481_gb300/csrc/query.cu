@@ -905,17 +905,23 @@ __global__ void reset_phase_kernel(Meta *C)
 
 // ------------------------------------------------------------------ subset query
 // Neighbours of the moved vertices (dynamic model, Sec. III-C), for the update of
-// an edge list: one warp per moved vertex v (sorted position owners[j]) and every
+// an edge list: moved vertex v (sorted position owners[j]) against every
 // band, inward and outward (the window of Sec. III-B at the band's inner radius
 // bounds every band).  A pair (v, w) counts when w is not v and either w did not
 // move or id_v < id_w (a pair of two moved vertices once).  Filter mode decides
 // undecided pairs with the FP64 predicate on the spot; FP64 mode tests every
 // candidate with it.  kEmit = false writes the count of vertex j; kEmit = true
 // writes its pairs from *base + offsets[j] (pairs past the capacity are skipped).
+constexpr uint32_t kSubsetPiece = 64;     // longer pieces become chunks
+constexpr uint32_t kSubsetChunk = 4096;   // candidates per chunk
+
 struct SubsetArgs {
     const uint32_t *owners;
-    uint64_t count;                          // entries of counts / offsets
+    uint64_t count;                          // moved vertices; counts / offsets slots 0 .. count - 1
     const unsigned long long *owners_found;  // owners listed on the device (<= count when ids repeat)
+    uint4 *chunks;                           // {owner index, lo, hi, certain}; slots count + c
+    uint64_t chunk_cap;
+    unsigned long long *chunk_n;
     const uint8_t *moved_by_pos;
     uint32_t *counts;
     const uint64_t *offsets;
@@ -923,20 +929,25 @@ struct SubsetArgs {
     uint64_t capacity;
 };
 
+// The pair (v at sorted position p, w at q).  Filter mode: the FP32 filter, and
+// the FP64 predicate (both points recomputed) when it cannot decide.
 template <bool kFilter>
-__device__ __forceinline__ bool subset_test(const QueryArgs &a, const Meta *M, float4 va, float4 vb, double phv,
-                                            double chv, double shv, uint32_t idv, uint32_t q, double coshR)
+__device__ __forceinline__ bool subset_test(const QueryArgs &a, const Meta *M, float4 va, float4 vb, uint32_t p,
+                                            uint32_t q, double coshR)
 {
     if (kFilter) {
         const int dec = filter_decide(va, vb, a.P.ang[q], a.P.pms[q]);
         if (dec != 2) return dec == 1;
-        double pw, cw, sw;
+        double pv, cv, sv, pw, cw, sw;
+        fp64_point(a, M, a.P.id[p], pv, cv, sv);
         fp64_point(a, M, a.P.id[q], pw, cw, sw);
-        return predicate_L(phv, chv, shv, pw, cw, sw) <= coshR;
+        return predicate_L(pv, cv, sv, pw, cw, sw) <= coshR;
     }
-    return predicate_L(phv, chv, shv, a.P.phi[q], a.P.ch[q], a.P.sh[q]) <= coshR;
+    return predicate_L(a.P.phi[p], a.P.ch[p], a.P.sh[p], a.P.phi[q], a.P.ch[q], a.P.sh[q]) <= coshR;
 }
 
+// One thread per (moved vertex, band): slot t = j * B + i of counts / offsets.
+// Its pairs are written contiguously from its offset.
 template <bool kFilter, bool kEmit>
 __global__ void __launch_bounds__(kThreads) subset_kernel(QueryArgs a, SubsetArgs sa)
 {
@@ -945,16 +956,17 @@ __global__ void __launch_bounds__(kThreads) subset_kernel(QueryArgs a, SubsetArg
     load_bands(S, M);
     __syncthreads();
     if (M->error || (M->filter != 0) != kFilter) return;
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
     const uint32_t B = M->B;
     const double coshR = M->coshR;
-    const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
     const uint64_t found_n = *sa.owners_found < sa.count ? *sa.owners_found : sa.count;
-    for (uint64_t j = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32; j < sa.count; j += warps) {
-        if (j >= found_n) {  // not listed: no pairs
-            if (!kEmit && lane == 0) sa.counts[j] = 0;
+    const uint64_t slots = sa.count * B;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < slots; t += stride) {
+        const uint64_t j = t / B;
+        const uint32_t i = static_cast<uint32_t>(t - j * B);
+        const uint32_t s = S.start[i], e = S.start[i + 1];
+        if (j >= found_n || s == e) {  // not listed, or an empty band: no pairs
+            if (!kEmit) sa.counts[t] = 0;
             continue;
         }
         const uint32_t p = sa.owners[j];
@@ -962,7 +974,6 @@ __global__ void __launch_bounds__(kThreads) subset_kernel(QueryArgs a, SubsetArg
         const uint32_t akv = a.P.akey[p];
         OwnerRegs mine{};
         float4 va = make_float4(0, 0, 0, 0), vb = va;
-        double phv, chv, shv;
         if (kFilter) {
             const float2 an = a.P.ang[p];
             const float4 q = a.P.pms[p];
@@ -973,63 +984,120 @@ __global__ void __launch_bounds__(kThreads) subset_kernel(QueryArgs a, SubsetArg
             mine.gam = q.w;
             va = make_float4(an.x, an.y, q.x, q.y);
             vb = make_float4(mine.S2, mine.PM, kCBase + q.w, 0.0f);
-            fp64_point(a, M, idv, phv, chv, shv);
         } else {
-            phv = a.P.phi[p];
             mine.r = a.P.r[p];
-            chv = mine.ch = a.P.ch[p];
-            shv = mine.sh = a.P.sh[p];
+            mine.ch = a.P.ch[p];
+            mine.sh = a.P.sh[p];
         }
         uint64_t out = 0;
-        if (kEmit) out = *sa.base + sa.offsets[j];
+        if (kEmit) out = *sa.base + sa.offsets[t];
         uint32_t found = 0;
-        for (uint32_t i = 0; i < B; ++i) {
-            const uint32_t s = S.start[i], e = S.start[i + 1];
-            if (s == e) continue;
-            const uint32_t Wf = kFilter ? window_filter(mine, S, i) : window_fp64(mine, S, i, coshR);
-            const bool plain = Wf < kFull && Wf <= akv && akv + Wf >= akv;
-            uint32_t f0, f1, f2, f3, c0 = 0, c1 = 0;
-            if (plain) {
-                int64_t Wc = -1;
-                if (kFilter) Wc = window_core(mine, S, i);
-                const uint32_t wc = Wc < 0 ? 0u : (Wc >= static_cast<int64_t>(Wf) ? Wf : static_cast<uint32_t>(Wc));
-                search4_indexed(a.P.akey, a.bidx + S.ioff[i], S.ishift[i], akv - Wf, akv + Wf, akv - wc, akv + wc,
-                                f0, f3, c0, c1);
-                if (Wc < 0) {
-                    c0 = c1 = f3;
-                    f1 = f2 = f3;
-                } else {
-                    f1 = c0;
-                    f2 = c1;
-                }
+        const uint32_t Wf = kFilter ? window_filter(mine, S, i) : window_fp64(mine, S, i, coshR);
+        const bool plain = Wf < kFull && Wf <= akv && akv + Wf >= akv;
+        uint32_t f0, f1, f2, f3, c0 = 0, c1 = 0;
+        if (plain) {
+            int64_t Wc = -1;
+            if (kFilter) Wc = window_core(mine, S, i);
+            const uint32_t wc = Wc < 0 ? 0u : (Wc >= static_cast<int64_t>(Wf) ? Wf : static_cast<uint32_t>(Wc));
+            search4_indexed(a.P.akey, a.bidx + S.ioff[i], S.ishift[i], akv - Wf, akv + Wf, akv - wc, akv + wc, f0,
+                            f3, c0, c1);
+            if (Wc < 0) {
+                c0 = c1 = f3;
+                f1 = f2 = f3;
             } else {
-                key_ranges(a.P.akey, s, e, akv, Wf, f0, f1, f2, f3);
+                f1 = c0;
+                f2 = c1;
             }
-            // three pieces: [f0, f1) and [f2, f3) tested, [c0, c1) certain
-            for (int piece = 0; piece < 3; ++piece) {
-                const uint32_t lo = piece == 0 ? f0 : (piece == 1 ? c0 : f2);
-                const uint32_t hi = piece == 0 ? f1 : (piece == 1 ? c1 : f3);
-                for (uint32_t q0 = lo; q0 < hi; q0 += 32) {
-                    const uint32_t q = q0 + lane;
-                    bool edge = false;
-                    uint32_t idw = 0;
-                    if (q < hi && q != p) {
-                        const bool wm = sa.moved_by_pos[q] != 0;
-                        if (wm || kEmit) idw = a.P.id[q];
-                        if (!wm || idv < idw)
-                            edge = piece == 1 ||
-                                   subset_test<kFilter>(a, M, va, vb, phv, chv, shv, idv, q, coshR);
+        } else {
+            key_ranges(a.P.akey, s, e, akv, Wf, f0, f1, f2, f3);
+        }
+        // three pieces: [f0, f1) and [f2, f3) tested, [c0, c1) certain; long
+        // pieces go to the chunk list (once, in the counting pass)
+        for (int piece = 0; piece < 3; ++piece) {
+            const uint32_t lo = piece == 0 ? f0 : (piece == 1 ? c0 : f2);
+            const uint32_t hi = piece == 0 ? f1 : (piece == 1 ? c1 : f3);
+            if (hi > lo && hi - lo > kSubsetPiece) {
+                if (!kEmit) {
+                    const uint32_t nc = (hi - lo + kSubsetChunk - 1) / kSubsetChunk;
+                    const unsigned long long at = atomicAdd(sa.chunk_n, static_cast<unsigned long long>(nc));
+                    for (uint32_t u = 0; u < nc; ++u) {
+                        if (at + u >= sa.chunk_cap) {
+                            atomicMax(&M->error, kErrListFull);
+                            break;
+                        }
+                        const uint32_t c0q = lo + u * kSubsetChunk;
+                        sa.chunks[at + u] = make_uint4(static_cast<uint32_t>(j), c0q,
+                                                       hi - c0q > kSubsetChunk ? c0q + kSubsetChunk : hi,
+                                                       piece == 1 ? 1u : 0u);
                     }
-                    const uint32_t word = __ballot_sync(full, edge);
-                    if (kEmit && edge) {
-                        const uint64_t at = out + found + __popc(word & lt);
-                        if (at < sa.capacity) write_edge<false>(a, at, idv, idw);
-                    }
-                    found += __popc(word);
                 }
+                continue;
+            }
+            for (uint32_t q = lo; q < hi; ++q) {
+                if (q == p) continue;
+                const bool wm = sa.moved_by_pos[q] != 0;
+                const uint32_t idw = (wm || kEmit) ? a.P.id[q] : 0u;
+                if (wm && idw < idv) continue;  // a pair of moved vertices once
+                if (piece != 1 && !subset_test<kFilter>(a, M, va, vb, p, q, coshR)) continue;
+                if (kEmit && out + found < sa.capacity) write_edge<false>(a, out + found, idv, idw);
+                ++found;
             }
         }
-        if (!kEmit && lane == 0) sa.counts[j] = found;
+        if (!kEmit) sa.counts[t] = found;
+    }
+}
+
+// Chunks of long pieces: one warp per chunk, the candidates over the lanes; the
+// chunk's count and pairs use slot count + c of counts / offsets.
+template <bool kFilter, bool kEmit>
+__global__ void __launch_bounds__(kThreads) subset_chunk_kernel(QueryArgs a, SubsetArgs sa)
+{
+    Meta *M = a.M;
+    if (M->error || (M->filter != 0) != kFilter) return;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const double coshR = M->coshR;
+    const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
+    const uint64_t nch = *sa.chunk_n < sa.chunk_cap ? *sa.chunk_n : sa.chunk_cap;
+    for (uint64_t c = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32; c < sa.chunk_cap;
+         c += warps) {
+        const uint64_t slot = sa.count * M->B + c;
+        if (c >= nch) {  // unused slot
+            if (!kEmit && lane == 0) sa.counts[slot] = 0;
+            continue;
+        }
+        const uint4 h = sa.chunks[c];  // {owner index, lo, hi, 1 = certain}
+        const uint32_t p = sa.owners[h.x];
+        const uint32_t idv = a.P.id[p];
+        float4 va = make_float4(0, 0, 0, 0), vb = va;
+        if (kFilter) {
+            const float2 an = a.P.ang[p];
+            const float4 q = a.P.pms[p];
+            va = make_float4(an.x, an.y, q.x, q.y);
+            vb = make_float4(2.0f * q.z, q.x + q.y, kCBase + q.w, 0.0f);
+        }
+        uint64_t out = 0;
+        if (kEmit) out = *sa.base + sa.offsets[slot];
+        uint32_t found = 0;
+        for (uint32_t q0 = h.y; q0 < h.z; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            bool edge = false;
+            uint32_t idw = 0;
+            if (q < h.z && q != p) {
+                const bool wm = sa.moved_by_pos[q] != 0;
+                if (wm || kEmit) idw = a.P.id[q];
+                if (!wm || idv < idw)
+                    edge = h.w != 0 || subset_test<kFilter>(a, M, va, vb, p, q, coshR);
+            }
+            const uint32_t word = __ballot_sync(full, edge);
+            if (kEmit && edge) {
+                const uint64_t at = out + found + __popc(word & lt);
+                if (at < sa.capacity) write_edge<false>(a, at, idv, idw);
+            }
+            found += __popc(word);
+        }
+        if (!kEmit && lane == 0) sa.counts[slot] = found;
     }
 }
 
@@ -1197,24 +1265,34 @@ Status launch_bucket_index(const QueryArgs &a, cudaStream_t stream)
 }
 
 Status launch_subset_query(const QueryArgs &a, const uint32_t *owners, uint64_t count,
-                           const unsigned long long *owners_found, const uint8_t *moved_by_pos, uint32_t *counts,
+                           const unsigned long long *owners_found, uint4 *chunks, uint64_t chunk_cap,
+                           unsigned long long *chunk_n, const uint8_t *moved_by_pos, uint32_t *counts,
                            const uint64_t *offsets, const unsigned long long *base, uint64_t capacity, bool emit,
                            cudaStream_t stream)
 {
-    Status st;
-    if (!count) return st;
-    const SubsetArgs sa{owners, count, owners_found, moved_by_pos, counts, offsets, base, capacity};
-    const uint64_t need = ceil_div(count, kWarps);
-    const uint64_t cap = static_cast<uint64_t>(num_sms()) * 8;
+    Status st;  // launched even for no moved vertex: the counting pass clears the chunk slots
+    const SubsetArgs sa{owners, count, owners_found, chunks, chunk_cap, chunk_n, moved_by_pos, counts, offsets, base,
+                        capacity};
+    const uint64_t need = ceil_div(count ? count * kMaxBands : 1, kThreads);
+    const uint64_t cap = static_cast<uint64_t>(num_sms()) * 16;
     const unsigned g = static_cast<unsigned>(need < cap ? need : cap);
+    const unsigned gw = static_cast<unsigned>(num_sms() * 4);
     if (emit) {
         subset_kernel<true, true><<<g, kThreads, 0, stream>>>(a, sa);
         RHG_LAUNCH_CHECK();
         subset_kernel<false, true><<<g, kThreads, 0, stream>>>(a, sa);
+        RHG_LAUNCH_CHECK();
+        subset_chunk_kernel<true, true><<<gw, kThreads, 0, stream>>>(a, sa);
+        RHG_LAUNCH_CHECK();
+        subset_chunk_kernel<false, true><<<gw, kThreads, 0, stream>>>(a, sa);
     } else {
         subset_kernel<true, false><<<g, kThreads, 0, stream>>>(a, sa);
         RHG_LAUNCH_CHECK();
         subset_kernel<false, false><<<g, kThreads, 0, stream>>>(a, sa);
+        RHG_LAUNCH_CHECK();
+        subset_chunk_kernel<true, false><<<gw, kThreads, 0, stream>>>(a, sa);
+        RHG_LAUNCH_CHECK();
+        subset_chunk_kernel<false, false><<<gw, kThreads, 0, stream>>>(a, sa);
     }
     RHG_LAUNCH_CHECK();
     return st;
