@@ -35,8 +35,9 @@ constexpr int kPlanThreads = 256;  // grid points j = 0..255 of the bracket sear
 __device__ void plan_block(Meta *M, const PlanArgs &a)
 {
     __shared__ int jstar;
-    __shared__ double R_sh;
-    __shared__ int fail;
+    __shared__ double R_sh, lo_sh, hi_sh;
+    __shared__ int fail, walk_done;
+    __shared__ uint8_t above[kPlanThreads];  // node t of a round's tree: kbar(its midpoint) > k
     const int t = threadIdx.x;
     const double nd = static_cast<double>(a.n);
     const double alpha = a.alpha, k = a.k;
@@ -51,20 +52,61 @@ __device__ void plan_block(Meta *M, const PlanArgs &a)
         if (kbar(static_cast<double>(t), nd, alpha) > k) atomicMax(&jstar, t);
         __syncthreads();
         if (t == 0) {
-            if (jstar < 0 || jstar == kPlanThreads - 1) {
-                fail = 1;
-            } else {
-                // binary search: kbar(lo) > k >= kbar(hi) until lo, hi are adjacent
-                double lo = static_cast<double>(jstar), hi = static_cast<double>(jstar + 1);
-                for (int it = 0; it < 200; ++it) {
+            fail = (jstar < 0 || jstar == kPlanThreads - 1) ? 1 : 0;
+            walk_done = fail;
+            lo_sh = static_cast<double>(jstar);
+            hi_sh = static_cast<double>(jstar + 1);
+        }
+        __syncthreads();
+        // binary search: mid = (lo + hi) / 2, kbar(mid) > k ? lo = mid : hi = mid, until
+        // lo and hi are adjacent (at most 200 steps); R = hi.  Each round takes eight
+        // steps at once: thread t (heap order, root 1) replays the path its index
+        // spells from (lo, hi) and evaluates kbar at its midpoint, then thread 0
+        // follows the comparisons: the same midpoints and decisions as one step at
+        // a time.
+        for (int round = 0; round < 25; ++round) {
+            if (walk_done) break;
+            if (t >= 1) {
+                double lo = lo_sh, hi = hi_sh;
+                const int depth = 31 - __clz(t);
+                bool live = true;
+                for (int d = depth - 1; d >= 0 && live; --d) {
                     const double mid = mul(add(lo, hi), 0.5);
-                    if (mid == lo || mid == hi) break;
-                    if (kbar(mid, nd, alpha) > k) lo = mid;
+                    if (mid == lo || mid == hi) live = false;
+                    else if ((t >> d) & 1) lo = mid;
                     else hi = mid;
                 }
-                R_sh = hi;
+                uint8_t b = 0;
+                if (live) {
+                    const double mid = mul(add(lo, hi), 0.5);
+                    if (mid != lo && mid != hi) b = kbar(mid, nd, alpha) > k ? 1 : 0;
+                }
+                above[t] = b;
             }
+            __syncthreads();
+            if (t == 0) {
+                double lo = lo_sh, hi = hi_sh;
+                int node = 1;
+                for (int d = 0; d < 8; ++d) {
+                    const double mid = mul(add(lo, hi), 0.5);
+                    if (mid == lo || mid == hi) {
+                        walk_done = 1;
+                        break;
+                    }
+                    if (above[node]) {
+                        lo = mid;
+                        node = 2 * node + 1;
+                    } else {
+                        hi = mid;
+                        node = 2 * node;
+                    }
+                }
+                lo_sh = lo;
+                hi_sh = hi;
+            }
+            __syncthreads();
         }
+        if (t == 0 && !fail) R_sh = hi_sh;
     }
     __syncthreads();
     const double R = fail ? 1.0 : R_sh;
@@ -72,42 +114,45 @@ __device__ void plan_block(Meta *M, const PlanArgs &a)
     const double G = 0.5 * ::log(2.0 * coshR);
     // e^k table (threads 0..128)
     if (t <= 2 * kExpTab) M->etab[t] = static_cast<float>(::exp(static_cast<double>(t - kExpTab)));
-    if (t != 0) return;
-    M->error = fail ? kErrNoSolution : kErrNone;
-    M->R = R;
-    M->coshR = coshR;
-    M->G = G;
-    M->alpha = alpha;
-    M->inv_alpha = div(1.0, alpha);
-    M->cm1 = sub(dm::cosh(mul(alpha, R)), 1.0);
     const uint32_t B = a.B;
-    const double p = a.p;
-    M->B = B;
-    M->n = a.n;
-    M->seed = a.seed;
-    M->k = k;
-    M->filter = (a.allow_filter && R <= kFilterMaxR && alpha * R <= kFilterMaxAlphaR) ? 1u : 0u;
-    M->verify = a.verify;
-    // Sec. III-A: c_0 = 0, c_{j+1} - c_j = c_1 p^j, c_1 = (1-p) R / (1 - p^B), c_B = R
-    M->c[0] = 0.0;
-    if (p == 1.0) {
-        for (uint32_t j = 1; j < B; ++j) M->c[j] = div(mul(R, static_cast<double>(j)), static_cast<double>(B));
-    } else {
-        double pw = 1.0;
-        for (uint32_t j = 0; j < B; ++j) pw = mul(pw, p);
-        const double c1 = div(mul(sub(1.0, p), R), sub(1.0, pw));
-        double step = c1;
-        for (uint32_t j = 1; j < B; ++j) {
-            const double next = add(M->c[j - 1], step);
-            M->c[j] = next < R ? next : R;
-            step = mul(step, p);
+    if (t == 0) {  // scalars and the boundaries (a short recurrence)
+        M->error = fail ? kErrNoSolution : kErrNone;
+        M->R = R;
+        M->coshR = coshR;
+        M->G = G;
+        M->alpha = alpha;
+        M->inv_alpha = div(1.0, alpha);
+        M->cm1 = sub(dm::cosh(mul(alpha, R)), 1.0);
+        const double p = a.p;
+        M->B = B;
+        M->n = a.n;
+        M->seed = a.seed;
+        M->k = k;
+        M->filter = (a.allow_filter && R <= kFilterMaxR && alpha * R <= kFilterMaxAlphaR) ? 1u : 0u;
+        M->verify = a.verify;
+        // Sec. III-A: c_0 = 0, c_{j+1} - c_j = c_1 p^j, c_1 = (1-p) R / (1 - p^B), c_B = R
+        M->c[0] = 0.0;
+        if (p == 1.0) {
+            for (uint32_t j = 1; j < B; ++j) M->c[j] = div(mul(R, static_cast<double>(j)), static_cast<double>(B));
+        } else {
+            double pw = 1.0;
+            for (uint32_t j = 0; j < B; ++j) pw = mul(pw, p);
+            const double c1 = div(mul(sub(1.0, p), R), sub(1.0, pw));
+            double step = c1;
+            for (uint32_t j = 1; j < B; ++j) {
+                const double next = add(M->c[j - 1], step);
+                M->c[j] = next < R ? next : R;
+                step = mul(step, p);
+            }
         }
+        M->c[B] = R;
     }
-    M->c[B] = R;
-    // FP32 window constants: the filter's radii carry an error up to kDeltaR, so
-    // band i is bounded by c_i - kDeltaR (inner) and c_{i+1} + kDeltaR (outer)
+    __syncthreads();
+    // FP32 window constants, one band per thread: the filter's radii carry an error
+    // up to kDeltaR, so band i is bounded by c_i - kDeltaR (inner) and c_{i+1} +
+    // kDeltaR (outer)
     const double sq = ::exp(-G);
-    for (uint32_t j = 0; j <= B; ++j) {
+    for (uint32_t j = t; j <= B; j += blockDim.x) {
         M->cosh_c[j] = ::cosh(M->c[j]);
         M->sinh_c[j] = ::sinh(M->c[j]);
         const double ci = M->c[j] - kDeltaR > 0.0 ? M->c[j] - kDeltaR : 0.0;
@@ -120,7 +165,8 @@ __device__ void plan_block(Meta *M, const PlanArgs &a)
         M->band_Mo[j] = static_cast<float>(::exp(-co) * sq);
         M->band_So[j] = static_cast<float>(::sinh(co) * sq * 1.4142135623730951);
     }
-    for (uint32_t j = 0; j < static_cast<uint32_t>(kMaxBands); ++j) M->band_count[j] = 0;
+    if (t < kMaxBands) M->band_count[t] = 0;
+    if (t != 0) return;
     M->m = 0;
     M->candidates = 0;
     M->near_threshold = 0;
