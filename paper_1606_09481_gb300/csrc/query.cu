@@ -692,11 +692,47 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
             // fringe tests, one candidate per lane per step
             uint64_t mask = 0;
             const uint32_t maxf = __reduce_max_sync(full, nf);
-            for (uint32_t t = 0; t < maxf; ++t) {
-                const bool in = t < nf;
-                const uint32_t q = t < nl ? f0 + t : f2 + (t - nl);
-                const int dec = decide_own<kFilter>(a, M, C, va, vb, mine, phv, p, idv, q, in, coshR, verify, near);
-                if (dec == 1) mask |= 1ull << t;
+            if (kFilter) {
+                // the next candidate's values are loaded while the current one is tested
+                float2 aw = make_float2(0.0f, 0.0f);
+                float4 pw = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (nf) {
+                    const uint32_t q = nl ? f0 : f2;
+                    aw = a.P.ang[q];
+                    pw = a.P.pms[q];
+                }
+                for (uint32_t t = 0; t < maxf; ++t) {
+                    const bool in = t < nf;
+                    const uint32_t q = t < nl ? f0 + t : f2 + (t - nl);
+                    const float2 ac = aw;
+                    const float4 pc = pw;
+                    if (t + 1 < nf) {
+                        const uint32_t qn = t + 1 < nl ? f0 + t + 1 : f2 + (t + 1 - nl);
+                        aw = a.P.ang[qn];
+                        pw = a.P.pms[qn];
+                    }
+                    const int dec = in ? filter_decide(va, vb, ac, pc) : 0;
+                    const uint32_t um = __ballot_sync(full, dec == 2);
+                    if (um) {
+                        uint32_t rb = 0;
+                        if (lane == 0) rb = atomicAdd(&C->recheck_n, static_cast<uint32_t>(__popc(um)));
+                        rb = __shfl_sync(full, rb, 0);
+                        if (dec == 2) {
+                            const uint32_t at = rb + __popc(um & ((1u << lane) - 1u));
+                            if (at < a.recheck_cap) a.recheck[at] = make_uint2(p, q);
+                            else atomicMax(&C->error, kErrListFull);
+                        }
+                    }
+                    if (verify && in && dec != 2) verify_pair(a, M, C, idv, a.P.id[q], dec, coshR);
+                    if (dec == 1) mask |= 1ull << t;
+                }
+            } else {
+                for (uint32_t t = 0; t < maxf; ++t) {
+                    const bool in = t < nf;
+                    const uint32_t q = t < nl ? f0 + t : f2 + (t - nl);
+                    const int dec = decide_own<kFilter>(a, M, C, va, vb, mine, phv, p, idv, q, in, coshR, verify, near);
+                    if (dec == 1) mask |= 1ull << t;
+                }
             }
             // one reservation for the warp's edges of this band: [base, base + T)
             // holds the core edges of lanes 0..31 in lane order, then come the
