@@ -269,7 +269,33 @@ def bench_batched(args, rhg, torch, stream):
     del wsp
     value = m / (ms / 1000.0)
     plain = plain_m / (plain_ms / 1000.0)
+    # the band count per size class chosen by the autotuner, then the same timing
+    from paper_1606_09481_gb300.autotune import gpu_runner, tune
+    table = tune(specs, gpu_runner(stream))
+    tuned_params = (rhg.Params * len(specs))(*[rhg.make_params(n, kk, a, sd, table.bands(n))
+                                                for (n, kk, a, sd) in specs])
+    tbuf = rhg.allocate_batch(tuned_params)
+    rc, tres, ttot = rhg.run_batch(tbuf, stream)
+    if rc == rhg.OVERFLOW:
+        caps = [max(int(tres[g].m), int(tbuf.offsets[g + 1] - tbuf.offsets[g])) for g in range(len(specs))]
+        del tbuf
+        tbuf = rhg.allocate_batch(tuned_params, caps)
+        rc, tres, ttot = rhg.run_batch(tbuf, stream)
+    for _ in range(max(args.warmup - 1, 0)):
+        rhg.run_batch(tbuf, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        rc, tres, ttot = rhg.run_batch(tbuf, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tuned_ms = e0.elapsed_time(e1) / args.steps
+    del tbuf
+    tuned = {"value": int(ttot.m) / (tuned_ms / 1000.0), "ms_per_step": tuned_ms,
+             "edges_equal_default": int(ttot.m) == m,
+             "band_offsets": {f"{lo}-{hi}": table.offsets.get(c, 0) for c, (lo, hi) in enumerate(table.classes)}}
     return {"value": value, "unit": "edges/s", "ms_per_step": ms, "graphs": len(specs), "points": points,
+            "autotuned_bands": tuned,
             "edges": m, "exact_edges_equal_plain": plain_m == m, "plain_per_graph_value": plain,
             "plain_per_graph_ms": plain_ms, "speedup_vs_plain": value / plain,
             "stages_ms": {s: timer.totals[s] / max(args.steps, 1) for s in rhg.STAGES if s != "csr"},

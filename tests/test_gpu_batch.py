@@ -94,3 +94,20 @@ def test_p4_shaped_batch_sample():
             want, res = _single(rhg, params[g])
             assert np.array_equal(got, want), g
     assert tot.m == sum(r.m for r in results)
+
+
+def test_autotuned_band_counts_give_the_same_graphs():
+    """The autotuner only changes band counts: every graph stays the same."""
+    rhg = require_gpu()
+    from paper_1606_09481_gb300.autotune import gpu_runner, tune
+    rng = np.random.default_rng(77)
+    specs = [(int(10 ** rng.uniform(3, 5)), int(rng.integers(6, 33)), float(rng.uniform(0.55, 1.5)), 3000 + j)
+             for j in range(48)]
+    table = tune(specs, gpu_runner(), per_class=16, repeats=1)
+    assert set(table.offsets) <= {0, 1}
+    tuned = rhg.batch_params([rhg.make_params(n, k, a, s, table.bands(n)) for (n, k, a, s) in specs])
+    v1, r1, _ = rhg.generate_batch(rhg.batch_params(specs))
+    v2, r2, _ = rhg.generate_batch(tuned)
+    for g in range(len(specs)):
+        assert r2[g].num_bands == table.bands(specs[g][0])
+        assert np.array_equal(sorted_pairs(v1[g]), sorted_pairs(v2[g])), g
