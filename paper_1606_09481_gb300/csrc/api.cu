@@ -240,6 +240,7 @@ Status enqueue(const Pipeline &pl, const PlanArgs &pa, const double *phi_in, con
     q.recheck_cap = pl.L.recheck_cap;
     q.heavy_min = heavy_min;
     q.bidx = at<uint32_t>(pl.ws, pl.L.bidx);
+    q.verify = pa.verify != 0;
     mark(RHG_STAGE_QUERY, false, stream);
     st = launch_query(q, kind == Output::Csr, stream);
     if (st.code) return st;
@@ -518,6 +519,7 @@ Status enqueue_batch(void *ws, const BatchLayout &L, const BatchHost &h, uint32_
     q.recheck = at<uint2>(ws, L.recheck);
     q.recheck_cap = L.recheck_cap;
     q.bidx = at<uint32_t>(ws, L.bidx);
+    for (const PlanArgs &g : h.args) q.verify = q.verify || g.verify != 0;
     mark(RHG_STAGE_QUERY, false, stream);
     st = launch_query_batch(q, stream);
     if (st.code) return st;

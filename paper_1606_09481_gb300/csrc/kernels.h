@@ -66,6 +66,7 @@ struct QueryArgs {
     uint32_t recheck_cap;
     uint32_t heavy_min;     // ranges longer than this go to the heavy chunks (UINT32_MAX: never)
     uint32_t *bidx;         // bucket index of the bands, index_entries(n) entries
+    bool verify;            // some graph runs in verification mode (RHG_FLAG_VERIFY)
 };
 
 // ---- points.cu ----

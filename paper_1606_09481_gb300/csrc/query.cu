@@ -37,6 +37,7 @@ constexpr int kListCap = 64;           // queued fringe entries per warp (>= 2 p
 constexpr int kCoreCap = 32;           // queued core entries per warp (>= 1 per lane)
 constexpr int kBitWords = 128;         // decision words per warp: kChunk / 32
 constexpr uint32_t kFull = 0x80000000u;  // window half-width meaning "whole band"
+constexpr int kBatchMinBlocks = 4;         // resident CTAs per SM the batch kernel is compiled for
 
 constexpr float kPiF = 3.14159265f;             // below pi: the unwrapped branch is safe to pi
 constexpr float kTwoPiHiF = 6.28318548202514648f;
@@ -539,8 +540,8 @@ __device__ __forceinline__ int decide_own(const QueryArgs &a, const Meta *Mg, Me
 // keeps the band table of its current graph in its own shared memory, and edges
 // go to the graph's output region and counter; lists and work counters live in
 // the control block.
-template <bool kFilter, bool kCsr, bool kMulti>
-__global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
+template <bool kFilter, bool kCsr, bool kMulti, bool kVerify>
+__global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryArgs a)
 {
     __shared__ BandShared Sm[kMulti ? kWarps : 1];
     const int lane = threadIdx.x & 31;
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
     const uint32_t n = static_cast<uint32_t>(a.P.n);
     uint32_t B = M->B;
     double coshR = M->coshR;
-    bool verify = M->verify != 0;
+    bool verify = kVerify && M->verify != 0;  // the variant without verification has no checks at all
     uint64_t obase = 0, cap = a.capacity;  // output region of the current graph
     uint32_t cur_g = 0xffffffffu;
     bool skip = false;
@@ -588,7 +589,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
                 __syncwarp();
                 B = M->B;
                 coshR = M->coshR;
-                verify = M->verify != 0;
+                verify = kVerify && M->verify != 0;
                 obase = a.bt.out_off[cur_g];
                 cap = a.bt.out_off[cur_g + 1] - obase;
                 skip = M->error || (M->filter != 0) != kFilter;
@@ -723,14 +724,15 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
                             else atomicMax(&C->error, kErrListFull);
                         }
                     }
-                    if (verify && in && dec != 2) verify_pair(a, M, C, idv, a.P.id[q], dec, coshR);
+                    if (kVerify && verify && in && dec != 2) verify_pair(a, M, C, idv, a.P.id[q], dec, coshR);
                     if (dec == 1) mask |= 1ull << t;
                 }
             } else {
                 for (uint32_t t = 0; t < maxf; ++t) {
                     const bool in = t < nf;
                     const uint32_t q = t < nl ? f0 + t : f2 + (t - nl);
-                    const int dec = decide_own<kFilter>(a, M, C, va, vb, mine, phv, p, idv, q, in, coshR, verify, near);
+                    const int dec = decide_own<kFilter>(a, M, C, va, vb, mine, phv, p, idv, q, in, coshR,
+                                                        kVerify && verify, near);
                     if (dec == 1) mask |= 1ull << t;
                 }
             }
@@ -773,7 +775,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(QueryArgs a)
                 if (j < T) {
                     const uint32_t w = __ldg(a.P.id + (j + dl));
                     write_edge<kCsr>(a, base + j, u, w);
-                    if (verify) verify_pair(a, M, C, u, w, 1, coshR);
+                    if (kVerify && verify) verify_pair(a, M, C, u, w, 1, coshR);
                 }
                 L = __shfl_sync(full, L, 31);  // owner of the window's last element
                 __syncwarp();
@@ -1242,10 +1244,11 @@ Status run(const QueryArgs &a, cudaStream_t stream)
     const uint64_t nbatch = kMulti ? static_cast<uint64_t>(a.bt.num_tiles) * (kTilePoints / 32) : (a.P.n + 31) / 32;
     const uint64_t need = ceil_div(nbatch ? nbatch : 1, kWarps);
     static int grid_b = 0, grid_h = 0;
-    if (!grid_b) grid_b = resident_ctas(batch_kernel<kFilter, kCsr, kMulti>);
+    if (!grid_b) grid_b = resident_ctas(batch_kernel<kFilter, kCsr, kMulti, false>);
     if (!grid_h) grid_h = resident_ctas(heavy_kernel<kFilter, kCsr, kMulti>);
     const unsigned gb = static_cast<unsigned>(need < static_cast<uint64_t>(grid_b) ? need : grid_b);
-    batch_kernel<kFilter, kCsr, kMulti><<<gb, kThreads, 0, stream>>>(a);
+    if (a.verify) batch_kernel<kFilter, kCsr, kMulti, true><<<gb, kThreads, 0, stream>>>(a);
+    else batch_kernel<kFilter, kCsr, kMulti, false><<<gb, kThreads, 0, stream>>>(a);
     RHG_LAUNCH_CHECK();
     heavy_kernel<kFilter, kCsr, kMulti><<<static_cast<unsigned>(grid_h), kThreads, 0, stream>>>(a);
     RHG_LAUNCH_CHECK();
