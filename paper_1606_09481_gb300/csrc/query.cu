@@ -384,7 +384,7 @@ __device__ __noinline__ void verify_pair(const QueryArgs &a, const Meta *Mg, Met
 
 // Decide candidate q (owner slot o); queue undecided pairs; in verification mode
 // compare every decided pair with the FP64 predicate.
-template <bool kFilter>
+template <bool kFilter, bool kVerify>
 __device__ __forceinline__ int decide(const QueryArgs &a, const Meta *Mg, Meta *C, const WarpSmem &W, uint32_t o,
                                       uint32_t q, bool in, double coshR, bool verify, uint32_t &near)
 {
@@ -404,7 +404,7 @@ __device__ __forceinline__ int decide(const QueryArgs &a, const Meta *Mg, Meta *
                 else atomicMax(&C->error, kErrListFull);
             }
         }
-        if (verify && in && dec != 2) verify_pair(a, Mg, C, W.oid[o], a.P.id[q], dec, coshR);
+        if (kVerify && verify && in && dec != 2) verify_pair(a, Mg, C, W.oid[o], a.P.id[q], dec, coshR);
     } else if (in) {
         const double2 v = W.od[o];
         const double L = predicate_L(v.x, v.y, W.osh[o], a.P.phi[q], a.P.ch[q], a.P.sh[q]);
@@ -416,7 +416,7 @@ __device__ __forceinline__ int decide(const QueryArgs &a, const Meta *Mg, Meta *
 
 // Write the queued core entries [0, ccount): certain edges, no test.
 // Output: graph Mg's edge counter, its region starting at obase with room for cap pairs.
-template <bool kCsr>
+template <bool kCsr, bool kVerify>
 __device__ __forceinline__ void flush_core(const QueryArgs &a, Meta *Mg, Meta *C, uint64_t obase, uint64_t cap,
                                            WarpSmem &W, int ccount, double coshR, bool verify)
 {
@@ -438,7 +438,7 @@ __device__ __forceinline__ void flush_core(const QueryArgs &a, Meta *Mg, Meta *C
             const uint32_t q = W.clo[e] + (j - W.cpre[e]);
             const uint32_t idv = W.oid[W.cown[e]], idw = a.P.id[q];
             write_edge<kCsr>(a, base + j, idv, idw);
-            if (verify) verify_pair(a, Mg, C, idv, idw, 1, coshR);
+            if (kVerify && verify) verify_pair(a, Mg, C, idv, idw, 1, coshR);
         }
     }
 }
@@ -448,7 +448,7 @@ __device__ __forceinline__ void flush_core(const QueryArgs &a, Meta *Mg, Meta *C
 // candidate, one output reservation per segment, then a replay of the set bits.
 // The entry of a round's first candidate advances monotonically (warp-uniform);
 // each lane then steps forward over the few entries its round crosses.
-template <bool kFilter, bool kCsr>
+template <bool kFilter, bool kCsr, bool kVerify>
 __device__ __forceinline__ void flush(const QueryArgs &a, Meta *Mg, Meta *C, uint64_t obase, uint64_t cap,
                                       WarpSmem &W, int count, double coshR, bool verify, uint32_t &near)
 {
@@ -469,7 +469,7 @@ __device__ __forceinline__ void flush(const QueryArgs &a, Meta *Mg, Meta *C, uin
             if (in)
                 while (W.pre[e + 1] <= j) ++e;
             const uint32_t q = W.lo[e] + (j - W.pre[e]);
-            const int dec = decide<kFilter>(a, Mg, C, W, W.own[e], q, in, coshR, verify, near);
+            const int dec = decide<kFilter, kVerify>(a, Mg, C, W, W.own[e], q, in, coshR, verify, near);
             const uint32_t word = __ballot_sync(full, dec == 1);
             if (lane == 0) {
                 W.bits[words] = word;
@@ -802,7 +802,7 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryA
 
 // Heavy chunks: one warp per chunk of at most kChunk candidates of one owner,
 // tested (type 0) or a core chunk of certain edges (type 1).
-template <bool kFilter, bool kCsr, bool kMulti>
+template <bool kFilter, bool kCsr, bool kMulti, bool kVerify>
 __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
 {
     __shared__ WarpSmem Wsm[kWarps];
@@ -823,7 +823,7 @@ __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
         Meta *Mg = kMulti ? a.M + g : a.M;
         if (kMulti && (Mg->error || (Mg->filter != 0) != kFilter)) continue;
         const double coshR = Mg->coshR;
-        const bool verify = Mg->verify != 0;
+        const bool verify = kVerify && Mg->verify != 0;
         const uint64_t obase = kMulti ? a.bt.out_off[g] : 0;
         const uint64_t cap = kMulti ? a.bt.out_off[g + 1] - obase : a.capacity;
         const bool core = (h.w & 1u) != 0;
@@ -842,8 +842,8 @@ __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
             }
         }
         __syncwarp();
-        if (core) flush_core<kCsr>(a, Mg, C, obase, cap, W, 1, coshR, verify);
-        else flush<kFilter, kCsr>(a, Mg, C, obase, cap, W, 1, coshR, verify, near);
+        if (core) flush_core<kCsr, kVerify>(a, Mg, C, obase, cap, W, 1, coshR, verify);
+        else flush<kFilter, kCsr, kVerify>(a, Mg, C, obase, cap, W, 1, coshR, verify, near);
         __syncwarp();
     }
     for (int off = 16; off; off >>= 1) near += __shfl_down_sync(full, near, off);
@@ -1245,12 +1245,13 @@ Status run(const QueryArgs &a, cudaStream_t stream)
     const uint64_t need = ceil_div(nbatch ? nbatch : 1, kWarps);
     static int grid_b = 0, grid_h = 0;
     if (!grid_b) grid_b = resident_ctas(batch_kernel<kFilter, kCsr, kMulti, false>);
-    if (!grid_h) grid_h = resident_ctas(heavy_kernel<kFilter, kCsr, kMulti>);
+    if (!grid_h) grid_h = resident_ctas(heavy_kernel<kFilter, kCsr, kMulti, false>);
     const unsigned gb = static_cast<unsigned>(need < static_cast<uint64_t>(grid_b) ? need : grid_b);
     if (a.verify) batch_kernel<kFilter, kCsr, kMulti, true><<<gb, kThreads, 0, stream>>>(a);
     else batch_kernel<kFilter, kCsr, kMulti, false><<<gb, kThreads, 0, stream>>>(a);
     RHG_LAUNCH_CHECK();
-    heavy_kernel<kFilter, kCsr, kMulti><<<static_cast<unsigned>(grid_h), kThreads, 0, stream>>>(a);
+    if (a.verify) heavy_kernel<kFilter, kCsr, kMulti, true><<<static_cast<unsigned>(grid_h), kThreads, 0, stream>>>(a);
+    else heavy_kernel<kFilter, kCsr, kMulti, false><<<static_cast<unsigned>(grid_h), kThreads, 0, stream>>>(a);
     RHG_LAUNCH_CHECK();
     if (kFilter) {
         if (kMulti) recheck_batch_kernel<<<static_cast<unsigned>(num_sms() * 4), kThreads, 0, stream>>>(a);
