@@ -32,7 +32,10 @@ __device__ double kbar(double R, double nd, double alpha)
 constexpr int kPlanThreads = 256;  // grid points j = 0..255 of the bracket search
 
 // R, boundaries and the band constants of one graph, by one CTA of kPlanThreads.
-__device__ void plan_block(Meta *M, const PlanArgs &a)
+// depth: bisection steps taken per round (2^depth - 1 speculative evaluations;
+// 8 when one graph wants the lowest latency, fewer when many graphs share the
+// FP64 units).
+__device__ void plan_block(Meta *M, const PlanArgs &a, int depth)
 {
     __shared__ int jstar;
     __shared__ double R_sh, lo_sh, hi_sh;
@@ -59,14 +62,16 @@ __device__ void plan_block(Meta *M, const PlanArgs &a)
         }
         __syncthreads();
         // binary search: mid = (lo + hi) / 2, kbar(mid) > k ? lo = mid : hi = mid, until
-        // lo and hi are adjacent (at most 200 steps); R = hi.  Each round takes eight
-        // steps at once: thread t (heap order, root 1) replays the path its index
-        // spells from (lo, hi) and evaluates kbar at its midpoint, then thread 0
-        // follows the comparisons: the same midpoints and decisions as one step at
-        // a time.
-        for (int round = 0; round < 25; ++round) {
+        // lo and hi are adjacent (at most 200 steps); R = hi.  Each round takes
+        // `depth` steps at once: thread t (heap order, root 1) replays the path its
+        // index spells from (lo, hi) and evaluates kbar at its midpoint, then thread
+        // 0 follows the comparisons: the same midpoints and decisions as one step
+        // at a time.
+        const int nodes = 1 << depth;
+        int steps = 0;
+        for (int round = 0; round < 200; ++round) {
             if (walk_done) break;
-            if (t >= 1) {
+            if (t >= 1 && t < nodes) {
                 double lo = lo_sh, hi = hi_sh;
                 const int depth = 31 - __clz(t);
                 bool live = true;
@@ -87,12 +92,13 @@ __device__ void plan_block(Meta *M, const PlanArgs &a)
             if (t == 0) {
                 double lo = lo_sh, hi = hi_sh;
                 int node = 1;
-                for (int d = 0; d < 8; ++d) {
+                for (int d = 0; d < depth; ++d) {
                     const double mid = mul(add(lo, hi), 0.5);
-                    if (mid == lo || mid == hi) {
+                    if (mid == lo || mid == hi || steps == 200) {
                         walk_done = 1;
                         break;
                     }
+                    ++steps;
                     if (above[node]) {
                         lo = mid;
                         node = 2 * node + 1;
@@ -178,14 +184,14 @@ __device__ void plan_block(Meta *M, const PlanArgs &a)
     M->work_counter = 0;
 }
 
-__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, PlanArgs a) { plan_block(M, a); }
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, PlanArgs a) { plan_block(M, a, 8); }
 
 // Batch: CTA g < G plans graph g; CTA G clears the control block's counters.
 __global__ void __launch_bounds__(kPlanThreads) plan_batch_kernel(Meta *metas, const PlanArgs *args, uint32_t G)
 {
     if (blockIdx.x < G) {
         const PlanArgs a = args[blockIdx.x];
-        plan_block(metas + blockIdx.x, a);
+        plan_block(metas + blockIdx.x, a, 3);
         return;
     }
     if (threadIdx.x != 0) return;
