@@ -2,7 +2,7 @@
 import os
 
 
-def test_graft_build():
+def test_entry_build():
     import __graft_entry__ as g
     g.build()
     import paper_1606_09481_gb300 as rhg
