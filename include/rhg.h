@@ -14,8 +14,10 @@
  *   returns a count to the host (m, R) synchronises that stream once, after the
  *   count is known.
  * - The caller provides all device memory: a workspace whose size
- *   rhg_workspace_bytes() reports, and the output buffers.  Inside an entry
- *   point the library allocates no device or host memory.
+ *   rhg_workspace_bytes() (or the entry point's own sizing call) reports, and
+ *   the output buffers.  Inside an entry point the library allocates no device
+ *   memory; rhg_generate_batch stages its per-graph tables in temporary host
+ *   memory, the other entry points allocate none.
  * - Vertex ids are the Philox counter indices 0..n-1 (uint32).  An edge {u,v}
  *   is reported once as the pair (u, v) with u < v; the order of pairs is
  *   unspecified.  CSR rows list both directions with ascending columns.

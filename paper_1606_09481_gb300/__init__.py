@@ -15,9 +15,11 @@ from dataclasses import dataclass
 from .build import LIB, build
 
 __all__ = [
-    "RhgError", "Params", "Result", "load", "status_str", "target_radius", "plan", "workspace_bytes",
-    "sample_points", "generate_pairs", "generate_pairs_host", "generate_csr", "edges_from_points",
-    "dm_eval", "default_bands", "FLAG_FP64_ONLY", "MAX_BANDS", "build",
+    "RhgError", "Params", "Result", "BatchGraph", "load", "status_str", "target_radius", "plan", "workspace_bytes",
+    "sample_points", "generate_pairs", "generate_pairs_host", "generate_pairs_static", "generate_csr",
+    "edges_from_points", "batch_params", "batch_workspace_bytes", "allocate_batch", "run_batch", "generate_batch",
+    "draw_movement", "move_points", "update_edges", "dm_eval", "default_bands", "make_params", "estimate_capacity",
+    "StageTimer", "launch_count", "FLAG_FP64_ONLY", "FLAG_VERIFY", "MAX_BANDS", "STATIC_MAX_POINTS", "build",
 ]
 
 OK, INVALID_ARG, NO_SOLUTION, OOM, CUDA_ERROR, TIMEOUT, OVERFLOW = range(7)
