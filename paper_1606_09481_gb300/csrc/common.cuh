@@ -14,7 +14,7 @@ namespace rhg {
 constexpr int kMaxBands = static_cast<int>(RHG_MAX_BANDS);
 // bucket index: about kBucketPoints..2 kBucketPoints points per bucket, at least
 // two buckets per band; index_entries(n) bounds the entries of all bands
-constexpr uint32_t kBucketPoints = 4;
+constexpr uint32_t kBucketPoints = 1;
 __host__ __device__ constexpr uint64_t index_entries(uint64_t n) { return n / kBucketPoints + 3 * kMaxBands + 1; }
 constexpr int kExpTab = 64;  // e^k table for k = -64..64 (FP32 filter values)
 

@@ -38,6 +38,7 @@ constexpr int kCoreCap = 32;           // queued core entries per warp (>= 1 per
 constexpr int kBitWords = 128;         // decision words per warp: kChunk / 32
 constexpr uint32_t kFull = 0x80000000u;  // window half-width meaning "whole band"
 constexpr int kBatchMinBlocks = 4;         // resident CTAs per SM the batch kernel is compiled for
+constexpr int kCoreGroup = 4;              // core-writer windows whose loads are issued together
 
 constexpr float kPiF = 3.14159265f;             // below pi: the unwrapped branch is safe to pi
 constexpr float kTwoPiHiF = 6.28318548202514648f;
@@ -429,16 +430,32 @@ __device__ __forceinline__ void flush_core(const QueryArgs &a, Meta *Mg, Meta *C
     if (base + total > cap) return;
     base += obase;
     int e0 = 0;
-    for (uint32_t j0 = 0; j0 < total; j0 += 32) {
-        while (W.cpre[e0 + 1] <= j0) ++e0;
-        const uint32_t j = j0 + lane;
-        if (j < total) {
-            int e = e0;
-            while (W.cpre[e + 1] <= j) ++e;
-            const uint32_t q = W.clo[e] + (j - W.cpre[e]);
-            const uint32_t idv = W.oid[W.cown[e]], idw = a.P.id[q];
-            write_edge<kCsr>(a, base + j, idv, idw);
-            if (kVerify && verify) verify_pair(a, Mg, C, idv, idw, 1, coshR);
+    for (uint32_t j0 = 0; j0 < total; j0 += 32 * kCoreGroup) {
+        uint32_t q[kCoreGroup], u[kCoreGroup], w[kCoreGroup];
+#pragma unroll
+        for (int g = 0; g < kCoreGroup; ++g) {
+            const uint32_t jw = j0 + 32 * g, j = jw + lane;
+            q[g] = 0;
+            u[g] = 0;
+            if (jw < total) {  // warp-uniform
+                while (W.cpre[e0 + 1] <= jw) ++e0;
+                if (j < total) {
+                    int e = e0;
+                    while (W.cpre[e + 1] <= j) ++e;
+                    q[g] = W.clo[e] + (j - W.cpre[e]);
+                    u[g] = W.oid[W.cown[e]];
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < kCoreGroup; ++g) w[g] = j0 + 32 * g + lane < total ? __ldg(a.P.id + q[g]) : 0u;
+#pragma unroll
+        for (int g = 0; g < kCoreGroup; ++g) {
+            const uint32_t j = j0 + 32 * g + lane;
+            if (j < total) {
+                write_edge<kCsr>(a, base + j, u[g], w[g]);
+                if (kVerify && verify) verify_pair(a, Mg, C, u[g], w[g], 1, coshR);
+            }
         }
     }
 }
@@ -761,31 +778,58 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryA
             // its owner is the lane whose segment starts last at or before j: the
             // segment starts inside each 32-element window are one OR-reduction and
             // a table of which lane starts where
+            // Owners of kCoreGroup windows are found first, then their id loads
+            // are issued together, so that one memory latency covers the group.
             const uint32_t start = ci - nc, delta = c0 - start;  // source position = j + delta
             uint32_t L = 0;
-            for (uint32_t j0 = 0; j0 < T; j0 += 32) {
-                const bool starts = nc != 0 && start >= j0 && start - j0 < 32;
-                if (starts) own[start - j0] = static_cast<uint8_t>(lane);
-                const uint32_t bits = __reduce_or_sync(full, starts ? 1u << (start - j0) : 0u);
-                __syncwarp();
-                const uint32_t upto = bits & (0xffffffffu >> (31 - lane));  // starts at offsets <= lane
-                if (upto) L = own[31 - __clz(upto)];
-                const uint32_t dl = __shfl_sync(full, delta, L), u = __shfl_sync(full, idv, L);
-                const uint32_t j = j0 + lane;
-                if (j < T) {
-                    const uint32_t w = __ldg(a.P.id + (j + dl));
-                    write_edge<kCsr>(a, base + j, u, w);
-                    if (kVerify && verify) verify_pair(a, M, C, u, w, 1, coshR);
+            for (uint32_t j0 = 0; j0 < T; j0 += 32 * kCoreGroup) {
+                uint32_t dl[kCoreGroup], u[kCoreGroup], w[kCoreGroup];
+#pragma unroll
+                for (int g = 0; g < kCoreGroup; ++g) {
+                    const uint32_t jw = j0 + 32 * g;
+                    dl[g] = 0;
+                    u[g] = 0;
+                    if (jw < T) {  // warp-uniform
+                        const bool starts = nc != 0 && start >= jw && start - jw < 32;
+                        if (starts) own[start - jw] = static_cast<uint8_t>(lane);
+                        const uint32_t bits = __reduce_or_sync(full, starts ? 1u << (start - jw) : 0u);
+                        __syncwarp();
+                        const uint32_t upto = bits & (0xffffffffu >> (31 - lane));  // starts at offsets <= lane
+                        if (upto) L = own[31 - __clz(upto)];
+                        dl[g] = __shfl_sync(full, delta, L);
+                        u[g] = __shfl_sync(full, idv, L);
+                        L = __shfl_sync(full, L, 31);  // owner of the window's last element
+                        __syncwarp();
+                    }
                 }
-                L = __shfl_sync(full, L, 31);  // owner of the window's last element
-                __syncwarp();
+#pragma unroll
+                for (int g = 0; g < kCoreGroup; ++g) {
+                    const uint32_t j = j0 + 32 * g + lane;
+                    w[g] = j < T ? __ldg(a.P.id + (j + dl[g])) : 0u;
+                }
+#pragma unroll
+                for (int g = 0; g < kCoreGroup; ++g) {
+                    const uint32_t j = j0 + 32 * g + lane;
+                    if (j < T) {
+                        write_edge<kCsr>(a, base + j, u[g], w[g]);
+                        if (kVerify && verify) verify_pair(a, M, C, u[g], w[g], 1, coshR);
+                    }
+                }
             }
+            // fringe edges, two per step with both id loads in flight
             uint64_t pos = base + T + (fi - nfe);
             while (mask) {
-                const uint32_t t = static_cast<uint32_t>(__ffsll(static_cast<long long>(mask)) - 1);
+                const uint32_t t0 = static_cast<uint32_t>(__ffsll(static_cast<long long>(mask)) - 1);
                 mask &= mask - 1;
-                const uint32_t q = t < nl ? f0 + t : f2 + (t - nl);
-                write_edge<kCsr>(a, pos++, idv, a.P.id[q]);
+                const bool two = mask != 0;
+                const uint32_t t1 = two ? static_cast<uint32_t>(__ffsll(static_cast<long long>(mask)) - 1) : t0;
+                if (two) mask &= mask - 1;
+                const uint32_t q0 = t0 < nl ? f0 + t0 : f2 + (t0 - nl);
+                const uint32_t q1 = t1 < nl ? f0 + t1 : f2 + (t1 - nl);
+                const uint32_t w0 = __ldg(a.P.id + q0), w1 = __ldg(a.P.id + q1);
+                write_edge<kCsr>(a, pos, idv, w0);
+                if (two) write_edge<kCsr>(a, pos + 1, idv, w1);
+                pos += two ? 2 : 1;
             }
         }
     }
