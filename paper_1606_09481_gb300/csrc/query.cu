@@ -34,7 +34,6 @@ constexpr uint32_t kChunk = 4096;      // candidates per heavy chunk
 constexpr uint32_t kCoreHeavy = 4096;  // core ranges longer than this become core chunks
 constexpr uint32_t kBatchBudget = 65536;  // candidates a warp batch keeps; beyond, ranges become chunks
 constexpr int kListCap = 64;           // queued fringe entries per warp (>= 2 per lane)
-constexpr int kCoreCap = 32;           // queued core entries per warp (>= 1 per lane)
 constexpr int kBitWords = 128;         // decision words per warp: kChunk / 32
 constexpr uint32_t kFull = 0x80000000u;  // window half-width meaning "whole band"
 constexpr int kBatchMinBlocks = 4;         // resident CTAs per SM the batch kernel is compiled for
@@ -87,11 +86,10 @@ struct OwnerRegs {
 
 // Per-warp shared state.  Queued fringe entries form a flat candidate stream:
 // entry e holds stream positions pre[e] .. pre[e+1]-1 at sorted positions
-// lo[e] + (j - pre[e]); core entries likewise with cpre/clo.  Owners by lane.
+// lo[e] + (j - pre[e]).  Owners by lane.
 struct WarpSmem {
     uint32_t lo[kListCap], pre[kListCap + 1];
-    uint32_t clo[kCoreCap], cpre[kCoreCap + 1];
-    uint8_t own[kListCap], cown[kCoreCap];
+    uint8_t own[kListCap];
     float4 oa[32];      // filter owner: angle hi, angle lo, P, M
     float4 ob[32];      // filter owner: 2 S, P + M, kCBase + gamma, unused
     double2 od[32];     // FP64 owner: phi, cosh r
@@ -415,46 +413,34 @@ __device__ __forceinline__ int decide(const QueryArgs &a, const Meta *Mg, Meta *
     return dec;
 }
 
-// Write the queued core entries [0, ccount): certain edges, no test.
-// Output: graph Mg's edge counter, its region starting at obase with room for cap pairs.
+// Write a core chunk: owner idv and the sorted positions [q0, q0 + total), all
+// certain edges; element j goes to base + j (coalesced), the id loads of four
+// 32-element windows issued together.  Output: graph Mg's edge counter, its
+// region starting at obase with room for cap pairs.
 template <bool kCsr, bool kVerify>
-__device__ __forceinline__ void flush_core(const QueryArgs &a, Meta *Mg, Meta *C, uint64_t obase, uint64_t cap,
-                                           WarpSmem &W, int ccount, double coshR, bool verify)
+__device__ __forceinline__ void write_core_chunk(const QueryArgs &a, Meta *Mg, Meta *C, uint64_t obase, uint64_t cap,
+                                                 uint32_t idv, uint32_t q0, uint32_t total, double coshR, bool verify)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const uint32_t total = W.cpre[ccount];
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(&Mg->m), total);
     base = __shfl_sync(full, base, 0);
     if (base + total > cap) return;
     base += obase;
-    int e0 = 0;
     for (uint32_t j0 = 0; j0 < total; j0 += 32 * kCoreGroup) {
-        uint32_t q[kCoreGroup], u[kCoreGroup], w[kCoreGroup];
+        uint32_t w[kCoreGroup];
 #pragma unroll
         for (int g = 0; g < kCoreGroup; ++g) {
-            const uint32_t jw = j0 + 32 * g, j = jw + lane;
-            q[g] = 0;
-            u[g] = 0;
-            if (jw < total) {  // warp-uniform
-                while (W.cpre[e0 + 1] <= jw) ++e0;
-                if (j < total) {
-                    int e = e0;
-                    while (W.cpre[e + 1] <= j) ++e;
-                    q[g] = W.clo[e] + (j - W.cpre[e]);
-                    u[g] = W.oid[W.cown[e]];
-                }
-            }
+            const uint32_t j = j0 + 32 * g + lane;
+            w[g] = j < total ? __ldg(a.P.id + (q0 + j)) : 0u;
         }
-#pragma unroll
-        for (int g = 0; g < kCoreGroup; ++g) w[g] = j0 + 32 * g + lane < total ? __ldg(a.P.id + q[g]) : 0u;
 #pragma unroll
         for (int g = 0; g < kCoreGroup; ++g) {
             const uint32_t j = j0 + 32 * g + lane;
             if (j < total) {
-                write_edge<kCsr>(a, base + j, u[g], w[g]);
-                if (kVerify && verify) verify_pair(a, Mg, C, u[g], w[g], 1, coshR);
+                write_edge<kCsr>(a, base + j, idv, w[g]);
+                if (kVerify && verify) verify_pair(a, Mg, C, idv, w[g], 1, coshR);
             }
         }
     }
@@ -510,6 +496,78 @@ __device__ __forceinline__ void flush(const QueryArgs &a, Meta *Mg, Meta *C, uin
                     while (W.pre[e + 1] <= j) ++e;
                     const uint32_t q = W.lo[e] + (j - W.pre[e]);
                     write_edge<kCsr>(a, base + run + __popc(word & lt), W.oid[W.own[e]], a.P.id[q]);
+                }
+                run += __popc(word);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Filter-mode fringe chunk of the owner in slot 0: candidates at the sorted
+// positions [lo, lo + total) in rounds of 32, the next round's candidate values
+// loaded while the current round is tested; one decision bit per candidate, one
+// output reservation per segment of kBitWords rounds, then a replay of the set
+// bits.
+template <bool kCsr, bool kVerify>
+__device__ __forceinline__ void test_fringe_chunk(const QueryArgs &a, Meta *Mg, Meta *C, uint64_t obase, uint64_t cap,
+                                                  WarpSmem &W, uint32_t lo, uint32_t total, double coshR, bool verify)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const float4 va = W.oa[0], vb = W.ob[0];
+    const uint32_t idv = W.oid[0], pv = W.opos[0];
+    for (uint32_t seg = 0; seg < total; seg += kBitWords * 32) {
+        const uint32_t seg_end = total - seg > kBitWords * 32 ? seg + kBitWords * 32 : total;
+        int words = 0;
+        uint32_t edges = 0;
+        float2 aw = make_float2(0.0f, 0.0f);
+        float4 pw = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (seg + lane < seg_end) {
+            aw = a.P.ang[lo + seg + lane];
+            pw = a.P.pms[lo + seg + lane];
+        }
+        for (uint32_t j0 = seg; j0 < seg_end; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            const bool in = j < seg_end;
+            const float2 ac = aw;
+            const float4 pc = pw;
+            if (j + 32 < seg_end) {
+                aw = a.P.ang[lo + j + 32];
+                pw = a.P.pms[lo + j + 32];
+            }
+            const int dec = in ? filter_decide(va, vb, ac, pc) : 0;
+            const uint32_t um = __ballot_sync(full, dec == 2);
+            if (um) {
+                uint32_t rb = 0;
+                if (lane == 0) rb = atomicAdd(&C->recheck_n, static_cast<uint32_t>(__popc(um)));
+                rb = __shfl_sync(full, rb, 0);
+                if (dec == 2) {
+                    const uint32_t at = rb + __popc(um & lt);
+                    if (at < a.recheck_cap) a.recheck[at] = make_uint2(pv, lo + j);
+                    else atomicMax(&C->error, kErrListFull);
+                }
+            }
+            if (kVerify && verify && in && dec != 2) verify_pair(a, Mg, C, idv, a.P.id[lo + j], dec, coshR);
+            const uint32_t word = __ballot_sync(full, dec == 1);
+            if (lane == 0) W.bits[words] = word;
+            ++words;
+            edges += __popc(word);
+        }
+        __syncwarp();
+        unsigned long long base = 0;
+        if (lane == 0 && edges) base = atomicAdd(reinterpret_cast<unsigned long long *>(&Mg->m), edges);
+        base = __shfl_sync(full, base, 0);
+        if (edges && base + edges <= cap) {
+            base += obase;
+            uint32_t run = 0;
+#pragma unroll 4
+            for (int wi = 0; wi < words; ++wi) {
+                const uint32_t word = W.bits[wi];
+                if ((word >> lane) & 1u) {
+                    const uint32_t j = seg + static_cast<uint32_t>(wi) * 32 + lane;
+                    write_edge<kCsr>(a, base + run + __popc(word & lt), idv, __ldg(a.P.id + (lo + j)));
                 }
                 run += __popc(word);
             }
@@ -873,12 +931,7 @@ __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
         const bool core = (h.w & 1u) != 0;
         if (lane == 0) {
             load_owner<kFilter>(a.P, W, 0, h.x);
-            if (core) {
-                W.clo[0] = h.y;
-                W.cpre[0] = 0;
-                W.cpre[1] = h.z - h.y;
-                W.cown[0] = 0;
-            } else {
+            if (!core) {
                 W.lo[0] = h.y;
                 W.pre[0] = 0;
                 W.pre[1] = h.z - h.y;
@@ -886,7 +939,8 @@ __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
             }
         }
         __syncwarp();
-        if (core) flush_core<kCsr, kVerify>(a, Mg, C, obase, cap, W, 1, coshR, verify);
+        if (core) write_core_chunk<kCsr, kVerify>(a, Mg, C, obase, cap, W.oid[0], h.y, h.z - h.y, coshR, verify);
+        else if (kFilter) test_fringe_chunk<kCsr, kVerify>(a, Mg, C, obase, cap, W, h.y, h.z - h.y, coshR, verify);
         else flush<kFilter, kCsr, kVerify>(a, Mg, C, obase, cap, W, 1, coshR, verify, near);
         __syncwarp();
     }
