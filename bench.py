@@ -250,6 +250,25 @@ def bench_batched(args, rhg, torch, stream):
     ms = e0.elapsed_time(e1) / args.steps
     m = int(tot.m)
     points = sum(sp[0] for sp in specs)
+    # the same batch prepared once and captured in a CUDA graph, then replayed
+    plan = rhg.batch_prepare(buf, stream)
+    graph = rhg.capture_batch(plan, buf)
+    with torch.cuda.stream(stream):
+        graph.replay()
+    grc, _, gtot = rhg.batch_read_results(plan, buf, stream)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup - 1, 0)):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / args.steps
+    graph_replay = {"value": int(gtot.m) / (graph_ms / 1000.0), "ms_per_step": graph_ms,
+                    "edges_equal_default": grc == rhg.OK and int(gtot.m) == m}
+    del graph
     del buf
     # the plain path, one call per graph, reusing one workspace sized for the largest graph
     big = max(specs, key=lambda sp: sp[0])
@@ -295,7 +314,7 @@ def bench_batched(args, rhg, torch, stream):
              "edges_equal_default": int(ttot.m) == m,
              "band_offsets": {f"{lo}-{hi}": table.offsets.get(c, 0) for c, (lo, hi) in enumerate(table.classes)}}
     return {"value": value, "unit": "edges/s", "ms_per_step": ms, "graphs": len(specs), "points": points,
-            "autotuned_bands": tuned,
+            "autotuned_bands": tuned, "graph_replay": graph_replay,
             "edges": m, "exact_edges_equal_plain": plain_m == m, "plain_per_graph_value": plain,
             "plain_per_graph_ms": plain_ms, "speedup_vs_plain": value / plain,
             "stages_ms": {s: timer.totals[s] / max(args.steps, 1) for s in rhg.STAGES if s != "csr"},

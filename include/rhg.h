@@ -16,8 +16,8 @@
  * - The caller provides all device memory: a workspace whose size
  *   rhg_workspace_bytes() (or the entry point's own sizing call) reports, and
  *   the output buffers.  Inside an entry point the library allocates no device
- *   memory; rhg_generate_batch stages its per-graph tables in temporary host
- *   memory, the other entry points allocate none.
+ *   memory; rhg_generate_batch and rhg_batch_prepare stage their per-graph
+ *   tables in temporary host memory, the other entry points allocate none.
  * - Vertex ids are the Philox counter indices 0..n-1 (uint32).  An edge {u,v}
  *   is reported once as the pair (u, v) with u < v; the order of pairs is
  *   unspecified.  CSR rows list both directions with ascending columns.
@@ -267,6 +267,47 @@ int rhg_batch_workspace_bytes(const rhg_params *graphs, uint32_t count, size_t *
 int rhg_generate_batch(const rhg_params *graphs, uint32_t count, void *d_workspace,
                        size_t workspace_bytes, uint32_t *d_pairs, const uint64_t *pair_offsets,
                        void *stream, rhg_batch_graph *results, rhg_result *totals);
+
+/*
+ * The same batch split into a host step and a capturable device step, so that
+ * the device work can be recorded once in a CUDA graph and replayed.
+ *
+ * rhg_batch_prepare -- the host part of rhg_generate_batch (same arguments and
+ * argument errors): checks the graphs, cuts them into tiles and copies the
+ * per-graph tables into d_workspace (returns when the copy is done), and fills
+ * *plan (host).  The tables stay valid in d_workspace until it is reused.
+ *
+ * rhg_batch_launch -- enqueues every stage of the prepared batch on `stream`:
+ * kernel launches only, with no host memory, synchronisation or allocation, so
+ * it may run inside stream capture (cudaStreamBeginCapture).  Each launch or
+ * replay regenerates the same graphs into d_pairs (the layout of
+ * rhg_generate_batch, pair_capacity = pair_offsets[count] pairs) and the
+ * per-graph results into d_workspace.  plan must be the one rhg_batch_prepare
+ * filled for this d_workspace; a plan whose counts do not describe a workspace
+ * of plan->workspace_bytes returns RHG_ERR_INVALID_ARG.  Unlike
+ * rhg_generate_batch it never reruns a batch in FP64 mode: if the FP64 recheck
+ * list overflows, every graph reports RHG_ERR_OOM and rhg_generate_batch (which
+ * reruns) is the fallback.
+ *
+ * rhg_batch_read_results -- waits for `stream`, then fills results (count
+ * entries) and totals (optional) from the last launch, as rhg_generate_batch
+ * does, and returns the same status.
+ */
+typedef struct {
+    uint32_t count;            /* graphs                                        */
+    uint32_t verify;           /* 1 if some graph has RHG_FLAG_VERIFY            */
+    uint64_t num_tiles;        /* work tiles (at most 2048 points, one graph)   */
+    uint64_t points;           /* points of all graphs                          */
+    uint64_t index_entries;    /* bucket-index entries of all graphs            */
+    uint64_t pair_capacity;    /* pair_offsets[count]                           */
+    uint64_t workspace_bytes;  /* = rhg_batch_workspace_bytes of the graphs     */
+} rhg_batch_plan;
+
+int rhg_batch_prepare(const rhg_params *graphs, uint32_t count, const uint64_t *pair_offsets,
+                      void *d_workspace, size_t workspace_bytes, void *stream, rhg_batch_plan *plan);
+int rhg_batch_launch(const rhg_batch_plan *plan, void *d_workspace, uint32_t *d_pairs, void *stream);
+int rhg_batch_read_results(const rhg_batch_plan *plan, const void *d_workspace, void *stream,
+                           rhg_batch_graph *results, rhg_result *totals);
 
 /*
  * Dynamic model (Sec. III-C): vertices move in discrete steps, each a rotation

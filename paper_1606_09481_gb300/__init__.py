@@ -18,6 +18,7 @@ __all__ = [
     "RhgError", "Params", "Result", "BatchGraph", "load", "status_str", "target_radius", "plan", "workspace_bytes",
     "sample_points", "generate_pairs", "generate_pairs_host", "generate_pairs_static", "generate_csr",
     "edges_from_points", "batch_params", "batch_workspace_bytes", "allocate_batch", "run_batch", "generate_batch",
+    "BatchPlan", "batch_prepare", "batch_launch", "batch_read_results", "capture_batch",
     "draw_movement", "move_points", "update_edges", "dm_eval", "default_bands", "make_params", "estimate_capacity",
     "StageTimer", "launch_count", "FLAG_FP64_ONLY", "FLAG_VERIFY", "MAX_BANDS", "STATIC_MAX_POINTS", "build",
 ]
@@ -51,6 +52,12 @@ class BatchGraph(ctypes.Structure):
     """rhg_batch_graph: one graph's outcome in rhg_generate_batch."""
     _fields_ = [("m", _c_u64), ("R", _c_dbl), ("num_bands", _c_u32), ("status", ctypes.c_int32),
                 ("mode", _c_u32), ("reserved", _c_u32)]
+
+
+class BatchPlan(ctypes.Structure):
+    """rhg_batch_plan: the counts rhg_batch_prepare records for rhg_batch_launch."""
+    _fields_ = [("count", _c_u32), ("verify", _c_u32), ("num_tiles", _c_u64), ("points", _c_u64),
+                ("index_entries", _c_u64), ("pair_capacity", _c_u64), ("workspace_bytes", _c_u64)]
 
 
 class RhgError(RuntimeError):
@@ -88,6 +95,11 @@ def load() -> ctypes.CDLL:
     L.rhg_batch_workspace_bytes.argtypes = [ctypes.POINTER(Params), _c_u32, ctypes.POINTER(_c_size)]
     L.rhg_generate_batch.argtypes = [ctypes.POINTER(Params), _c_u32, _p, _c_size, _p, ctypes.POINTER(_c_u64), _p,
                                      ctypes.POINTER(BatchGraph), ctypes.POINTER(Result)]
+    L.rhg_batch_prepare.argtypes = [ctypes.POINTER(Params), _c_u32, ctypes.POINTER(_c_u64), _p, _c_size, _p,
+                                    ctypes.POINTER(BatchPlan)]
+    L.rhg_batch_launch.argtypes = [ctypes.POINTER(BatchPlan), _p, _p, _p]
+    L.rhg_batch_read_results.argtypes = [ctypes.POINTER(BatchPlan), _p, _p, ctypes.POINTER(BatchGraph),
+                                         ctypes.POINTER(Result)]
     L.rhg_draw_movement.argtypes = [_c_u64, _c_u64, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _p, _p, _p]
     L.rhg_move_points.argtypes = [_p, _c_u64, _c_u64, _p, _p, _p, _p, _c_dbl, _c_dbl, _p]
     L.rhg_workspace_bytes_update.argtypes = [_c_u64, _c_u64, _c_u32, ctypes.POINTER(_c_size)]
@@ -313,6 +325,41 @@ def run_batch(buf: BatchBuffers, stream=None):
     rc = load().rhg_generate_batch(buf.params, G, buf.ws.data_ptr(), buf.ws.numel(), buf.out.data_ptr(),
                                    buf.offsets, _stream(stream), res, ctypes.byref(tot))
     return rc, res, tot
+
+
+def batch_prepare(buf: BatchBuffers, stream=None) -> BatchPlan:
+    """rhg_batch_prepare: check the graphs of `buf` and copy their tables into its
+    workspace; the plan is what rhg_batch_launch needs."""
+    plan = BatchPlan()
+    _check(load().rhg_batch_prepare(buf.params, len(buf.params), buf.offsets, buf.ws.data_ptr(), buf.ws.numel(),
+                                    _stream(stream), ctypes.byref(plan)), "rhg_batch_prepare")
+    return plan
+
+
+def batch_launch(plan: BatchPlan, buf: BatchBuffers, stream=None) -> None:
+    """rhg_batch_launch: enqueue the prepared batch (kernel launches only; may be
+    captured into a CUDA graph)."""
+    _check(load().rhg_batch_launch(ctypes.byref(plan), buf.ws.data_ptr(), buf.out.data_ptr(), _stream(stream)),
+           "rhg_batch_launch")
+
+
+def batch_read_results(plan: BatchPlan, buf: BatchBuffers, stream=None):
+    """rhg_batch_read_results after a launch or replay: (status, [BatchGraph], totals)."""
+    res = (BatchGraph * plan.count)()
+    tot = Result()
+    rc = load().rhg_batch_read_results(ctypes.byref(plan), buf.ws.data_ptr(), _stream(stream), res,
+                                       ctypes.byref(tot))
+    return rc, res, tot
+
+
+def capture_batch(plan: BatchPlan, buf: BatchBuffers):
+    """A torch.cuda.CUDAGraph holding one rhg_batch_launch of the prepared batch;
+    graph.replay() regenerates the batch into buf.out."""
+    torch = _torch()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch_launch(plan, buf)
+    return graph
 
 
 def generate_batch(specs, flags=0, num_bands=0, band_ratio=0.0, stream=None):

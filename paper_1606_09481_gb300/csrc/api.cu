@@ -383,7 +383,8 @@ int batch_host(const rhg_params *graphs, uint32_t count, const uint64_t *pair_of
     return RHG_OK;
 }
 
-BatchLayout batch_layout(const BatchHost &h)
+// Byte offsets of a batch's buffers from its graph, point, tile and index counts.
+BatchLayout batch_layout(uint64_t G, uint64_t N, uint64_t num_tiles, uint64_t idx_total)
 {
     BatchLayout L{};
     size_t o = 0;
@@ -392,7 +393,6 @@ BatchLayout batch_layout(const BatchHost &h)
         o = align_up(o + bytes);
         return at;
     };
-    const uint64_t N = h.N, G = h.G;
     L.heavy_cap = static_cast<uint32_t>(N / 4 + 65536);
     L.recheck_cap = static_cast<uint32_t>(N / 2 + 65536);
     L.metas = take((G + 1) * sizeof(Meta));
@@ -401,7 +401,7 @@ BatchLayout batch_layout(const BatchHost &h)
     o += G * sizeof(PlanArgs);
     o = (o + 15) & ~size_t{15};
     L.tiles = o;
-    o += h.tiles.size() * sizeof(uint4);
+    o += num_tiles * sizeof(uint4);
     L.tile_first = o;
     o += (G + 1) * 4;
     L.pt_off = o;
@@ -427,13 +427,15 @@ BatchLayout batch_layout(const BatchHost &h)
     L.r = take(N * 8);
     L.ch = take(N * 8);
     L.sh = take(N * 8);
-    L.bidx = take(h.idx_total * 4);
+    L.bidx = take(idx_total * 4);
     L.heavy = take(static_cast<size_t>(L.heavy_cap) * 16);
     L.recheck = take(static_cast<size_t>(L.recheck_cap) * 8);
-    L.sort_tmp = take(segmented_temp_bytes(static_cast<uint32_t>(h.tiles.size())));
+    L.sort_tmp = take(segmented_temp_bytes(static_cast<uint32_t>(num_tiles)));
     L.total = o;
     return L;
 }
+
+BatchLayout batch_layout(const BatchHost &h) { return batch_layout(h.G, h.N, h.tiles.size(), h.idx_total); }
 
 // Copies the tables into the workspace (pageable source: returns when copied).
 Status upload_tables(void *ws, const BatchLayout &L, const BatchHost &h, cudaStream_t stream)
@@ -454,11 +456,11 @@ Status upload_tables(void *ws, const BatchLayout &L, const BatchHost &h, cudaStr
     return st;
 }
 
-BatchTables batch_tables(void *ws, const BatchLayout &L, const BatchHost &h)
+BatchTables batch_tables(void *ws, const BatchLayout &L, uint32_t G, uint64_t num_tiles)
 {
     BatchTables bt;
-    bt.G = h.G;
-    bt.num_tiles = static_cast<uint32_t>(h.tiles.size());
+    bt.G = G;
+    bt.num_tiles = static_cast<uint32_t>(num_tiles);
     bt.tiles = at<uint4>(ws, L.tiles);
     bt.tile_first = at<uint32_t>(ws, L.tile_first);
     bt.pt_off = at<uint32_t>(ws, L.pt_off);
@@ -468,14 +470,17 @@ BatchTables batch_tables(void *ws, const BatchLayout &L, const BatchHost &h)
 }
 
 // Every stage of the batch on the stream: plan (all graphs), sample, band
-// offsets, segmented sort, gather, bucket index and range query, results.
-Status enqueue_batch(void *ws, const BatchLayout &L, const BatchHost &h, uint32_t *d_pairs, cudaStream_t stream)
+// offsets, segmented sort, gather, bucket index and range query, results.  Only
+// kernel launches (and stage events when timing is on): no host memory, no
+// synchronisation, so the sequence can be captured into a CUDA graph.
+Status enqueue_batch(void *ws, const BatchLayout &L, uint32_t G, uint64_t N, uint64_t num_tiles, bool verify,
+                     uint32_t *d_pairs, cudaStream_t stream)
 {
     Status st;
     Meta *metas = at<Meta>(ws, L.metas);
-    const BatchTables bt = batch_tables(ws, L, h);
+    const BatchTables bt = batch_tables(ws, L, G, num_tiles);
     mark(RHG_STAGE_PLAN, false, stream);
-    st = launch_plan_batch(metas, at<PlanArgs>(ws, L.args), h.G, stream);
+    st = launch_plan_batch(metas, at<PlanArgs>(ws, L.args), G, stream);
     if (st.code) return st;
     mark(RHG_STAGE_PLAN, true, stream);
     uint64_t *k0 = at<uint64_t>(ws, L.keys0), *k1 = at<uint64_t>(ws, L.keys1);
@@ -495,7 +500,7 @@ Status enqueue_batch(void *ws, const BatchLayout &L, const BatchHost &h, uint32_
     if (st.code) return st;
     mark(RHG_STAGE_SORT, true, stream);
     SortedPoints P;
-    P.n = h.N;
+    P.n = N;
     P.key = ks;
     P.akey = at<uint32_t>(ws, L.akey);
     P.id = at<uint32_t>(ws, L.id);
@@ -519,12 +524,53 @@ Status enqueue_batch(void *ws, const BatchLayout &L, const BatchHost &h, uint32_
     q.recheck = at<uint2>(ws, L.recheck);
     q.recheck_cap = L.recheck_cap;
     q.bidx = at<uint32_t>(ws, L.bidx);
-    for (const PlanArgs &g : h.args) q.verify = q.verify || g.verify != 0;
+    q.verify = verify;
     mark(RHG_STAGE_QUERY, false, stream);
     st = launch_query_batch(q, stream);
     if (st.code) return st;
     mark(RHG_STAGE_QUERY, true, stream);
-    return launch_batch_results(metas, h.G, at<uint4>(ws, L.results), stream);
+    return launch_batch_results(metas, G, at<uint4>(ws, L.results), stream);
+}
+
+bool any_verify(const BatchHost &h)
+{
+    for (const PlanArgs &g : h.args)
+        if (g.verify) return true;
+    return false;
+}
+
+// Per-graph results and totals from the device results table (two uint4 per
+// graph), the batch's control block and the pair offsets.
+int fill_batch_results(uint32_t count, const uint4 *res, const Meta &ctl, const uint64_t *out_off,
+                       rhg_batch_graph *results, rhg_result *totals)
+{
+    int rc = RHG_OK;
+    uint64_t total_m = 0;
+    uint32_t all_filter = 1;
+    for (uint32_t g = 0; g < count; ++g) {
+        const uint4 a = res[2 * g], b = res[2 * g + 1];
+        rhg_batch_graph &r = results[g];
+        r.m = static_cast<uint64_t>(a.x) | (static_cast<uint64_t>(a.y) << 32);
+        const uint64_t Rb = static_cast<uint64_t>(a.z) | (static_cast<uint64_t>(a.w) << 32);
+        std::memcpy(&r.R, &Rb, sizeof(double));
+        r.num_bands = b.x;
+        r.mode = b.z ? 1u : 0u;
+        r.status = ctl.error ? error_from_meta(ctl.error) : error_from_meta(b.y);
+        if (r.status == RHG_OK && r.m > out_off[g + 1] - out_off[g]) r.status = RHG_ERR_OVERFLOW;
+        if (r.status == RHG_OK) total_m += r.m;
+        if (!r.mode) all_filter = 0;
+        if (rc == RHG_OK && r.status != RHG_OK) rc = r.status;
+    }
+    if (totals) {
+        totals->m = total_m;
+        totals->candidates = ctl.candidates;
+        totals->near_threshold = ctl.near_threshold;
+        totals->rechecks = ctl.rechecks;
+        totals->verify_failures = ctl.verify_failures;
+        totals->heavy_chunks = ctl.heavy_n;
+        totals->mode = all_filter;
+    }
+    return rc;
 }
 
 // ------------------------------------------------------------------ dynamic
@@ -585,6 +631,15 @@ int static_scratch(void **ptr, cudaError_t *err)
     return RHG_OK;
 }
 
+// The layout a plan describes; false if the plan is not one rhg_batch_prepare made.
+bool plan_layout(const rhg_batch_plan *plan, BatchLayout &L)
+{
+    if (!plan || plan->count == 0 || plan->count > kMaxBatch || plan->num_tiles < plan->count ||
+        plan->points >= 0xFFFFFFFFull || plan->index_entries >= 0xFFFFFFFFull || plan->verify > 1)
+        return false;
+    L = batch_layout(plan->count, plan->points, plan->num_tiles, plan->index_entries);
+    return L.total == plan->workspace_bytes;
+}
 }  // namespace
 }  // namespace rhg
 
@@ -814,7 +869,7 @@ int rhg_generate_batch(const rhg_params *graphs, uint32_t count, void *d_workspa
     for (int attempt = 0; attempt < 2; ++attempt) {
         Status st = upload_tables(d_workspace, L, h, s);
         if (st.code) return finish(st, totals);
-        st = enqueue_batch(d_workspace, L, h, d_pairs, s);
+        st = enqueue_batch(d_workspace, L, h.G, h.N, h.tiles.size(), any_verify(h), d_pairs, s);
         if (st.code) return finish(st, totals);
         const cudaError_t e1 = cudaMemcpyAsync(res.data(), at<uint4>(d_workspace, L.results),
                                                res.size() * sizeof(uint4), cudaMemcpyDeviceToHost, s);
@@ -829,33 +884,68 @@ int rhg_generate_batch(const rhg_params *graphs, uint32_t count, void *d_workspa
         if (ctl.error != kErrListFull || attempt) break;
         for (auto &a : h.args) a.allow_filter = 0;  // the FP64 mode needs no recheck list
     }
-    rc = RHG_OK;
-    uint64_t total_m = 0;
-    uint32_t all_filter = 1;
-    for (uint32_t g = 0; g < count; ++g) {
-        const uint4 a = res[2 * g], b = res[2 * g + 1];
-        rhg_batch_graph &r = results[g];
-        r.m = static_cast<uint64_t>(a.x) | (static_cast<uint64_t>(a.y) << 32);
-        const uint64_t Rb = static_cast<uint64_t>(a.z) | (static_cast<uint64_t>(a.w) << 32);
-        std::memcpy(&r.R, &Rb, sizeof(double));
-        r.num_bands = b.x;
-        r.mode = b.z ? 1u : 0u;
-        r.status = ctl.error ? error_from_meta(ctl.error) : error_from_meta(b.y);
-        if (r.status == RHG_OK && r.m > h.out_off[g + 1] - h.out_off[g]) r.status = RHG_ERR_OVERFLOW;
-        if (r.status == RHG_OK) total_m += r.m;
-        if (!r.mode) all_filter = 0;
-        if (rc == RHG_OK && r.status != RHG_OK) rc = r.status;
+    return fill_batch_results(count, res.data(), ctl, h.out_off.data(), results, totals);
+}
+
+int rhg_batch_prepare(const rhg_params *graphs, uint32_t count, const uint64_t *pair_offsets, void *d_workspace,
+                      size_t workspace_bytes, void *stream, rhg_batch_plan *plan)
+{
+    if (plan) std::memset(plan, 0, sizeof(*plan));
+    if (!d_workspace || !pair_offsets || !plan) return RHG_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_workspace) & 255) return RHG_ERR_INVALID_ARG;
+    BatchHost h;
+    const int rc = batch_host(graphs, count, pair_offsets, h);
+    if (rc) return rc;
+    const BatchLayout L = batch_layout(h);
+    if (workspace_bytes < L.total) return RHG_ERR_OOM;
+    const Status st = upload_tables(d_workspace, L, h, static_cast<cudaStream_t>(stream));
+    if (st.code) return st.code;
+    plan->count = count;
+    plan->verify = any_verify(h) ? 1u : 0u;
+    plan->num_tiles = h.tiles.size();
+    plan->points = h.N;
+    plan->index_entries = h.idx_total;
+    plan->pair_capacity = h.out_off[count];
+    plan->workspace_bytes = L.total;
+    return RHG_OK;
+}
+
+int rhg_batch_launch(const rhg_batch_plan *plan, void *d_workspace, uint32_t *d_pairs, void *stream)
+{
+    BatchLayout L;
+    if (!plan_layout(plan, L) || !d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+        return RHG_ERR_INVALID_ARG;
+    if (plan->pair_capacity && (!d_pairs || (reinterpret_cast<uintptr_t>(d_pairs) & 7))) return RHG_ERR_INVALID_ARG;
+    const Status st = enqueue_batch(d_workspace, L, plan->count, plan->points, plan->num_tiles, plan->verify != 0,
+                                    d_pairs, static_cast<cudaStream_t>(stream));
+    return st.code;
+}
+
+int rhg_batch_read_results(const rhg_batch_plan *plan, const void *d_workspace, void *stream,
+                           rhg_batch_graph *results, rhg_result *totals)
+{
+    if (totals) std::memset(totals, 0, sizeof(*totals));
+    BatchLayout L;
+    if (!plan_layout(plan, L) || !d_workspace || !results) return RHG_ERR_INVALID_ARG;
+    const uint32_t count = plan->count;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<uint4> res(2 * static_cast<size_t>(count));
+    std::vector<uint64_t> out_off(static_cast<size_t>(count) + 1);
+    Meta ctl;
+    const char *ws = static_cast<const char *>(d_workspace);
+    const cudaError_t e1 =
+        cudaMemcpyAsync(res.data(), ws + L.results, res.size() * sizeof(uint4), cudaMemcpyDeviceToHost, s);
+    const cudaError_t e2 = cudaMemcpyAsync(&ctl, ws + L.metas + count * sizeof(Meta), sizeof(Meta),
+                                           cudaMemcpyDeviceToHost, s);
+    const cudaError_t e3 =
+        cudaMemcpyAsync(out_off.data(), ws + L.out_off, out_off.size() * 8, cudaMemcpyDeviceToHost, s);
+    const cudaError_t e4 = cudaStreamSynchronize(s);
+    const cudaError_t e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4;
+    if (e != cudaSuccess) {
+        if (totals) totals->cuda_error = static_cast<int32_t>(e);
+        return RHG_ERR_CUDA;
     }
-    if (totals) {
-        totals->m = total_m;
-        totals->candidates = ctl.candidates;
-        totals->near_threshold = ctl.near_threshold;
-        totals->rechecks = ctl.rechecks;
-        totals->verify_failures = ctl.verify_failures;
-        totals->heavy_chunks = ctl.heavy_n;
-        totals->mode = all_filter;
-    }
-    return rc;
+    return fill_batch_results(count, res.data(), ctl, out_off.data(), results, totals);
 }
 
 int rhg_draw_movement(uint64_t n, uint64_t seed, double phi_lo, double phi_hi, double r_lo, double r_hi,

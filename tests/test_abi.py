@@ -90,3 +90,26 @@ def test_product_package_does_not_touch_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 for bad in ("import oracle", "from oracle", "rhg_oracle", "librhg_oracle"):
                     assert bad not in txt, (f, bad)
+
+
+def test_batch_plan_layout_and_validation(rhg):
+    """rhg_batch_plan matches the header; plans that rhg_batch_prepare did not
+    make, and missing buffers, are refused on the host."""
+    assert ctypes.sizeof(rhg.BatchPlan) == 48
+    L = rhg.load()
+    params = rhg.batch_params([(1000, 8, 1.0, 1), (3000, 10, 0.8, 2)])
+    offs = (ctypes.c_uint64 * 3)(0, 10_000, 30_000)
+    plan = rhg.BatchPlan()
+    assert L.rhg_batch_prepare(params, 2, offs, None, 1 << 30, None, ctypes.byref(plan)) == rhg.INVALID_ARG
+    assert L.rhg_batch_prepare(params, 2, None, 256, 1 << 30, None, ctypes.byref(plan)) == rhg.INVALID_ARG
+    assert L.rhg_batch_prepare(params, 0, offs, 256, 1 << 30, None, ctypes.byref(plan)) == rhg.INVALID_ARG
+    assert L.rhg_batch_prepare(params, 2, offs, 256, 16, None, ctypes.byref(plan)) == rhg.OOM
+    # a plan with counts that describe no workspace of its size
+    fake = rhg.BatchPlan(count=2, verify=0, num_tiles=3, points=4000, index_entries=4000, pair_capacity=30_000,
+                         workspace_bytes=12345)
+    assert L.rhg_batch_launch(ctypes.byref(fake), 256, 256, None) == rhg.INVALID_ARG
+    assert L.rhg_batch_launch(None, 256, 256, None) == rhg.INVALID_ARG
+    zero = rhg.BatchPlan()
+    assert L.rhg_batch_launch(ctypes.byref(zero), 256, 256, None) == rhg.INVALID_ARG
+    res = (rhg.BatchGraph * 2)()
+    assert L.rhg_batch_read_results(ctypes.byref(fake), 256, None, res, None) == rhg.INVALID_ARG

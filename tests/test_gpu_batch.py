@@ -111,3 +111,32 @@ def test_autotuned_band_counts_give_the_same_graphs():
     for g in range(len(specs)):
         assert r2[g].num_bands == table.bands(specs[g][0])
         assert np.array_equal(sorted_pairs(v1[g]), sorted_pairs(v2[g])), g
+
+
+def test_captured_batch_replays_the_same_graphs():
+    """rhg_batch_prepare once, rhg_batch_launch captured in a CUDA graph: the
+    direct launch and every replay give exactly the graphs of rhg_generate_batch."""
+    rhg = require_gpu()
+    import torch
+    want, wres, wtot = rhg.generate_batch(MIXED)
+    params = rhg.batch_params(MIXED)
+    buf = rhg.allocate_batch(params, [max(int(r.m), 1) + 7 for r in wres])
+    plan = rhg.batch_prepare(buf)
+    assert plan.count == len(MIXED) and plan.points == sum(sp[0] for sp in MIXED)
+    assert plan.workspace_bytes == rhg.batch_workspace_bytes(params)
+
+    def check():
+        rc, res, tot = rhg.batch_read_results(plan, buf)
+        assert rc == rhg.OK and tot.m == wtot.m
+        for g in range(len(MIXED)):
+            assert res[g].m == wres[g].m and res[g].R == wres[g].R and res[g].status == rhg.OK
+            got = buf.out[2 * buf.offsets[g]: 2 * (buf.offsets[g] + res[g].m)].view(-1, 2)
+            assert np.array_equal(sorted_pairs(got), sorted_pairs(want[g])), g
+
+    rhg.batch_launch(plan, buf)
+    check()
+    graph = rhg.capture_batch(plan, buf)
+    for _ in range(2):
+        buf.out.fill_(-1)
+        graph.replay()
+        check()
