@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
             L.ro_prepared_count.argtypes = [_p, _p, _u64, _p]
             L.ro_prepared_count.restype = _i64
             L.ro_prepared_free.argtypes = [_p]
+            L.ro_set_threads.argtypes = [ctypes.c_int32]
             L.ro_asinh.restype = _dbl
             L.ro_asinh.argtypes = [_dbl]
             L.ro_draw_movement.argtypes = [_u64, _u64, _dbl, _dbl, _dbl, _dbl, _p, _p]
@@ -291,10 +292,17 @@ class Prepared:
         if not self.h:
             raise MemoryError("ro_prepare failed")
 
-    def count_edges(self, ids):
+    def count_edges(self, ids, threads: int = 0):
+        """(edges, threads used); threads > 0 caps the OpenMP threads for this call."""
         ids = np.ascontiguousarray(ids, dtype=np.uint32)
         nt = ctypes.c_int32(0)
-        m = lib().ro_prepared_count(self.h, _ptr(ids), len(ids), ctypes.byref(nt))
+        if threads > 0:
+            lib().ro_set_threads(threads)
+        try:
+            m = lib().ro_prepared_count(self.h, _ptr(ids), len(ids), ctypes.byref(nt))
+        finally:
+            if threads > 0:
+                lib().ro_set_threads(0)
         return int(m), int(nt.value)
 
     def close(self):

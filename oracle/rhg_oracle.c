@@ -674,6 +674,19 @@ int64_t ro_band_count_subset(uint64_t n, const double *phi, const double *r, dou
     return m;
 }
 
+/* Threads of the calling thread's next OpenMP regions (the timed baseline is
+ * reported on one thread and on all cores); nt <= 0 restores the default. */
+void ro_set_threads(int32_t nt)
+{
+#ifdef _OPENMP
+    static int initial = 0;
+    if (!initial) initial = omp_get_max_threads();
+    omp_set_num_threads(nt > 0 ? nt : initial);
+#else
+    (void)nt;
+#endif
+}
+
 int ro_openmp_threads(void)
 {
 #ifdef _OPENMP

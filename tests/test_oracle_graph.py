@@ -80,3 +80,24 @@ def test_statistics_config2(O):
     assert abs(gamma - (2 * alpha + 1)) < 0.35, gamma
     assert g["stats"]["candidates"] >= len(pairs)
     assert g["stats"]["candidates"] < 3 * len(pairs)
+
+
+def test_timed_baseline_counts_the_outward_edges(O):
+    """The timed CPU baseline (band structure built once, outward queries of a
+    vertex set) counts each edge from its outward endpoint: over all vertices it
+    gives the all-pairs edge count, on one thread and on all threads alike."""
+    n, k, alpha, seed = 3000, 12, 0.75, 7
+    R = O.target_radius(n, k, alpha)
+    phi, r = O.sample_points(n, alpha, R, seed)
+    m = len(O.brute_edges(phi, r, R))
+    prep = O.Prepared(phi, r, R, O.default_bands(n), 0.9)
+    try:
+        ids = np.arange(n, dtype=np.uint32)
+        m_all, threads = prep.count_edges(ids)
+        m_one, one = prep.count_edges(ids, threads=1)
+        assert m_all == m_one == m
+        assert one == 1 and threads == O.openmp_threads()
+        halves = prep.count_edges(ids[: n // 2])[0] + prep.count_edges(ids[n // 2:])[0]
+        assert halves == m
+    finally:
+        prep.close()
