@@ -367,6 +367,9 @@ int rhg_dm_eval(int fn, const double *d_in, double *d_out, uint64_t count, void 
  * before and after stage s, for s < count / 2 and s < RHG_NUM_STAGES, so that
  * cudaEventElapsedTime gives each stage's device time.  Process-wide and not
  * thread-safe; NULL switches it off.  Stages that do not run record nothing.
+ * Independently of this, every stage is an NVTX range ("rhg.plan",
+ * "rhg.sample", "rhg.sort", "rhg.gather", "rhg.query", "rhg.csr") on the calling
+ * thread, for Nsight tools.
  *
  * rhg_launch_count -- number of kernels this library has launched in this
  * process so far (all devices, all threads).

@@ -1,13 +1,16 @@
 // api.cu -- the extern "C" entry points declared in include/rhg.h: argument
 // validation, workspace layout, and the stream-ordered pipeline
-//   plan -> sample -> band offsets -> radix sort -> gather -> query count ->
-//   scan -> (one 64-byte D2H of the metadata) -> query emit [-> CSR sort/finish].
+//   plan -> sample -> band offsets -> radix sort -> gather -> bucket index ->
+//   range query (edges reserved per warp and band) -> FP64 recheck
+//   [-> CSR sort/finish] -> one D2H of the metadata (m, R, counters).
 #include <atomic>
 #include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "kernels.h"
 
@@ -22,8 +25,22 @@ namespace {
 void *const *g_events = nullptr;
 uint32_t g_num_events = 0;
 
+// Stage boundaries: an NVTX range per stage on the calling thread (seen by
+// Nsight tools; a few nanoseconds without one) and, when rhg_set_stage_events
+// is on, the caller's events on the stream.
 void mark(uint32_t stage, bool end, cudaStream_t s)
 {
+    static const char *const kStageNames[RHG_NUM_STAGES] = {"rhg.plan", "rhg.sample", "rhg.sort",
+                                                            "rhg.gather", "rhg.query", "rhg.csr"};
+    thread_local nvtxRangeId_t open[RHG_NUM_STAGES] = {};
+    if (stage < RHG_NUM_STAGES) {
+        if (!end) {
+            open[stage] = nvtxRangeStartA(kStageNames[stage]);
+        } else if (open[stage]) {
+            nvtxRangeEnd(open[stage]);
+            open[stage] = 0;
+        }
+    }
     const uint32_t i = 2 * stage + (end ? 1 : 0);
     if (g_events && i < g_num_events && g_events[i])
         cudaEventRecord(static_cast<cudaEvent_t>(g_events[i]), s);
