@@ -26,7 +26,11 @@ def test_config1_equals_brute_force(O):
 
 SMALL = [(2, 0.5, 1.0, 1), (3, 1, 1.0, 2), (17, 4, 0.8, 3), (100, 6, 1.0, 4), (257, 10, 0.55, 5),
          (1000, 30, 0.6, 6), (2047, 6, 1.0, 7), (2049, 6, 1.0, 8), (4097, 12, 0.75, 9), (5000, 3, 3.0, 10),
-         (3000, 60, 1.5, 11), (6000, 1, 1.0, 12), (8191, 8, 0.9, 2**40 + 3)]
+         (3000, 60, 1.5, 11), (6000, 1, 1.0, 12), (8191, 8, 0.9, 2**40 + 3),
+         # dense graphs with small R (core and fringe chunks of the heavy kernel), a
+         # steep radial density, and the largest seed
+         (500, 200, 1.0, 13), (2000, 600, 0.6, 16), (8000, 1000, 0.7, 15), (3000, 8, 10.0, 14),
+         (4000, 10, 1.0, 2**64 - 1)]
 
 
 @pytest.mark.parametrize("n,k,alpha,seed", SMALL)
