@@ -188,6 +188,12 @@ def cpu_baseline(args, budget_s: float = 20.0, steps: int = 1):
     m1, _ = prep.count_edges(ids1, threads=1)
     t1 = time.perf_counter() - t0 + (t_points + t_bands) * size1 / n
     prep.close()
+    # the O(n^2) all-pairs definition on the small plain graph (n = 10^4, k = 6, alpha = 1, seed 1)
+    R1 = oracle.target_radius(10_000, 6, 1.0)
+    phi1, r1 = oracle.sample_points(10_000, 1.0, R1, 1)
+    t0 = time.perf_counter()
+    mb = len(oracle.brute_edges(phi1, r1, R1))
+    tb = time.perf_counter() - t0
     info = {"value": value, "unit": "edges/s", "cores": threads, "kind": "oracle",
             "sample": (f"outward range queries of {size} random vertices per step x {steps} step(s) on the full "
                        f"n={n} point set ({total_edges} edges); point sampling ({t_points:.1f} s, 1 thread) and "
@@ -195,7 +201,9 @@ def cpu_baseline(args, budget_s: float = 20.0, steps: int = 1):
             "seconds": total_time,
             "single_thread": {"value": m1 / t1, "unit": "edges/s", "cores": 1,
                               "sample": f"outward range queries of {size1} random vertices ({m1} edges), set-up "
-                                        f"charged pro rata"}}
+                                        f"charged pro rata"},
+            "all_pairs_small": {"value": mb / tb, "unit": "edges/s", "cores": 1, "seconds": tb,
+                                "sample": f"O(n^2) all pairs of n=10000, k=6, alpha=1, seed 1 ({mb} edges)"}}
     return value, info
 
 
