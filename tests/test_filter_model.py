@@ -1,0 +1,159 @@
+"""The FP32 filter's error model, checked on the CPU.
+
+The device decides a candidate pair in FP32 (X = P_v M_w + M_v P_w +
+2 S_v S_w sin^2(d/2), which is Eq. 3 divided by cosh R) only when |X - 1|
+exceeds its error bound; every other pair goes to the FP64 predicate.  This
+test restates that arithmetic in numpy float32, operation by operation
+(filter values as the gather stores them, then the decision), perturbs the
+radius by the largest error of the FP32-assisted sampler radius, and checks on
+adversarial pairs right at the threshold, across the 0/2pi seam, on the rim,
+near the origin and at R close to the filter's limit, that no decided pair
+contradicts the oracle's FP64 predicate.  The constants are read from the
+CUDA sources, so the test follows them.
+"""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1606_09481_gb300", "csrc")
+f32, f64 = np.float32, np.float64
+
+
+def _constants():
+    src = open(os.path.join(CSRC, "common.cuh")).read() + open(os.path.join(CSRC, "query.cu")).read()
+    out = {}
+    for name in ("kEpsPM", "kEps32", "kCBase", "kAngAbs", "kC64", "kPiF", "kTwoPiHiF", "kTwoPiLoF"):
+        m = re.search(r"constexpr float %s = ([-0-9.eE+]+)f;" % name, src)
+        assert m, name
+        out[name] = f32(float(m.group(1)))
+    m = re.search(r"constexpr double kDeltaR = ([-0-9.eE+]+);", src)
+    out["kDeltaR"] = float(m.group(1))
+    m = re.search(r"constexpr int kExpTab = (\d+);", src)
+    out["kExpTab"] = int(m.group(1))
+    return out
+
+
+C = _constants()
+
+
+def fma(a, b, c):
+    """fmaf: the float32 product is exact in float64, one rounding of the sum (a
+    second rounding to float32 differs from a single one only at exact ties)."""
+    return (np.asarray(a, f64) * np.asarray(b, f64) + np.asarray(c, f64)).astype(f32)
+
+
+def filter_values(ph, r, G):
+    """Angle hi/lo and (P, M, S, gamma) of points with FP64 angle ph and radius r."""
+    K = C["kExpTab"]
+    etab = np.exp(np.arange(-K, K + 1, dtype=f64)).astype(f32)
+    hi = ph.astype(f32)
+    lo = (ph - hi.astype(f64)).astype(f32)
+
+    def exp_split(x):
+        kd = np.rint(x)
+        f = (x - kd).astype(f32)
+        return (etab[kd.astype(np.int64) + K] * np.exp(f)).astype(f32)
+
+    P, M = exp_split(r - G), exp_split(-r - G)
+    big = r >= 1.0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        S_big = ((P - M) * f32(0.70710678118654752)).astype(f32)
+        g_big = (C["kEpsPM"] * ((P + M) / (P - M)) + f32(2.0) * C["kEps32"]).astype(f32)
+        S_small = (np.sinh(r) * math.exp(-G) * 1.4142135623730951).astype(f32)
+        g_small = (C["kEpsPM"] * (np.cosh(r) / np.sinh(r)).astype(f32) + f32(2.0) * C["kEps32"]).astype(f32)
+    S = np.where(big, S_big, np.where(r > 0, S_small, f32(0))).astype(f32)
+    gam = np.where(big, g_big, np.where(r > 0, g_small, f32(0))).astype(f32)
+    return hi, lo, P, M, S, gam
+
+
+def filter_decide(v, w):
+    """1 = edge, 0 = no edge, 2 = undecided, for owner values v and candidate w
+    (tuples from filter_values)."""
+    vhi, vlo, Pv, Mv, Sv, gv = v
+    whi, wlo, Pw, Mw, Sw, gw = w
+    S2v, PMv, cv = (f32(2.0) * Sv).astype(f32), (Pv + Mv).astype(f32), (C["kCBase"] + gv).astype(f32)
+    dh = (vhi - whi).astype(f32)
+    d_plain = np.abs((dh + (vlo - wlo).astype(f32)).astype(f32))
+    vbig = dh > 0
+    bh, bl = np.where(vbig, vhi, whi), np.where(vbig, vlo, wlo)
+    sh, sl = np.where(vbig, whi, vhi), np.where(vbig, wlo, vlo)
+    d_wrap = ((((C["kTwoPiHiF"] - bh).astype(f32) + sh).astype(f32)
+               + ((C["kTwoPiLoF"] - bl).astype(f32) + sl).astype(f32)).astype(f32))
+    d = np.where(np.abs(dh) > C["kPiF"], d_wrap, d_plain).astype(f32)
+    x = (f32(0.5) * d).astype(f32)
+    z = (x * x).astype(f32)
+    zx = (z * x).astype(f32)
+    t_small = fma(zx, f32(-0.166666672), x)
+    t = fma(z, f32(-2.50521079e-08), f32(2.75573188e-06))
+    t = fma(z, t, f32(-1.98412701e-04))
+    t = fma(z, t, f32(8.33333377e-03))
+    t = fma(z, t, f32(-1.66666672e-01))
+    t = np.where(x < f32(0.0078125), t_small, fma(zx, t, x)).astype(f32)
+    ss = (S2v * Sw).astype(f32)
+    sst = (ss * t).astype(f32)
+    X = fma(sst, t, fma(Pv, Mw, (Mv * Pw).astype(f32)))
+    err = fma(X, (cv + gw).astype(f32),
+              fma((C["kC64"] * PMv).astype(f32), (Pw + Mw).astype(f32), (sst * C["kAngAbs"]).astype(f32)))
+    return np.where((X + err).astype(f32) <= 1, 1, np.where((X - err).astype(f32) > 1, 0, 2))
+
+
+def _pairs(rng, R, count):
+    """Radii from several regimes, angles at the exact threshold angle times
+    (1 + delta) with |delta| from 1e-9 to 1e-1, half of them across the seam."""
+    kind = rng.integers(0, 4, count)
+    rv = np.where(kind == 0, rng.uniform(0, R, count), np.where(kind == 1, R - rng.exponential(1.0, count),
+                  np.where(kind == 2, rng.uniform(0, 1.5, count), R - rng.exponential(0.2, count))))
+    rw = np.where(kind == 3, R - rng.exponential(0.2, count), R - rng.exponential(2.0, count))
+    rv, rw = np.clip(rv, 0, R), np.clip(rw, 0, R)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        A = (np.cosh(rv) * np.cosh(rw) - math.cosh(R)) / (np.sinh(rv) * np.sinh(rw))
+    theta = np.arccos(np.clip(np.nan_to_num(A, nan=1.0), -1.0, 1.0))
+    delta = rng.choice([-1.0, 1.0], count) * 10.0 ** rng.uniform(-9, -1, count)
+    dphi = np.clip(theta * (1 + delta), 0, math.pi)
+    phv = np.where(rng.random(count) < 0.5, rng.uniform(0, 1e-3, count), rng.uniform(0, 2 * math.pi, count))
+    phw = np.mod(phv - dphi, 2 * math.pi)
+    phw = np.where(phw >= 2 * math.pi, np.nextafter(2 * math.pi, 0), phw)
+    return phv, rv, phw, rw, delta
+
+
+@pytest.mark.parametrize("R", [3.0046, 16.705, 23.5089, 25.564, 31.9])
+def test_filter_decisions_are_sound(O, R):
+    rng = np.random.default_rng(int(R * 1000))
+    n = 20000
+    phv, rv, phw, rw, delta = _pairs(rng, R, n)
+    G = 0.5 * math.log(2 * math.cosh(R))
+    # the sampler's FP32-assisted radius is within kDeltaR / 2 of the FP64 one
+    eps = C["kDeltaR"] * 0.54
+    rva = np.clip(rv + rng.choice([-eps, eps, 0.0], n), 0, R)
+    rwa = np.clip(rw + rng.choice([-eps, eps, 0.0], n), 0, R)
+    dec = filter_decide(filter_values(phv, rva, G), filter_values(phw, rwa, G))
+    truth = np.array([O.edge(phv[i], rv[i], phw[i], rw[i], R) for i in range(n)], dtype=np.int64)
+    decided = dec != 2
+    wrong = np.flatnonzero(decided & (dec != truth))
+    assert wrong.size == 0, [(phv[i], rv[i], phw[i], rw[i], dec[i], truth[i]) for i in wrong[:5]]
+    # and it is useful: far from the threshold most pairs are decided
+    far = np.abs(delta) > 1e-2
+    assert decided[far].mean() > 0.5
+    assert truth.min() == 0 and truth.max() == 1
+
+
+def test_emulation_flags_a_planted_error(O):
+    """With the error bound removed (err = 0) the same pairs do contradict the
+    FP64 predicate, so the sound result above is not vacuous."""
+    R = 23.5089
+    rng = np.random.default_rng(5)
+    n = 20000
+    phv, rv, phw, rw, delta = _pairs(rng, R, n)
+    G = 0.5 * math.log(2 * math.cosh(R))
+    saved = dict(C)
+    try:
+        C["kCBase"], C["kC64"], C["kAngAbs"], C["kEpsPM"], C["kEps32"] = (f32(0),) * 5
+        dec = filter_decide(filter_values(phv, rv, G), filter_values(phw, rw, G))
+    finally:
+        C.update(saved)
+    truth = np.array([O.edge(phv[i], rv[i], phw[i], rw[i], R) for i in range(n)], dtype=np.int64)
+    assert np.count_nonzero((dec != 2) & (dec != truth)) > 0
