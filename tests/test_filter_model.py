@@ -8,8 +8,11 @@ test restates that arithmetic in numpy float32, operation by operation
 radius by the largest error of the FP32-assisted sampler radius, and checks on
 adversarial pairs right at the threshold, across the 0/2pi seam, on the rim,
 near the origin and at R close to the filter's limit, that no decided pair
-contradicts the oracle's FP64 predicate.  The constants are read from the
-CUDA sources, so the test follows them.
+contradicts the oracle's FP64 predicate.  The same is done for the angular
+windows in key units: every edge partner of a band lies inside the owner's
+window, and every point inside its core is an edge, with the FP32 quotient,
+rsqrt and asin taken at their documented error in the harmful direction.  The
+constants are read from the CUDA sources, so the test follows them.
 """
 import math
 import os
@@ -157,3 +160,174 @@ def test_emulation_flags_a_planted_error(O):
         C.update(saved)
     truth = np.array([O.edge(phv[i], rv[i], phw[i], rw[i], R) for i in range(n)], dtype=np.int64)
     assert np.count_nonzero((dec != 2) & (dec != truth)) > 0
+
+
+# ---------------------------------------------------------------------------
+# Windows in angle-key units (Sec. III-B getMinMaxPhi with the filter's error
+# terms): every edge partner in band i lies within the window, and every point
+# within the core is an edge.  The FP32 transcendentals (quotient, rsqrt, asin)
+# are taken at their documented error, rounded in the direction that hurts.
+
+def _cq():
+    src = open(os.path.join(CSRC, "query.cu")).read() + open(os.path.join(CSRC, "common.cuh")).read()
+    out = {}
+    for name in ("kWinE1", "kNearMargin", "kKeyPerRadF"):
+        m = re.search(r"constexpr float %s = ([-0-9.eE+]+)f;" % name, src)
+        assert m, name
+        out[name] = f32(float(m.group(1)))
+    m = re.search(r"constexpr double kKeyScale = (0x[0-9a-fp+.-]+);", src)
+    out["kKeyScale"] = float.fromhex(m.group(1))
+    return out
+
+
+W = _cq()
+KFULL = 0x80000000
+
+
+def bump(x, ulps):
+    """x moved by |ulps| float32 ulps towards +inf (ulps > 0) or -inf."""
+    x = np.asarray(x, f32)
+    for _ in range(abs(ulps)):
+        x = np.nextafter(x, f32(np.inf) if ulps > 0 else f32(-np.inf)).astype(f32)
+    return x
+
+
+def half_angle(Q, s):
+    """asin(sqrt(Q)); s = -1 takes every approximate step at its low end, +1 high."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rs = bump((1.0 / np.sqrt(np.asarray(Q, f64))).astype(f32), 2 * s)
+        y = (Q * rs).astype(f32)
+    y2 = (y * y).astype(f32)
+    small = (y * fma(y2, fma(y2, f32(0.075), f32(0.16666667)), f32(1.0))).astype(f32)
+    big = bump(np.arcsin(np.minimum(y, f32(1.0))).astype(f32), 2 * s)
+    return np.where(Q > 0, np.where(y < f32(0.125), small, big), f32(0)).astype(f32)
+
+
+def band_constants(R, c, i, G):
+    sq = math.exp(-G)
+    ci = max(c[i] - C["kDeltaR"], 0.0)
+    co = c[i + 1] + C["kDeltaR"]
+    return dict(P=f32(math.exp(ci) * sq), Mm=f32(math.exp(-ci) * sq), S=f32(math.sinh(ci) * sq * 1.4142135623730951),
+                PMn=f32(2.0 * math.cosh(co) * sq * (1.0 + 1e-6)), Po=f32(math.exp(co) * sq),
+                Mo=f32(math.exp(-co) * sq), So=f32(math.sinh(co) * sq * 1.4142135623730951))
+
+
+def window_filter(v, B, i):
+    _, _, P, M, S, gam = v
+    S2, PM = (f32(2) * S).astype(f32), (P + M).astype(f32)
+    T = fma(P, B["Mm"], (M * B["P"]).astype(f32))
+    beta = fma((C["kC64"] * PM).astype(f32), B["PMn"], f32(1.0))
+    num = fma((f32(1.0) + T).astype(f32), W["kWinE1"], (beta - T).astype(f32))
+    den = ((S2 * B["S"]).astype(f32) * (f32(1.0) - (gam + f32(6.0) * C["kEps32"]).astype(f32))).astype(f32)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        Q = bump((num / den).astype(f32), -2)
+    full = (i == 0) | ~(B["S"] > 0) | ~(S2 > 0) | ~(Q < 1)
+    th = half_angle(np.maximum(Q, f32(0)), -1)
+    K = (W["kKeyPerRadF"] * (f32(2.0) * (f32(1.0) + f32(2e-5))).astype(f32)).astype(f32)
+    keys = fma(th, K, f32(3.0))
+    full |= keys >= f32(2147483648.0)
+    return np.where(full, KFULL, np.floor(np.where(full, 0, keys)).astype(np.int64))
+
+
+def window_core(v, B):
+    _, _, P, M, S, gam = v
+    S2, PM = (f32(2) * S).astype(f32), (P + M).astype(f32)
+    m = fma((C["kC64"] * PM).astype(f32), B["PMn"], W["kNearMargin"])
+    S2d = (S2 * (f32(1.0) + (gam + f32(6.0) * C["kEps32"]).astype(f32))).astype(f32)
+    Q = np.full(P.shape, f32(4.0))
+    none = np.zeros(P.shape, bool)
+    for Pb, Mb, Sb in ((B["Po"], B["Mo"], B["So"]), (B["P"], B["Mm"], B["S"])):
+        T = fma(P, Mb, (M * Pb).astype(f32))
+        num = (((f32(1.0) - m).astype(f32) - T).astype(f32) - ((f32(1.0) + T).astype(f32) * W["kWinE1"]).astype(f32))
+        none |= ~(num > 0)
+        den = (S2d * Sb).astype(f32)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            q = bump((num / den).astype(f32), 2)
+        Q = np.where(den > 0, np.minimum(Q, q), Q).astype(f32)
+    th = half_angle(Q, 1)
+    K = (W["kKeyPerRadF"] * (f32(2.0) * (f32(1.0) - f32(4e-5))).astype(f32)).astype(f32)
+    keys = ((th * K).astype(f32) - f32(4.0)).astype(f32)
+    core = np.where(keys < 0, -1, np.floor(np.maximum(keys, 0)).astype(np.int64))
+    core = np.where(Q >= 1, KFULL, core)
+    return np.where(none, -1, core)
+
+
+def angle_key(ph):
+    t = np.floor(ph * W["kKeyScale"])
+    return np.clip(t, 0, 4294967295).astype(np.int64)
+
+
+@pytest.mark.parametrize("n,k,alpha", [(10_000, 6, 1.0), (10**7, 200, 1.0), (10**6, 16, 0.75), (5000, 60, 1.5)])
+def test_windows_contain_every_edge_and_cores_only_edges(O, n, k, alpha):
+    R = O.target_radius(n, k, alpha)
+    B = O.default_bands(n)
+    c = O.boundaries(R, B)
+    G = 0.5 * math.log(2 * math.cosh(R))
+    rng = np.random.default_rng(n + k)
+    count = 20000
+    eps = C["kDeltaR"] * 0.54
+    checked = cores = 0
+    for _ in range(4):
+        i = rng.integers(1, B, count)  # candidate band (band 0 is always searched whole)
+        # the sampler's radius of w: in band i, a third at each edge of the band
+        u = rng.random(count)
+        u = np.where(rng.random(count) < 0.33, 0.0, np.where(rng.random(count) < 0.5, 1.0 - 1e-12, u))
+        rw_a = c[i] + (c[i + 1] - c[i]) * u
+        rw = np.clip(rw_a + rng.uniform(-eps, eps, count), 0, R)
+        bv = (rng.random(count) * (i + 1)).astype(np.int64)  # v in band i or inside it
+        rv_a = np.minimum(c[bv] + (c[bv + 1] - c[bv]) * rng.random(count), R)
+        rv = np.clip(rv_a + rng.uniform(-eps, eps, count), 0, R)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            A = (np.cosh(rv) * np.cosh(rw) - math.cosh(R)) / (np.sinh(rv) * np.sinh(rw))
+        theta = np.arccos(np.clip(np.nan_to_num(A, nan=1.0), -1.0, 1.0))
+        # a quarter of the pairs anywhere inside the threshold angle, the rest at it
+        near = theta * (1 + rng.choice([-1, 1], count) * 10.0 ** rng.uniform(-9, -0.5, count))
+        dphi = np.clip(np.where(rng.random(count) < 0.25, theta * rng.random(count), near), 0, math.pi)
+        S = 2 * math.pi * 2.0 ** -53
+        uv = rng.integers(0, 2**53, count, dtype=np.int64)
+        uw = np.mod(uv + np.rint(rng.choice([-1, 1], count) * dphi / S).astype(np.int64), 2**53)
+        phv, phw = uv.astype(f64) * S, uw.astype(f64) * S
+        kv, kw = angle_key(phv), angle_key(phw)
+        kd = np.abs(kv - kw)
+        kd = np.minimum(kd, 2**32 - kd)
+        v = filter_values(phv, rv_a, G)
+        for band in np.unique(i):
+            sel = np.flatnonzero(i == band)
+            Bc = band_constants(R, c, band, G)
+            vs = tuple(a[sel] for a in v)
+            wf = window_filter(vs, Bc, band)
+            wc = window_core(vs, Bc)
+            truth = np.array([O.edge(phv[j], rv[j], phw[j], rw[j], R) for j in sel], dtype=bool)
+            inside = (wf == KFULL) | (kd[sel] <= wf)
+            missed = sel[truth & ~inside]
+            assert missed.size == 0, [(rv[j], rw[j], kd[j], band) for j in missed[:5]]
+            plain = wf < KFULL
+            core = np.where(wc == KFULL, wf, np.minimum(wc, wf))
+            in_core = plain & (wc >= 0) & (kd[sel] <= core)
+            bad = sel[in_core & ~truth]
+            assert bad.size == 0, [(rv[j], rw[j], kd[j], band) for j in bad[:5]]
+            checked += sel.size
+            cores += int(in_core.sum())
+    assert cores > 0.05 * checked  # the core test is not vacuous
+
+
+def test_window_checks_detect_planted_errors(O, monkeypatch):
+    """A window 10^-4 too narrow, or a core 10^-4 too wide, fails the check
+    above: its pairs come close enough to the band edges and the threshold."""
+    import sys
+    mod = sys.modules[__name__]
+    wf0, wc0 = mod.window_filter, mod.window_core
+
+    def narrow(v, B, i):
+        w = wf0(v, B, i)
+        return np.where(w < KFULL, np.floor(w * (1 - 1e-4) - 8).astype(np.int64), w)
+
+    def wide(v, B):
+        w = wc0(v, B)
+        return np.where((w >= 0) & (w < KFULL), np.floor(w * (1 + 1e-4) + 8).astype(np.int64), w)
+
+    for name, fake in (("window_filter", narrow), ("window_core", wide)):
+        with monkeypatch.context() as m:
+            m.setattr(mod, name, fake)
+            with pytest.raises(AssertionError):
+                test_windows_contain_every_edge_and_cores_only_edges(O, 10**7, 200, 1.0)
