@@ -28,6 +28,13 @@
  *     of Aldecoa et al. that Sec. II describes) and the band algorithm (Alg. 1:
  *     bands, per-band angular sort, getMinMaxPhi windows, binary search,
  *     candidate test, outward-only iteration).
+ *   - Dynamic model (Sec. III-C, Algorithm 2): step values from Philox counter
+ *     (i,1,0,0), rotation modulo 2 pi, the radial step in sinh(alpha r) with
+ *     reflection at 0 and sinh(alpha R), and asinh for the way back.
+ *   - Timed CPU baseline: the band structure built once and the outward
+ *     queries of a vertex set counted, OpenMP over the vertices.
+ * Every function is pinned in tests/test_oracle_*.py against independent facts
+ * (closed forms, mpmath, brute force, invariants, distribution tests).
  */
 #include <stdint.h>
 #include <stdlib.h>
