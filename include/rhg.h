@@ -39,7 +39,7 @@
  *   library's deterministic exp/log/cos; the edge set is therefore a pure
  *   function of (n, k, alpha, seed) and does not depend on num_bands,
  *   band_ratio or the filter flags.
- * - By default (R <= 32 and alpha R <= 80) an FP32 test decides each candidate
+ * - By default (R <= 32 and alpha R <= 44) an FP32 test decides each candidate
  *   pair whenever its proven error bound, which includes the rounding of the FP64
  *   predicate, allows; the remaining pairs are decided by the FP64 predicate.
  */

@@ -32,7 +32,7 @@ constexpr float kCBase = 6e-6f;          // 2 kEpsPM + 8 eps32 + 2 eps_sin, roun
 constexpr float kAngAbs = 2e-13f;        // absolute error of |phi_v - phi_w| from the hi/lo split, x2
 constexpr float kC64 = 3.56e-15f;        // 32 u (1 + 1e-3): |L - X H| / H <= kC64 (P_v+M_v)(P_w+M_w)
 constexpr double kFilterMaxR = 32.0;     // above this the FP64 noise of Eq. 3 makes the filter useless
-constexpr double kFilterMaxAlphaR = 80.0;  // FP32 range of cosh(alpha R) in the approximate radius
+constexpr double kFilterMaxAlphaR = 44.0;  // w (w + 2) finite in FP32: w <= cosh(alpha R) - 1 < 1.84e19
 
 // Per-graph metadata, written by the plan kernel and read by all later stages.
 struct Meta {
@@ -153,7 +153,8 @@ __device__ __forceinline__ U64x4 draw(uint64_t id, uint64_t seed)
 // (relative error <= 4 * 2^-24), ln y = e ln 2 + ln m with m in [sqrt(1/2),
 // sqrt(2)) (logf: 1 ulp, <= 3e-8 here), assembled in FP64:
 // |r_approx - r| <= (2.4e-7 + 3e-8) / alpha <= 5.4e-7 < kDeltaR for alpha > 1/2.
-// Requires alpha R <= kFilterMaxAlphaR (w must be finite in FP32).
+// Requires alpha R <= kFilterMaxAlphaR: w (w + 2) must stay below FLT_MAX, i.e.
+// w < 1.84e19, i.e. alpha R < 45.05.
 __device__ __forceinline__ double radius_approx(uint64_t u53, double R, double cm1, double inv_alpha)
 {
     const double U = static_cast<double>(u53) * kU53;

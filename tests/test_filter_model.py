@@ -331,3 +331,57 @@ def test_window_checks_detect_planted_errors(O, monkeypatch):
             m.setattr(mod, name, fake)
             with pytest.raises(AssertionError):
                 test_windows_contain_every_edge_and_cores_only_edges(O, 10**7, 200, 1.0)
+
+
+# ---------------------------------------------------------------------------
+# The sampler's FP32-assisted radius (band assignment and filter values): within
+# kDeltaR of the FP64 radius for every alpha > 1/2 and alpha R up to the filter's
+# limit, with logf taken 2 ulp off in either direction.
+
+def radius_approx(u53, R, alpha, s):
+    cm1 = math.cosh(alpha * R) - 1.0
+    U = u53.astype(f64) * 2.0 ** -53
+    wf = (U * cm1).astype(f32)
+    y = ((f32(1.0) + wf).astype(f32) + np.sqrt((wf * (wf + f32(2.0)).astype(f32)).astype(f32))).astype(f32)
+    m, e = np.frexp(y)
+    low = m < f32(0.70710678)
+    m = np.where(low, (m * f32(2.0)).astype(f32), m).astype(f32)
+    e = np.where(low, e - 1, e)
+    lg = e.astype(f64) * 0.69314718055994530942 + bump(np.log(m).astype(f32), 2 * s).astype(f64)
+    r = lg * (1.0 / alpha)
+    return np.where(r < R, np.maximum(r, 0.0), R)
+
+
+@pytest.mark.parametrize("alpha,R", [(0.51, 30.0), (0.55, 25.0), (0.75, 25.564), (1.0, 23.5089), (1.5, 16.0),
+                                     (3.0, 14.66), (1.375, 32.0), (1.0, 31.9)])
+def test_sampler_radius_within_kDeltaR(alpha, R):
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 200
+    rng = np.random.default_rng(int(alpha * 100 + R))
+    u53 = np.concatenate([rng.integers(0, 2**53, 3000, dtype=np.int64),
+                          (2.0 ** rng.uniform(0, 53, 1000)).astype(np.int64),
+                          np.array([0, 1, 2, 3, 2**20, 2**40, 2**52, 2**53 - 2, 2**53 - 1], dtype=np.int64)])
+    cm1 = mpmath.cosh(mpmath.mpf(alpha) * R) - 1
+    exact = np.array([float(mpmath.acosh(1 + mpmath.mpf(int(u)) / 2**53 * cm1) / alpha) for u in u53])
+    exact = np.minimum(exact, R)
+    for s in (-1, 0, 1):
+        err = np.abs(radius_approx(u53, R, alpha, s) - exact)
+        assert err.max() <= 5.4e-7, (s, err.max(), u53[err.argmax()])
+    assert 5.4e-7 < C["kDeltaR"]
+
+
+def test_filter_range_keeps_the_sampler_radius_finite():
+    """The filter is used only for alpha R <= kFilterMaxAlphaR; there the FP32
+    w (w + 2) of the approximate radius must not overflow (it would put every
+    point at R), and just above the limit it would."""
+    src = open(os.path.join(CSRC, "common.cuh")).read()
+    lim = float(re.search(r"constexpr double kFilterMaxAlphaR = ([0-9.]+);", src).group(1))
+    for aR, finite in ((lim, True), (45.2, False)):
+        wf = f32(math.cosh(aR) - 1.0)
+        with np.errstate(over="ignore"):
+            prod = (wf * (wf + f32(2.0)).astype(f32)).astype(f32)
+        assert np.isfinite(prod) == finite, aR
+    # at the limit the approximate radius of the largest variate is still right
+    alpha, R = 1.375, lim / 1.375
+    r = radius_approx(np.array([2**53 - 1], dtype=np.int64), R, alpha, 0)
+    assert abs(r[0] - R) < 5.4e-7

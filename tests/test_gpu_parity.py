@@ -106,3 +106,16 @@ def test_no_solution_and_invalid():
     with pytest.raises(rhg.RhgError) as e:
         rhg.generate_pairs(1, 6, 1.0, 1)
     assert e.value.status == rhg.INVALID_ARG
+
+
+@pytest.mark.parametrize("n,k,alpha,seed,mode", [(5000, 3, 3.0, 21, 1), (5000, 2, 3.0, 22, 0), (4000, 3, 4.0, 23, 0),
+                                                  (3000, 2, 5.0, 24, 0)])
+def test_steep_density_near_the_filter_range(O, n, k, alpha, seed, mode):
+    """alpha R just below 44 runs the FP32 filter; above it (where the FP32-assisted
+    sampler radius would overflow) the graph runs in FP64 mode; both equal all pairs."""
+    rhg = require_gpu()
+    pairs, res = rhg.generate_pairs(n, k, alpha, seed)
+    R = O.target_radius(n, k, alpha)
+    assert res.mode == mode, (alpha * R, res.mode)
+    phi, r = O.sample_points(n, alpha, R, seed)
+    assert np.array_equal(sorted_pairs(pairs), O.brute_edges(phi, r, R))
