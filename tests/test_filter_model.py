@@ -385,3 +385,68 @@ def test_filter_range_keeps_the_sampler_radius_finite():
     alpha, R = 1.375, lim / 1.375
     r = radius_approx(np.array([2**53 - 1], dtype=np.int64), R, alpha, 0)
     assert abs(r[0] - R) < 5.4e-7
+
+
+def window_fp64(rv, c, i, R):
+    """The FP64-mode half-width in key units (kFull: the whole band)."""
+    chv, shv = np.cosh(rv), np.sinh(rv)
+    u = 2.0 ** -53
+    b = (math.cosh(R) + 64.0 * u * chv * math.cosh(c[i + 1])) * (1.0 + 1e-12)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        Q = (b - np.cosh(rv - c[i])) / (2.0 * shv * math.sinh(c[i]))
+    full = (c[i] <= 0) | (rv <= 0) | (shv <= 0) | ~(Q < 1.0)
+    with np.errstate(invalid="ignore"):
+        th = 2.0 * np.arcsin(np.sqrt(np.where(Q > 0, Q, 0.0))) * (1.0 + 1e-9) + 1e-12
+    keys = th * 683565275.57643158 + 3.0
+    full |= keys >= 2147483648.0
+    return np.where(full, KFULL, np.floor(np.where(full, 0, keys)).astype(np.int64))
+
+
+@pytest.mark.parametrize("n,k,alpha", [(5000, 2, 3.0), (3000, 2, 5.0), (10**6, 1, 0.6), (10**4, 6, 1.0)])
+def test_fp64_windows_contain_every_edge(O, n, k, alpha):
+    """FP64 mode (bands from the FP64 radius): every edge partner in band i lies
+    within the owner's window, at both edges of the band and at the threshold."""
+    R = O.target_radius(n, k, alpha)
+    B = O.default_bands(n)
+    c = O.boundaries(R, B)
+    rng = np.random.default_rng(n + 7)
+    count = 40000
+    i = rng.integers(1, B, count)
+    u = rng.random(count)
+    u = np.where(rng.random(count) < 0.33, 0.0, np.where(rng.random(count) < 0.5, 1.0 - 1e-12, u))
+    rw = c[i] + (c[i + 1] - c[i]) * u
+    bv = (rng.random(count) * (i + 1)).astype(np.int64)
+    rv = np.minimum(c[bv] + (c[bv + 1] - c[bv]) * rng.random(count), R)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        A = (np.cosh(rv) * np.cosh(rw) - math.cosh(R)) / (np.sinh(rv) * np.sinh(rw))
+    theta = np.arccos(np.clip(np.nan_to_num(A, nan=1.0), -1.0, 1.0))
+    dphi = np.clip(theta * (1 - 10.0 ** rng.uniform(-12, -1, count)), 0, math.pi)
+    S = 2 * math.pi * 2.0 ** -53
+    uv = rng.integers(0, 2**53, count, dtype=np.int64)
+    uw = np.mod(uv + np.rint(rng.choice([-1, 1], count) * dphi / S).astype(np.int64), 2**53)
+    phv, phw = uv.astype(f64) * S, uw.astype(f64) * S
+    kd = np.abs(angle_key(phv) - angle_key(phw))
+    kd = np.minimum(kd, 2**32 - kd)
+    truth = np.array([O.edge(phv[j], rv[j], phw[j], rw[j], R) for j in range(count)], dtype=bool)
+    wf = np.empty(count, np.int64)
+    for band in np.unique(i):
+        sel = i == band
+        wf[sel] = window_fp64(rv[sel], c, band, R)
+    missed = np.flatnonzero(truth & ~((wf == KFULL) | (kd <= wf)))
+    assert missed.size == 0, [(rv[j], rw[j], kd[j], wf[j]) for j in missed[:5]]
+    assert truth.mean() > 0.5  # most pairs sit just inside the threshold
+
+
+def test_fp64_window_check_detects_a_planted_error(O, monkeypatch):
+    """The same check fails for a window only 4 keys narrower."""
+    import sys
+    mod = sys.modules[__name__]
+    w0 = mod.window_fp64
+
+    def narrow(rv, c, i, R):
+        w = w0(rv, c, i, R)
+        return np.where(w < KFULL, w - 4, w)
+
+    monkeypatch.setattr(mod, "window_fp64", narrow)
+    with pytest.raises(AssertionError):
+        test_fp64_windows_contain_every_edge(O, 10**4, 6, 1.0)
