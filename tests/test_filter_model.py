@@ -353,7 +353,7 @@ def radius_approx(u53, R, alpha, s):
 
 
 @pytest.mark.parametrize("alpha,R", [(0.51, 30.0), (0.55, 25.0), (0.75, 25.564), (1.0, 23.5089), (1.5, 16.0),
-                                     (3.0, 14.66), (1.375, 32.0), (1.0, 31.9)])
+                                     (3.0, 14.66), (1.375, 32.0), (1.0, 31.9), (0.51, 3.0), (1.0, 2.0)])
 def test_sampler_radius_within_kDeltaR(alpha, R):
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.prec = 200
