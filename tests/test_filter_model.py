@@ -287,9 +287,14 @@ def test_windows_contain_every_edge_and_cores_only_edges(O, n, k, alpha):
         uv = rng.integers(0, 2**53, count, dtype=np.int64)
         uw = np.mod(uv + np.rint(rng.choice([-1, 1], count) * dphi / S).astype(np.int64), 2**53)
         phv, phw = uv.astype(f64) * S, uw.astype(f64) * S
-        kv, kw = angle_key(phv), angle_key(phw)
-        kd = np.abs(kv - kw)
-        kd = np.minimum(kd, 2**32 - kd)
+        # keys of loaded points (floor of phi 2^32 / 2pi) and of generated points
+        # (the top 32 bits of the 53-bit angle draw): the window must hold the
+        # larger distance, the core must exclude non-edges at the smaller one
+        dists = []
+        for kv, kw in ((angle_key(phv), angle_key(phw)), (uv >> 21, uw >> 21)):
+            d = np.abs(kv - kw)
+            dists.append(np.minimum(d, 2**32 - d))
+        kd, kd_core = np.maximum(*dists), np.minimum(*dists)
         v = filter_values(phv, rv_a, G)
         for band in np.unique(i):
             sel = np.flatnonzero(i == band)
@@ -303,7 +308,7 @@ def test_windows_contain_every_edge_and_cores_only_edges(O, n, k, alpha):
             assert missed.size == 0, [(rv[j], rw[j], kd[j], band) for j in missed[:5]]
             plain = wf < KFULL
             core = np.where(wc == KFULL, wf, np.minimum(wc, wf))
-            in_core = plain & (wc >= 0) & (kd[sel] <= core)
+            in_core = plain & (wc >= 0) & (kd_core[sel] <= core)
             bad = sel[in_core & ~truth]
             assert bad.size == 0, [(rv[j], rw[j], kd[j], band) for j in bad[:5]]
             checked += sel.size
@@ -425,8 +430,10 @@ def test_fp64_windows_contain_every_edge(O, n, k, alpha):
     uv = rng.integers(0, 2**53, count, dtype=np.int64)
     uw = np.mod(uv + np.rint(rng.choice([-1, 1], count) * dphi / S).astype(np.int64), 2**53)
     phv, phw = uv.astype(f64) * S, uw.astype(f64) * S
-    kd = np.abs(angle_key(phv) - angle_key(phw))
-    kd = np.minimum(kd, 2**32 - kd)
+    kd = np.zeros(count, np.int64)
+    for kv, kw in ((angle_key(phv), angle_key(phw)), (uv >> 21, uw >> 21)):
+        d = np.abs(kv - kw)
+        kd = np.maximum(kd, np.minimum(d, 2**32 - d))
     truth = np.array([O.edge(phv[j], rv[j], phw[j], rw[j], R) for j in range(count)], dtype=bool)
     wf = np.empty(count, np.int64)
     for band in np.unique(i):
