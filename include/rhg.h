@@ -57,9 +57,10 @@ typedef enum rhg_status {
     RHG_OK = 0,
     RHG_ERR_INVALID_ARG = 1,  /* a parameter or buffer is outside its domain          */
     RHG_ERR_NO_SOLUTION = 2,  /* no R gives average degree k (Eq. 22 peaks below k)   */
-    RHG_ERR_OOM = 3,          /* the workspace passed is smaller than required, or the
-                                 graph is too dense for the workspace's work lists
-                                 (average degree in the thousands)                    */
+    RHG_ERR_OOM = 3,          /* the workspace passed is smaller than required, or a
+                                 work list of the workspace overflowed (a graph far
+                                 denser than its sizing assumed, e.g. num_bands = 1
+                                 on a large n)                                        */
     RHG_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed          */
     RHG_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up                   */
     RHG_ERR_OVERFLOW = 6      /* the output buffer holds fewer entries than required;
@@ -301,6 +302,7 @@ typedef struct {
     uint64_t index_entries;    /* bucket-index entries of all graphs            */
     uint64_t pair_capacity;    /* pair_offsets[count]                           */
     uint64_t workspace_bytes;  /* = rhg_batch_workspace_bytes of the graphs     */
+    uint64_t chunk_extra;      /* chunk-list entries for graphs in FP64 mode    */
 } rhg_batch_plan;
 
 int rhg_batch_prepare(const rhg_params *graphs, uint32_t count, const uint64_t *pair_offsets,

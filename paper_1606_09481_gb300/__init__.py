@@ -57,7 +57,8 @@ class BatchGraph(ctypes.Structure):
 class BatchPlan(ctypes.Structure):
     """rhg_batch_plan: the counts rhg_batch_prepare records for rhg_batch_launch."""
     _fields_ = [("count", _c_u32), ("verify", _c_u32), ("num_tiles", _c_u64), ("points", _c_u64),
-                ("index_entries", _c_u64), ("pair_capacity", _c_u64), ("workspace_bytes", _c_u64)]
+                ("index_entries", _c_u64), ("pair_capacity", _c_u64), ("workspace_bytes", _c_u64),
+                ("chunk_extra", _c_u64)]
 
 
 class RhgError(RuntimeError):

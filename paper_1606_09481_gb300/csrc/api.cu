@@ -57,7 +57,31 @@ struct Layout {
     uint32_t heavy_cap, recheck_cap;
 };
 
-Layout make_layout(uint64_t n, uint64_t csr_entries)
+constexpr uint64_t kMaxListEntries = 0x7fffffffull;
+
+// Chunk-list entries beyond n/4 + 65536 for a graph that may run in FP64 mode
+// (RHG_FLAG_FP64_ONLY, or R > 32 or alpha R > 44, which decide the mode on the
+// device): without a core every window is tested, and each tested piece longer
+// than 32 candidates becomes at least one chunk, so the list is sized by the
+// candidates, about 1.1-2 times the n k / 2 edges: n k / 20 entries.  For an
+// R_override the degree comes from Eq. 22 at that R.
+uint64_t fp64_chunk_extra(const rhg_params &p)
+{
+    bool fp64 = (p.flags & RHG_FLAG_FP64_ONLY) != 0 || p.alpha * kFilterMaxR > kFilterMaxAlphaR;
+    double k = p.k;
+    if (p.R_override > 0.0) {
+        fp64 = fp64 || p.R_override > kFilterMaxR || p.alpha * p.R_override > kFilterMaxAlphaR;
+        const double R = p.R_override, a = p.alpha, xi = a / (a - 0.5), pi = 3.14159265358979323846;
+        const double inner = pi / (4.0 * a * a) - (pi - 1.0) / a + (pi - 2.0);
+        k = 2.0 / pi * xi * xi * static_cast<double>(p.n) *
+            (std::exp(-R / 2.0) + std::exp(-a * R) * (a * R / 2.0 * inner - 1.0));
+    }
+    if (!fp64 || !(k > 0.0)) return 0;
+    const double extra = std::ceil(static_cast<double>(p.n) * k / 20.0);
+    return extra < static_cast<double>(kMaxListEntries) ? static_cast<uint64_t>(extra) : kMaxListEntries;
+}
+
+Layout make_layout(uint64_t n, uint64_t csr_entries, uint64_t chunk_extra = 0)
 {
     Layout L{};
     size_t o = 0;
@@ -66,7 +90,8 @@ Layout make_layout(uint64_t n, uint64_t csr_entries)
         o = align_up(o + bytes);
         return at;
     };
-    L.heavy_cap = static_cast<uint32_t>(n / 4 + 65536);
+    const uint64_t chunks = n / 4 + 65536 + chunk_extra;
+    L.heavy_cap = static_cast<uint32_t>(chunks < kMaxListEntries ? chunks : kMaxListEntries);
     L.recheck_cap = static_cast<uint32_t>(n / 2 + 65536);
     L.meta = take(sizeof(Meta));
     L.keys0 = take(n * 8);
@@ -299,7 +324,7 @@ int generate(const rhg_params *p, void *d_ws, size_t ws_bytes, Output kind, uint
     if (kind == Output::Pairs && capacity && (!d_pairs || (reinterpret_cast<uintptr_t>(d_pairs) & 7)))
         return RHG_ERR_INVALID_ARG;
     if (kind == Output::Csr && (!d_row_ptr || (capacity && !d_col))) return RHG_ERR_INVALID_ARG;
-    const Layout L = make_layout(p->n, kind == Output::Csr ? capacity : 0);
+    const Layout L = make_layout(p->n, kind == Output::Csr ? capacity : 0, fp64_chunk_extra(*p));
     if (ws_bytes < L.total) return RHG_ERR_OOM;
     if (reinterpret_cast<uintptr_t>(d_ws) & 255) return RHG_ERR_INVALID_ARG;
     Pipeline pl{d_ws, L, p->n};
@@ -346,6 +371,7 @@ struct BatchHost {
     uint32_t G = 0;
     uint64_t N = 0;          // points of all graphs
     uint64_t idx_total = 0;  // bucket-index entries of all graphs
+    uint64_t chunk_extra = 0;  // chunk-list entries for graphs that may run in FP64 mode
     std::vector<PlanArgs> args;
     std::vector<uint4> tiles;
     std::vector<uint32_t> tile_first, pt_off, idx_base;
@@ -384,6 +410,7 @@ int batch_host(const rhg_params *graphs, uint32_t count, const uint64_t *pair_of
         }
         pos += q.n;
         idx += index_entries(q.n);
+        h.chunk_extra += fp64_chunk_extra(q);
         if (pos >= 0xFFFFFFFFull || idx >= 0xFFFFFFFFull) return RHG_ERR_INVALID_ARG;  // 32-bit positions
         h.pt_off[g + 1] = static_cast<uint32_t>(pos);
         h.idx_base[g + 1] = static_cast<uint32_t>(idx);
@@ -401,7 +428,7 @@ int batch_host(const rhg_params *graphs, uint32_t count, const uint64_t *pair_of
 }
 
 // Byte offsets of a batch's buffers from its graph, point, tile and index counts.
-BatchLayout batch_layout(uint64_t G, uint64_t N, uint64_t num_tiles, uint64_t idx_total)
+BatchLayout batch_layout(uint64_t G, uint64_t N, uint64_t num_tiles, uint64_t idx_total, uint64_t chunk_extra)
 {
     BatchLayout L{};
     size_t o = 0;
@@ -410,7 +437,8 @@ BatchLayout batch_layout(uint64_t G, uint64_t N, uint64_t num_tiles, uint64_t id
         o = align_up(o + bytes);
         return at;
     };
-    L.heavy_cap = static_cast<uint32_t>(N / 4 + 65536);
+    const uint64_t chunks = N / 4 + 65536 + chunk_extra;
+    L.heavy_cap = static_cast<uint32_t>(chunks < kMaxListEntries ? chunks : kMaxListEntries);
     L.recheck_cap = static_cast<uint32_t>(N / 2 + 65536);
     L.metas = take((G + 1) * sizeof(Meta));
     // the tables are one contiguous upload
@@ -452,7 +480,10 @@ BatchLayout batch_layout(uint64_t G, uint64_t N, uint64_t num_tiles, uint64_t id
     return L;
 }
 
-BatchLayout batch_layout(const BatchHost &h) { return batch_layout(h.G, h.N, h.tiles.size(), h.idx_total); }
+BatchLayout batch_layout(const BatchHost &h)
+{
+    return batch_layout(h.G, h.N, h.tiles.size(), h.idx_total, h.chunk_extra);
+}
 
 // Copies the tables into the workspace (pageable source: returns when copied).
 Status upload_tables(void *ws, const BatchLayout &L, const BatchHost &h, cudaStream_t stream)
@@ -652,9 +683,10 @@ int static_scratch(void **ptr, cudaError_t *err)
 bool plan_layout(const rhg_batch_plan *plan, BatchLayout &L)
 {
     if (!plan || plan->count == 0 || plan->count > kMaxBatch || plan->num_tiles < plan->count ||
-        plan->points >= 0xFFFFFFFFull || plan->index_entries >= 0xFFFFFFFFull || plan->verify > 1)
+        plan->points >= 0xFFFFFFFFull || plan->index_entries >= 0xFFFFFFFFull || plan->verify > 1 ||
+        plan->chunk_extra > kMaxListEntries)
         return false;
-    L = batch_layout(plan->count, plan->points, plan->num_tiles, plan->index_entries);
+    L = batch_layout(plan->count, plan->points, plan->num_tiles, plan->index_entries, plan->chunk_extra);
     return L.total == plan->workspace_bytes;
 }
 }  // namespace
@@ -696,7 +728,7 @@ int rhg_workspace_bytes(const rhg_params *p, uint64_t capacity_entries, size_t *
     const int rc = check_params(p, &B, &ratio);
     if (rc) return rc;
     if (!bytes) return RHG_ERR_INVALID_ARG;
-    *bytes = make_layout(p->n, capacity_entries).total;
+    *bytes = make_layout(p->n, capacity_entries, fp64_chunk_extra(*p)).total;
     return RHG_OK;
 }
 
@@ -844,7 +876,7 @@ int rhg_generate_pairs_static(const rhg_params *p, uint32_t *d_pairs, uint64_t c
 {
     if (result) std::memset(result, 0, sizeof(*result));
     if (!p || p->n > RHG_STATIC_MAX_POINTS) return RHG_ERR_INVALID_ARG;
-    const size_t need = make_layout(p->n, 0).total;
+    const size_t need = make_layout(p->n, 0, fp64_chunk_extra(*p)).total;
     if (need > RHG_STATIC_SCRATCH_BYTES) return RHG_ERR_INVALID_ARG;
     void *ws = nullptr;
     cudaError_t err = cudaSuccess;
@@ -924,6 +956,7 @@ int rhg_batch_prepare(const rhg_params *graphs, uint32_t count, const uint64_t *
     plan->index_entries = h.idx_total;
     plan->pair_capacity = h.out_off[count];
     plan->workspace_bytes = L.total;
+    plan->chunk_extra = h.chunk_extra;
     return RHG_OK;
 }
 

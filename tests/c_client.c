@@ -53,7 +53,7 @@ int main(void)
     memset(&plan, 0, sizeof(plan));
     CHECK(rhg_batch_launch(&plan, NULL, NULL, NULL) == RHG_ERR_INVALID_ARG);
     CHECK(rhg_batch_read_results(&plan, NULL, NULL, res, &totals) == RHG_ERR_INVALID_ARG);
-    CHECK(sizeof(rhg_params) == 56 && sizeof(rhg_result) == 64 && sizeof(rhg_batch_plan) == 48);
+    CHECK(sizeof(rhg_params) == 56 && sizeof(rhg_result) == 64 && sizeof(rhg_batch_plan) == 56);
 
     if (fails) fprintf(stderr, "%d checks failed\n", fails);
     else printf("c client ok\n");

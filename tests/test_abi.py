@@ -95,7 +95,7 @@ def test_product_package_does_not_touch_oracle():
 def test_batch_plan_layout_and_validation(rhg):
     """rhg_batch_plan matches the header; plans that rhg_batch_prepare did not
     make, and missing buffers, are refused on the host."""
-    assert ctypes.sizeof(rhg.BatchPlan) == 48
+    assert ctypes.sizeof(rhg.BatchPlan) == 56
     L = rhg.load()
     params = rhg.batch_params([(1000, 8, 1.0, 1), (3000, 10, 0.8, 2)])
     offs = (ctypes.c_uint64 * 3)(0, 10_000, 30_000)

@@ -119,3 +119,23 @@ def test_steep_density_near_the_filter_range(O, n, k, alpha, seed, mode):
     assert res.mode == mode, (alpha * R, res.mode)
     phi, r = O.sample_points(n, alpha, R, seed)
     assert np.array_equal(sorted_pairs(pairs), O.brute_edges(phi, r, R))
+
+
+def test_dense_graphs_in_fp64_mode(O):
+    """Dense graphs in FP64 mode (no core, every window tested, one chunk per long
+    piece): the chunk list, sized for FP64 mode from n k, holds them.  The
+    FP64-only flag gives the default mode's graph, and a dense graph with
+    alpha R > 44 equals the oracle's Algorithm 1."""
+    rhg = require_gpu()
+    n, k, alpha, seed = 20000, 1500, 0.7, 41
+    a, ra = rhg.generate_pairs(n, k, alpha, seed)
+    b, rb = rhg.generate_pairs(n, k, alpha, seed, flags=rhg.FLAG_FP64_ONLY)
+    assert ra.mode == 1 and rb.mode == 0
+    assert rb.heavy_chunks > n // 4 + 65536  # more than the list holds without the FP64 sizing
+    assert np.array_equal(sorted_pairs(a), sorted_pairs(b))
+    n, k, alpha, seed = 100_000, 200, 4.0, 31
+    pairs, res = rhg.generate_pairs(n, k, alpha, seed)
+    R = O.target_radius(n, k, alpha)
+    assert res.mode == 0 and alpha * R > 44
+    phi, r = O.sample_points(n, alpha, R, seed)
+    assert np.array_equal(sorted_pairs(pairs), O.band_edges(phi, r, R, O.default_bands(n)))
