@@ -187,7 +187,9 @@ int rhg_generate_pairs_host(const rhg_params *p, void *d_workspace, size_t works
  * the device-wide synchronisation a cudaFree implies.
  *
  * The scratch is one fixed array of RHG_STATIC_SCRATCH_BYTES in the library's
- * device image, so p->n is limited to RHG_STATIC_MAX_POINTS; a larger n returns
+ * device image, so p->n is limited to RHG_STATIC_MAX_POINTS; a larger n, or a
+ * graph whose workspace (rhg_workspace_bytes) exceeds the scratch (a dense graph
+ * that may run in FP64 mode, whose chunk list grows with n k), returns
  * RHG_ERR_INVALID_ARG before anything is launched.  The array's address is
  * looked up on the first call on each device (with that device current), so
  * that first call should come before any stream capture begins.  Nothing in the
