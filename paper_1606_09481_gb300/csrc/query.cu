@@ -39,7 +39,7 @@ constexpr uint32_t kFull = 0x80000000u;  // window half-width meaning "whole ban
 constexpr int kBatchMinBlocks = 4;         // resident CTAs per SM the batch kernel is compiled for
 constexpr int kCoreGroup = 4;              // core-writer windows whose loads are issued together
 
-constexpr float kPiF = 3.14159265f;             // below pi: the unwrapped branch is safe to pi
+constexpr float kPiF = 3.14159265f;             // 3.14159274f, just above pi; sin^2(d/2) is even about pi
 constexpr float kTwoPiHiF = 6.28318548202514648f;
 constexpr float kTwoPiLoF = -1.74845553e-07f;    // 2 pi - kTwoPiHiF
 constexpr float kKeyPerRadF = 683565248.0f;      // 2^32 / (2 pi) in FP32 (slightly low)
