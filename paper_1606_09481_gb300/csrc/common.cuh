@@ -3,6 +3,7 @@
 // error-checking helpers.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
@@ -238,12 +239,14 @@ void note_launch();
 
 inline int num_sms()
 {
-    static int sms = 0;
+    static std::atomic<int> cached{0};  // host threads may race to fill it; all write the same value
+    int sms = cached.load(std::memory_order_relaxed);
     if (!sms) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
+        cached.store(sms, std::memory_order_relaxed);
     }
     return sms;
 }

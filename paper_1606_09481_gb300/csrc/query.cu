@@ -1341,9 +1341,12 @@ Status run(const QueryArgs &a, cudaStream_t stream)
     Status st;
     const uint64_t nbatch = kMulti ? static_cast<uint64_t>(a.bt.num_tiles) * (kTilePoints / 32) : (a.P.n + 31) / 32;
     const uint64_t need = ceil_div(nbatch ? nbatch : 1, kWarps);
-    static int grid_b = 0, grid_h = 0;
-    if (!grid_b) grid_b = resident_ctas(batch_kernel<kFilter, kCsr, kMulti, false>);
-    if (!grid_h) grid_h = resident_ctas(heavy_kernel<kFilter, kCsr, kMulti, false>);
+    static std::atomic<int> grid_b_cache{0}, grid_h_cache{0};  // filled once; racing threads agree
+    int grid_b = grid_b_cache.load(std::memory_order_relaxed), grid_h = grid_h_cache.load(std::memory_order_relaxed);
+    if (!grid_b) grid_b_cache.store(grid_b = resident_ctas(batch_kernel<kFilter, kCsr, kMulti, false>),
+                                    std::memory_order_relaxed);
+    if (!grid_h) grid_h_cache.store(grid_h = resident_ctas(heavy_kernel<kFilter, kCsr, kMulti, false>),
+                                    std::memory_order_relaxed);
     const unsigned gb = static_cast<unsigned>(need < static_cast<uint64_t>(grid_b) ? need : grid_b);
     if (a.verify) batch_kernel<kFilter, kCsr, kMulti, true><<<gb, kThreads, 0, stream>>>(a);
     else batch_kernel<kFilter, kCsr, kMulti, false><<<gb, kThreads, 0, stream>>>(a);
