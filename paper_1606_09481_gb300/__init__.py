@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
+import threading
 from dataclasses import dataclass
 
 from .build import LIB, build
@@ -71,8 +72,18 @@ class RhgError(RuntimeError):
 _lib = None
 
 
+_load_lock = threading.Lock()
+
+
 def load() -> ctypes.CDLL:
-    """Load librhg.so (built by build()); raises if it is missing."""
+    """Load librhg.so (built by build()); raises if it is missing.  Thread-safe."""
+    if _lib is not None:
+        return _lib
+    with _load_lock:
+        return _load_locked()
+
+
+def _load_locked() -> ctypes.CDLL:
     global _lib
     if _lib is not None:
         return _lib
