@@ -113,3 +113,20 @@ def test_batch_plan_layout_and_validation(rhg):
     assert L.rhg_batch_launch(ctypes.byref(zero), 256, 256, None) == rhg.INVALID_ARG
     res = (rhg.BatchGraph * 2)()
     assert L.rhg_batch_read_results(ctypes.byref(fake), 256, None, res, None) == rhg.INVALID_ARG
+
+
+def test_library_loads_once_across_threads(rhg):
+    """Serving threads that call into the binding at once share one library handle."""
+    import threading
+    saved = rhg._lib
+    rhg._lib = None
+    try:
+        got = []
+        threads = [threading.Thread(target=lambda: got.append(rhg.load())) for _ in range(8)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        assert len(got) == 8 and len({id(x) for x in got}) == 1
+    finally:
+        rhg._lib = saved if saved is not None else rhg._lib
