@@ -123,7 +123,7 @@ def _pairs(rng, R, count):
     return phv, rv, phw, rw, delta
 
 
-@pytest.mark.parametrize("R", [3.0046, 16.705, 23.5089, 25.564, 31.9])
+@pytest.mark.parametrize("R", [0.7, 2.0, 3.0046, 16.705, 23.5089, 25.564, 31.9])
 def test_filter_decisions_are_sound(O, R):
     rng = np.random.default_rng(int(R * 1000))
     n = 20000
