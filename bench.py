@@ -287,10 +287,12 @@ def bench_batched(args, rhg, torch, stream):
                     "edges_equal_default": grc == rhg.OK and int(gtot.m) == m}
     del graph
     del buf
-    # the plain path, one call per graph, reusing one workspace sized for the largest graph
-    big = max(specs, key=lambda sp: sp[0])
+    # the plain path, one call per graph, reusing one workspace sized for the most
+    # demanding graph (the largest n, or a graph that may run in FP64 mode)
     cap = max(int(r.m) for r in res) + 4096
-    wsp = rhg.allocate_pairs(rhg.make_params(*big), cap)
+    ws_bytes = max(rhg.workspace_bytes(rhg.make_params(*sp)) for sp in specs)
+    wsp = rhg.Workspace(torch.empty(ws_bytes, dtype=torch.uint8, device="cuda"),
+                        torch.empty(2 * cap, dtype=torch.int32, device="cuda"), cap)
     for sp in specs[:64]:
         rhg.generate_pairs(*sp, workspace=wsp)
     torch.cuda.synchronize()
