@@ -87,20 +87,35 @@ def lib() -> ctypes.CDLL:
             L.ro_constants.argtypes = [_p]
             L.ro_prepare.argtypes = [_u64, _p, _p, _dbl, _u32, _dbl]
             L.ro_prepare.restype = _p
-            L.ro_prepared_count.argtypes = [_p, _p, _u64, _p]
+            L.ro_prepared_count.argtypes = [_p, _p, _u64, _p, _p]
             L.ro_prepared_count.restype = _i64
+            L.ro_prepared_upper_pairs.argtypes = [_p, _u64, _u64, _p, _u64]
+            L.ro_prepared_upper_pairs.restype = _i64
+            L.ro_prepared_window_misses.argtypes = [_p, _p, _u64, _dbl, _p]
             L.ro_prepared_free.argtypes = [_p]
             L.ro_set_threads.argtypes = [ctypes.c_int32]
             L.ro_asinh.restype = _dbl
             L.ro_asinh.argtypes = [_dbl]
             L.ro_draw_movement.argtypes = [_u64, _u64, _dbl, _dbl, _dbl, _dbl, _p, _p]
-            L.ro_move.argtypes = [_u64, _p, _p, _p, _p, _p, _dbl, _dbl]
+            L.ro_move.argtypes = [_u64, _p, _p, _p, _p, _p, _dbl, _dbl, ctypes.c_int32]
             _lib = L
     return _lib
 
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_p)
+
+
+NUM_STATS = 6
+STAT_NAMES = ("candidates", "near_threshold", "windows", "rounding_band", "disagree_fp64_wellcond",
+              "disagree_longdouble_wellcond")
+
+
+def _stats_dict(stats) -> dict:
+    """Counters of the examined pairs: near_threshold = |L - cosh R| <= 1e-12 cosh R;
+    rounding_band = |L - cosh R| <= 8 u cosh r_v cosh r_w; disagree_* = pairs the
+    cancellation-free form of Eq. 3 decides otherwise (FP64, long double)."""
+    return {k: int(v) for k, v in zip(STAT_NAMES, stats)}
 
 
 # --------------------------------------------------------------------------- Philox
@@ -191,15 +206,22 @@ def draw_movement(n: int, seed: int, phi_range=(-1.0, 1.0), r_range=(-10.0, 1.0)
     return tphi, tr
 
 
-def move(ids, phi, r, tau_phi, tau_r, R: float, alpha: float):
-    """One movement step (rotation + Algorithm 2 radial movement with reflection)
-    of the nodes `ids`; returns new (phi, r, tau_r) arrays, the inputs unchanged."""
+COORD_UNIFORM = 0  # radial step in cosh(alpha r) - 1, uniform under Eq. 1 (Theorem 1 holds)
+COORD_SINH = 1     # radial step in sinh(alpha r), as Algorithm 2 prints it
+
+
+def move(ids, phi, r, tau_phi, tau_r, R: float, alpha: float, coord: int = COORD_UNIFORM):
+    """One movement step (rotation + the radial movement of Algorithm 2 with
+    reflection) of the nodes `ids`; returns new (phi, r, tau_r) arrays, the inputs
+    unchanged.  `coord` selects the coordinate of the radial step (see the header
+    of rhg_oracle.c)."""
     ids = np.ascontiguousarray(ids, dtype=np.uint32)
     phi = np.array(phi, dtype=np.float64)
     r = np.array(r, dtype=np.float64)
     tau_r = np.array(tau_r, dtype=np.float64)
     tau_phi = np.ascontiguousarray(tau_phi, dtype=np.float64)
-    lib().ro_move(len(ids), _ptr(ids), _ptr(phi), _ptr(r), _ptr(tau_phi), _ptr(tau_r), float(R), float(alpha))
+    lib().ro_move(len(ids), _ptr(ids), _ptr(phi), _ptr(r), _ptr(tau_phi), _ptr(tau_r), float(R), float(alpha),
+                  int(coord))
     return phi, r, tau_r
 
 
@@ -254,7 +276,7 @@ def band_edges(phi, r, R: float, B: int, p: float = 0.9, with_stats: bool = Fals
     """Alg. 1 range query; returns pairs (u < v) sorted lexicographically."""
     phi, r = _pts(phi, r)
     n = len(phi)
-    stats = np.zeros(3, dtype=np.int64)
+    stats = np.zeros(NUM_STATS, dtype=np.int64)
     cap = max(1024, 8 * n)
     while True:
         out = np.zeros((cap, 2), dtype=np.uint32)
@@ -267,18 +289,21 @@ def band_edges(phi, r, R: float, B: int, p: float = 0.9, with_stats: bool = Fals
     pairs = out[:m]
     pairs = pairs[np.lexsort((pairs[:, 1], pairs[:, 0]))]
     if with_stats:
-        return pairs, {"candidates": int(stats[0]), "near_threshold": int(stats[1]),
-                       "windows": int(stats[2])}
+        return pairs, _stats_dict(stats)
     return pairs
 
 
-def band_count_subset(phi, r, R: float, B: int, p: float, ids: np.ndarray):
-    """Edges found from the given vertices' outward queries, and threads used."""
+def band_count_subset(phi, r, R: float, B: int, p: float, ids: np.ndarray, with_stats: bool = False):
+    """Edges found from the given vertices' outward queries, and threads used
+    (and the diagnostics of the examined pairs with with_stats)."""
     phi, r = _pts(phi, r)
     ids = np.ascontiguousarray(ids, dtype=np.uint32)
     nt = ctypes.c_int32(0)
+    stats = np.zeros(NUM_STATS, dtype=np.int64)
     m = lib().ro_band_count_subset(len(phi), _ptr(phi), _ptr(r), R, B, p, _ptr(ids), len(ids),
-                                   ctypes.byref(nt), None)
+                                   ctypes.byref(nt), _ptr(stats))
+    if with_stats:
+        return int(m), int(nt.value), _stats_dict(stats)
     return int(m), int(nt.value)
 
 
@@ -292,18 +317,47 @@ class Prepared:
         if not self.h:
             raise MemoryError("ro_prepare failed")
 
-    def count_edges(self, ids, threads: int = 0):
-        """(edges, threads used); threads > 0 caps the OpenMP threads for this call."""
+    def count_edges(self, ids, threads: int = 0, with_stats: bool = False):
+        """(edges, threads used[, diagnostics]); threads > 0 caps the OpenMP threads
+        for this call."""
         ids = np.ascontiguousarray(ids, dtype=np.uint32)
         nt = ctypes.c_int32(0)
+        stats = np.zeros(NUM_STATS, dtype=np.int64)
         if threads > 0:
             lib().ro_set_threads(threads)
         try:
-            m = lib().ro_prepared_count(self.h, _ptr(ids), len(ids), ctypes.byref(nt))
+            m = lib().ro_prepared_count(self.h, _ptr(ids), len(ids), ctypes.byref(nt), _ptr(stats))
         finally:
             if threads > 0:
                 lib().ro_set_threads(0)
+        if with_stats:
+            return int(m), int(nt.value), _stats_dict(stats)
         return int(m), int(nt.value)
+
+    def upper_pairs(self, u0: int, u1: int, capacity: int = 0) -> np.ndarray:
+        """Every edge (u, w) with u0 <= u < u1 and u < w, in lexicographic order
+        (uint32, shape (m, 2))."""
+        cap = capacity or max(1 << 16, 64 * (u1 - u0))
+        while True:
+            out = np.empty((cap, 2), dtype=np.uint32)
+            m = lib().ro_prepared_upper_pairs(self.h, u0, u1, _ptr(out), cap)
+            if m < 0:
+                raise MemoryError(f"ro_prepared_upper_pairs status {-m}")
+            if m <= cap:
+                return out[:m]
+            cap = int(m)
+
+    def window_misses(self, ids, theta_scale: float = 1.0) -> dict:
+        """All-pairs edges of the listed vertices checked against their
+        getMinMaxPhi windows (Sec. III-B); theta_scale < 1 narrows the windows
+        (negative control)."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        out = np.zeros(4, dtype=np.int64)
+        st = lib().ro_prepared_window_misses(self.h, _ptr(ids), len(ids), float(theta_scale), _ptr(out))
+        if st != STATUS_OK:
+            raise ValueError(f"ro_prepared_window_misses status {st}")
+        return {"edges": int(out[0]), "misses": int(out[1]), "alg1_edges": int(out[2]),
+                "inner_endpoint_edges": int(out[3])}
 
     def close(self):
         if self.h:

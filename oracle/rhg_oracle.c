@@ -28,11 +28,19 @@
  *     of Aldecoa et al. that Sec. II describes) and the band algorithm (Alg. 1:
  *     bands, per-band angular sort, getMinMaxPhi windows, binary search,
  *     candidate test, outward-only iteration).
- *   - Dynamic model (Sec. III-C, Algorithm 2): step values from Philox counter
- *     (i,1,0,0), rotation modulo 2 pi, the radial step in sinh(alpha r) with
- *     reflection at 0 and sinh(alpha R), and asinh for the way back.
+ *   - Dynamic model (Sec. III-C, Algorithm 2, Theorem 1): step values from
+ *     Philox counter (i,1,0,0), rotation modulo 2 pi, the radial step with
+ *     reflection in the coordinate cosh(alpha r) - 1, which is uniform under
+ *     Eq. 1 as Theorem 1 requires (the sinh(alpha r) of the printed algorithm
+ *     is kept as an option for the test that shows it is not).
  *   - Timed CPU baseline: the band structure built once and the outward
  *     queries of a vertex set counted, OpenMP over the vertices.
+ *   - Checks at scale: every edge (u, w), u < w, of a vertex range in order
+ *     (windowed search of all bands), for pair-by-pair comparison of large
+ *     graphs; the count of edges outside their getMinMaxPhi window (must be
+ *     0); rounding diagnostics of the canonical predicate (pairs within
+ *     8 u cosh r_v cosh r_w of the threshold; pairs a cancellation-free form
+ *     of Eq. 3 decides otherwise, in FP64 and in long double).
  * Every function is pinned in tests/test_oracle_*.py against independent facts
  * (closed forms, mpmath, brute force, invariants, distribution tests).
  */
@@ -264,7 +272,7 @@ double ro_kbar(double R, uint64_t n, double alpha)
     return pre * sum;
 }
 
-/* Binary search for R (the paper fixes only "binary search"; the bracket is the
+/* Binary search for R (the paper names only the method; the bracket is the
  * largest integer grid point j in [0, 255] with kbar(j) > k, and the search
  * keeps kbar(lo) > k >= kbar(hi) until lo and hi are adjacent doubles). */
 int ro_target_radius(uint64_t n, double k, double alpha, double *R_out)
@@ -321,7 +329,7 @@ int ro_boundaries(double R, uint32_t B, double p, double *c)
 }
 
 /* ------------------------------------------------------------------------- */
-/* Alg. 1 lines "draw phi", "draw r": phi ~ U[0,2pi), r with density Eq. 1.   */
+/* Alg. 1, sampling step: phi ~ U[0,2pi), r with the density of Eq. 1.         */
 /* Inverse CDF: F(r) = (cosh(alpha r) - 1)/(cosh(alpha R) - 1), so            */
 /* r = acosh(1 + U (cosh(alpha R) - 1)) / alpha, acosh(1+w) = ln(1 + w +      */
 /* sqrt(w (w + 2))).                                                          */
@@ -550,7 +558,53 @@ typedef struct {
     int64_t candidates;   /* candidate pairs examined (each unordered pair once)    */
     int64_t near;         /* of those, |L - cosh R| <= 1e-12 cosh R                  */
     int64_t windows;      /* (v, band) windows evaluated                             */
+    int64_t band8u;       /* of the candidates, |L - cosh R| <= 8 u ch_v ch_w        */
+    int64_t disagree_wc;  /* decided otherwise by the well-conditioned FP64 form     */
+    int64_t disagree_ld;  /* decided otherwise by the well-conditioned long double form */
 } ro_stats;
+
+#define RO_NUM_STATS 6
+
+static void ro_stats_store(const ro_stats *s, int64_t *out)
+{
+    out[0] = s->candidates; out[1] = s->near; out[2] = s->windows;
+    out[3] = s->band8u; out[4] = s->disagree_wc; out[5] = s->disagree_ld;
+}
+
+static void ro_stats_add(ro_stats *a, const ro_stats *b)
+{
+    a->candidates += b->candidates; a->near += b->near; a->windows += b->windows;
+    a->band8u += b->band8u; a->disagree_wc += b->disagree_wc; a->disagree_ld += b->disagree_ld;
+}
+
+/* Diagnostics of one examined pair with canonical value L (reported, never used
+ * to decide an edge).  The canonical Eq. 3 cancels: its rounding error is below
+ * a few u ch_v ch_w, so only pairs within 16 u ch_v ch_w of the threshold can be
+ * decided differently by a form without cancellation.  For those, Eq. 3 is
+ * rewritten with cosh(a) cosh(b) - sinh(a) sinh(b) = cosh(a - b) and
+ * 1 - cos d = 2 sin^2(d/2):
+ *   L' = cosh(r_v - r_w) + 2 sinh r_v sinh r_w sin^2(d/2),
+ * evaluated once in FP64 (libm) and once in long double (libm). */
+static void ro_diagnose(double phv, double rv, double chv, double shv, double phw, double rw, double chw,
+                        double shw, double L, double coshR, double R, ro_stats *st)
+{
+    const double u = 0x1.0p-53;
+    const double dev = fabs(L - coshR);
+    if (dev <= 1e-12 * coshR) st->near++;
+    const double chch = chv * chw;
+    if (dev <= 8.0 * u * chch) st->band8u++;
+    if (dev > 16.0 * u * chch) return;
+    const int edge = L <= coshR;
+    double d = fabs(phv - phw);
+    double sd = sin(0.5 * d);
+    double Lw = cosh(rv - rw) + 2.0 * shv * shw * (sd * sd);
+    if ((Lw <= cosh(R)) != edge) st->disagree_wc++;
+    long double dl = fabsl((long double)phv - (long double)phw);
+    long double sdl = sinl(0.5L * dl);
+    long double Ll = coshl((long double)rv - (long double)rw) +
+                     2.0L * sinhl((long double)rv) * sinhl((long double)rw) * (sdl * sdl);
+    if ((Ll <= coshl((long double)R)) != edge) st->disagree_ld++;
+}
 
 /* The range query of Alg. 1 for the vertices v in [v0, v1) (ids).  For each
  * band i with c_{i+1} > r_v -- read as every band from v's own band outward --
@@ -600,7 +654,8 @@ static int64_t ro_query_range(const ro_bands *S, const ro_pts *P, const double *
                     if (i == bv && w < v) continue;
                     st->candidates++;
                     double L = ro_L(phi[v], P->ch[v], P->sh[v], phi[w], P->ch[w], P->sh[w]);
-                    if (fabs(L - P->coshR) <= 1e-12 * P->coshR) st->near++;
+                    ro_diagnose(phi[v], r[v], P->ch[v], P->sh[v], phi[w], r[w], P->ch[w], P->sh[w], L, P->coshR,
+                                P->R, st);
                     if (L <= P->coshR) {
                         if ((uint64_t)m < capacity) {
                             pairs[2 * m] = (uint32_t)(v < w ? v : w);
@@ -614,7 +669,8 @@ static int64_t ro_query_range(const ro_bands *S, const ro_pts *P, const double *
     return m;
 }
 
-/* Full band algorithm (Alg. 1) on given points; stats[3] = {candidates, near, windows}. */
+/* Full band algorithm (Alg. 1) on given points; stats[6] = {candidates, near,
+ * windows, band8u, disagree_wc, disagree_ld} (see ro_stats). */
 int64_t ro_band_edges(uint64_t n, const double *phi, const double *r, double R, uint32_t B,
                       double p, uint32_t *pairs, uint64_t capacity, int64_t *stats)
 {
@@ -624,9 +680,10 @@ int64_t ro_band_edges(uint64_t n, const double *phi, const double *r, double R, 
     if (ro_pts_init(&P, n, r, R) != RO_OK) return -RO_ERR_OOM;
     int st = ro_bands_build(&S, n, phi, r, R, B, p);
     if (st != RO_OK) { ro_pts_free(&P); ro_bands_free(&S); return -st; }
-    ro_stats s = {0, 0, 0};
+    ro_stats s;
+    memset(&s, 0, sizeof(s));
     int64_t m = ro_query_range(&S, &P, phi, r, 0, n, pairs, capacity, 0, &s);
-    if (stats) { stats[0] = s.candidates; stats[1] = s.near; stats[2] = s.windows; }
+    if (stats) ro_stats_store(&s, stats);
     ro_pts_free(&P);
     ro_bands_free(&S);
     return m;
@@ -644,38 +701,48 @@ int ro_band_assign(uint64_t n, const double *r, double R, uint32_t B, double p, 
 
 /* Timed CPU baseline: the band algorithm over the given vertex ids, counting
  * edges (no output), OpenMP-parallel over the ids when built with OpenMP.
- * Returns the edge count; *threads receives the number of threads used. */
+ * Returns the edge count; *threads receives the number of threads used and
+ * stats (if not NULL) the RO_NUM_STATS counters of ro_stats. */
+static int64_t ro_count_ids(const ro_bands *S, const ro_pts *P, const double *phi, const double *r,
+                            const uint32_t *ids, uint64_t nids, int32_t *threads, int64_t *stats)
+{
+    int64_t m = 0;
+    int nt = 1;
+    ro_stats tot;
+    memset(&tot, 0, sizeof(tot));
+#ifdef _OPENMP
+#pragma omp parallel reduction(+ : m)
+    {
+        ro_stats loc;
+        memset(&loc, 0, sizeof(loc));
+#pragma omp single
+        nt = omp_get_num_threads();
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t q = 0; q < (int64_t)nids; ++q)
+            m += ro_query_range(S, P, phi, r, ids[q], (uint64_t)ids[q] + 1, NULL, 0, 0, &loc);
+#pragma omp critical
+        ro_stats_add(&tot, &loc);
+    }
+#else
+    for (uint64_t q = 0; q < nids; ++q)
+        m += ro_query_range(S, P, phi, r, ids[q], (uint64_t)ids[q] + 1, NULL, 0, 0, &tot);
+#endif
+    if (threads) *threads = nt;
+    if (stats) ro_stats_store(&tot, stats);
+    return m;
+}
+
 int64_t ro_band_count_subset(uint64_t n, const double *phi, const double *r, double R,
                              uint32_t B, double p, const uint32_t *ids, uint64_t nids,
-                             int32_t *threads, double *setup_seconds_unused)
+                             int32_t *threads, int64_t *stats)
 {
-    (void)setup_seconds_unused;
     ro_pts P;
     ro_bands S;
     memset(&S, 0, sizeof(S));
     if (ro_pts_init(&P, n, r, R) != RO_OK) return -RO_ERR_OOM;
     int st = ro_bands_build(&S, n, phi, r, R, B, p);
     if (st != RO_OK) { ro_pts_free(&P); ro_bands_free(&S); return -st; }
-    int64_t m = 0;
-    int nt = 1;
-#ifdef _OPENMP
-#pragma omp parallel reduction(+ : m)
-    {
-#pragma omp single
-        nt = omp_get_num_threads();
-#pragma omp for schedule(dynamic, 64)
-        for (int64_t q = 0; q < (int64_t)nids; ++q) {
-            ro_stats s = {0, 0, 0};
-            m += ro_query_range(&S, &P, phi, r, ids[q], (uint64_t)ids[q] + 1, NULL, 0, 0, &s);
-        }
-    }
-#else
-    for (uint64_t q = 0; q < nids; ++q) {
-        ro_stats s = {0, 0, 0};
-        m += ro_query_range(&S, &P, phi, r, ids[q], (uint64_t)ids[q] + 1, NULL, 0, 0, &s);
-    }
-#endif
-    if (threads) *threads = nt;
+    int64_t m = ro_count_ids(&S, &P, phi, r, ids, nids, threads, stats);
     ro_pts_free(&P);
     ro_bands_free(&S);
     return m;
@@ -738,30 +805,10 @@ void *ro_prepare(uint64_t n, const double *phi, const double *r, double R, uint3
     return h;
 }
 
-int64_t ro_prepared_count(void *handle, const uint32_t *ids, uint64_t nids, int32_t *threads)
+int64_t ro_prepared_count(void *handle, const uint32_t *ids, uint64_t nids, int32_t *threads, int64_t *stats)
 {
     ro_prepared *h = (ro_prepared *)handle;
-    int64_t m = 0;
-    int nt = 1;
-#ifdef _OPENMP
-#pragma omp parallel reduction(+ : m)
-    {
-#pragma omp single
-        nt = omp_get_num_threads();
-#pragma omp for schedule(dynamic, 16)
-        for (int64_t q = 0; q < (int64_t)nids; ++q) {
-            ro_stats s = {0, 0, 0};
-            m += ro_query_range(&h->S, &h->P, h->phi, h->r, ids[q], (uint64_t)ids[q] + 1, NULL, 0, 0, &s);
-        }
-    }
-#else
-    for (uint64_t q = 0; q < nids; ++q) {
-        ro_stats s = {0, 0, 0};
-        m += ro_query_range(&h->S, &h->P, h->phi, h->r, ids[q], (uint64_t)ids[q] + 1, NULL, 0, 0, &s);
-    }
-#endif
-    if (threads) *threads = nt;
-    return m;
+    return ro_count_ids(&h->S, &h->P, h->phi, h->r, ids, nids, threads, stats);
 }
 
 void ro_prepared_free(void *handle)
@@ -773,8 +820,208 @@ void ro_prepared_free(void *handle)
     free(h);
 }
 
+/* Is phw inside the angular window [phv - th, phv + th] (modulo 2 pi)?  The same
+ * membership the range query's binary searches give (both ends included). */
+static int ro_in_window(double phv, double th, double phw)
+{
+    if (th >= RO_PI) return 1;
+    double lo = phv - th, hi = phv + th;
+    if (lo < 0.0) return phw >= lo + RO_TWO_PI || phw <= hi;
+    if (hi >= RO_TWO_PI) return phw >= lo || phw <= hi - RO_TWO_PI;
+    return lo <= phw && phw <= hi;
+}
+
+static int ro_cmp_u32(const void *a, const void *b)
+{
+    uint32_t x = *(const uint32_t *)a, y = *(const uint32_t *)b;
+    return x < y ? -1 : (x > y);
+}
+
+/* Neighbours w > u of one vertex u, ascending, appended to *buf (grown as needed).
+ * Every band is searched (inward as well as outward): getMinMaxPhi's window at a
+ * band's inner radius bounds the angle of every neighbour in that band, whichever
+ * side of u the band lies (Sec. III-B: for b >= cosh r_u the admissible angle
+ * grows with r_w, so the inner radius is the worst case).  Returns the new length
+ * or -1 when out of memory. */
+static int64_t ro_upper_neighbors_one(const ro_bands *S, const ro_pts *P, const double *phi, const double *r,
+                                      uint64_t u, uint32_t **buf, uint64_t *cap, uint64_t len)
+{
+    uint64_t first = len;
+    for (uint32_t i = 0; i < S->B; ++i) {
+        uint64_t s = S->start[i], e = S->start[i + 1];
+        if (s == e) continue;
+        double th = ro_min_max_phi(r[u], P->ch[u], P->sh[u], P->coshR, S->c[i], S->c[i + 1]);
+        uint64_t ranges[2][2];
+        int nr;
+        if (th >= RO_PI) {
+            ranges[0][0] = s; ranges[0][1] = e; nr = 1;
+        } else {
+            double lo = phi[u] - th, hi = phi[u] + th;
+            if (lo < 0.0) {
+                ranges[0][0] = ro_lower(S->sphi, s, e, lo + RO_TWO_PI); ranges[0][1] = e;
+                ranges[1][0] = s; ranges[1][1] = ro_upper(S->sphi, s, e, hi);
+                nr = 2;
+            } else if (hi >= RO_TWO_PI) {
+                ranges[0][0] = ro_lower(S->sphi, s, e, lo); ranges[0][1] = e;
+                ranges[1][0] = s; ranges[1][1] = ro_upper(S->sphi, s, e, hi - RO_TWO_PI);
+                nr = 2;
+            } else {
+                ranges[0][0] = ro_lower(S->sphi, s, e, lo);
+                ranges[0][1] = ro_upper(S->sphi, s, e, hi);
+                nr = 1;
+            }
+            if (nr == 2 && ranges[1][1] > ranges[0][0]) {
+                ranges[0][0] = s; ranges[0][1] = e; nr = 1;
+            }
+        }
+        for (int k = 0; k < nr; ++k)
+            for (uint64_t q = ranges[k][0]; q < ranges[k][1]; ++q) {
+                uint32_t w = S->order[q];
+                if (w <= u) continue;
+                double L = ro_L(phi[u], P->ch[u], P->sh[u], phi[w], P->ch[w], P->sh[w]);
+                if (L > P->coshR) continue;
+                if (len == *cap) {
+                    uint64_t nc = *cap ? 2 * *cap : 4096;
+                    uint32_t *nb = (uint32_t *)realloc(*buf, sizeof(uint32_t) * 2 * nc);
+                    if (!nb) return -1;
+                    *buf = nb;
+                    *cap = nc;
+                }
+                (*buf)[2 * len] = (uint32_t)u;
+                (*buf)[2 * len + 1] = w;
+                ++len;
+            }
+    }
+    /* one vertex's pairs share u: sorting the (u, w) records by w sorts the row */
+    uint64_t cnt = len - first;
+    if (cnt > 1) {
+        uint32_t *row = (uint32_t *)malloc(sizeof(uint32_t) * cnt);
+        if (!row) return -1;
+        for (uint64_t j = 0; j < cnt; ++j) row[j] = (*buf)[2 * (first + j) + 1];
+        qsort(row, cnt, sizeof(uint32_t), ro_cmp_u32);
+        for (uint64_t j = 0; j < cnt; ++j) (*buf)[2 * (first + j) + 1] = row[j];
+        free(row);
+    }
+    return (int64_t)len;
+}
+
+/* Every edge (u, w) with u in [u0, u1) and u < w, in lexicographic order: the
+ * edge set of the plain definition cut into vertex ranges, so that a large graph
+ * can be compared pair by pair one range at a time.  OpenMP over u with a static
+ * schedule (thread t owns the t-th contiguous block of u, so concatenating the
+ * threads' buffers in thread order keeps the order).  Writes the pairs when they
+ * fit into `capacity`; returns m (or a negative status). */
+int64_t ro_prepared_upper_pairs(void *handle, uint64_t u0, uint64_t u1, uint32_t *pairs, uint64_t capacity)
+{
+    ro_prepared *h = (ro_prepared *)handle;
+    if (!h || u1 > h->n || u0 > u1) return -RO_ERR_INVALID_ARG;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = omp_get_max_threads();
+#endif
+    uint32_t **bufs = (uint32_t **)calloc((size_t)nt, sizeof(uint32_t *));
+    uint64_t *lens = (uint64_t *)calloc((size_t)nt, sizeof(uint64_t));
+    int failed = 0;
+    if (!bufs || !lens) { free(bufs); free(lens); return -RO_ERR_OOM; }
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        uint64_t cap = 0, len = 0;
+        uint32_t *buf = NULL;
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int64_t u = (int64_t)u0; u < (int64_t)u1; ++u) {
+            int f;
+#ifdef _OPENMP
+#pragma omp atomic read
+#endif
+            f = failed;
+            if (f) continue;
+            int64_t nl = ro_upper_neighbors_one(&h->S, &h->P, h->phi, h->r, (uint64_t)u, &buf, &cap, len);
+            if (nl < 0) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+                failed = 1;
+            } else {
+                len = (uint64_t)nl;
+            }
+        }
+        bufs[t] = buf;
+        lens[t] = len;
+    }
+    uint64_t m = 0;
+    for (int t = 0; t < nt; ++t) m += lens[t];
+    if (!failed && m <= capacity) {
+        uint64_t at = 0;
+        for (int t = 0; t < nt; ++t) {
+            if (lens[t]) memcpy(pairs + 2 * at, bufs[t], sizeof(uint32_t) * 2 * lens[t]);
+            at += lens[t];
+        }
+    }
+    for (int t = 0; t < nt; ++t) free(bufs[t]);
+    free(bufs);
+    free(lens);
+    return failed ? -RO_ERR_OOM : (int64_t)m;
+}
+
+/* Window check at scale (Sec. III-B getMinMaxPhi): for each listed vertex v, every
+ * edge (v, w) of the plain definition (all n points tested) must lie inside v's
+ * window for w's band, evaluated at that band's inner radius, inward bands
+ * included.  out[0] = edges examined, out[1] = edges outside their window (must be
+ * 0), out[2] = edges found by Alg. 1 from v's side (outward bands, same band from
+ * the smaller id), out[3] = edges of v whose inner endpoint is v by that rule.
+ * theta_scale multiplies every window narrower than the whole band: 1 for the
+ * check, below 1 for the test that shows the check detects narrow windows.
+ * OpenMP over the listed vertices. */
+int ro_prepared_window_misses(void *handle, const uint32_t *ids, uint64_t nids, double theta_scale, int64_t *out)
+{
+    ro_prepared *h = (ro_prepared *)handle;
+    if (!h || !out) return RO_ERR_INVALID_ARG;
+    int64_t edges = 0, misses = 0, alg1 = 0, owned = 0;
+    const ro_bands *S = &h->S;
+    const ro_pts *P = &h->P;
+    const double *phi = h->phi, *r = h->r;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : edges, misses, alg1, owned)
+#endif
+    for (int64_t q = 0; q < (int64_t)nids; ++q) {
+        uint64_t v = ids[q];
+        if (v >= h->n) continue;
+        double th[RO_MAX_BANDS];
+        for (uint32_t i = 0; i < S->B; ++i) {
+            th[i] = ro_min_max_phi(r[v], P->ch[v], P->sh[v], P->coshR, S->c[i], S->c[i + 1]);
+            if (th[i] < RO_PI) th[i] = th[i] * theta_scale;
+        }
+        uint32_t bv = S->band[v];
+        for (uint64_t w = 0; w < h->n; ++w) {
+            if (w == v) continue;
+            double L = ro_L(phi[v], P->ch[v], P->sh[v], phi[w], P->ch[w], P->sh[w]);
+            if (L > P->coshR) continue;
+            ++edges;
+            uint32_t bw = S->band[w];
+            if (!ro_in_window(phi[v], th[bw], phi[w])) ++misses;
+            if (bw > bv || (bw == bv && w > v)) ++owned;
+        }
+        ro_stats st;
+        memset(&st, 0, sizeof(st));
+        alg1 += ro_query_range(S, P, phi, r, v, v + 1, NULL, 0, 0, &st);
+    }
+    out[0] = edges;
+    out[1] = misses;
+    out[2] = alg1;
+    out[3] = owned;
+    return RO_OK;
+}
+
 /* ------------------------------------------------------------------------- */
-/* Dynamic model (Sec. III-C; Algorithm 2, radial movement).                  */
+/* Dynamic model (Sec. III-C; Algorithm 2, radial movement; Theorem 1).       */
 /*                                                                            */
 /* Step values of node i: Philox counter (i, 1, 0, 0), key (seed, 0), words    */
 /* x0, x1; U = (x >> 11) * 2^-53; tau_phi = lo_phi + (hi_phi - lo_phi) * U0,   */
@@ -784,12 +1031,23 @@ void ro_prepared_free(void *handle)
 /*   rotation   p = phi + tau_phi, brought into [0, 2pi) by subtracting or     */
 /*              adding 2pi (a sum that rounds up to 2pi becomes the largest    */
 /*              double below 2pi);                                            */
-/*   radial     x = sinh(alpha r), y = x + tau_r; while y is outside           */
-/*              [0, sinh(alpha R)] the step is mirrored at the boundary it      */
-/*              crossed (y = 2 sinh(alpha R) - y, or y = -y) and tau_r changes  */
-/*              sign (the node bounces); r = asinh(y) / alpha (times 1/alpha),  */
-/*              at most R.                                                    */
+/*   radial     the radius is mapped to a coordinate x, moved to y = x + tau_r */
+/*              and mapped back; while y is outside [0, top] the step is       */
+/*              mirrored at the boundary it crossed (y = 2 top - y, or y = -y) */
+/*              and tau_r changes sign (the node bounces).                    */
+/* Theorem 1 needs x to be uniformly distributed when r follows Eq. 1 (the      */
+/* figure of Sec. III-C says so of its coordinate): then a reflected walk of   */
+/* x keeps the density.  Under Eq. 1 the CDF is (cosh(alpha r) - 1) /           */
+/* (cosh(alpha R) - 1), so the uniform coordinate is                           */
+/*   coord 0:   x = cosh(alpha r) - 1 = 2 sinh^2(alpha r / 2), top = cosh(alpha R) - 1, */
+/*              r = 2 asinh(sqrt(y / 2)) / alpha;                              */
+/* Algorithm 2 as printed maps to sinh(alpha r), whose density under Eq. 1 is  */
+/* x / ((cosh(alpha R) - 1) sqrt(1 + x^2)), not uniform (the proof omits the    */
+/* Jacobian of the map); it is kept as                                         */
+/*   coord 1:   x = sinh(alpha r), top = sinh(alpha R), r = asinh(y) / alpha,  */
+/* and the tests show that it does not keep Eq. 1 while coord 0 does.         */
 /*   asinh(y) = log(y + sqrt(y*y + 1)) for y >= 0, each operation rounded.     */
+/* The way back is capped at R.                                               */
 /* ------------------------------------------------------------------------- */
 double ro_asinh(double y)
 {
@@ -818,10 +1076,10 @@ void ro_draw_movement(uint64_t n, uint64_t seed, double phi_lo, double phi_hi, d
 }
 
 void ro_move(uint64_t count, const uint32_t *ids, double *phi, double *r, const double *tau_phi, double *tau_r,
-             double R, double alpha)
+             double R, double alpha, int32_t coord)
 {
     double aR = alpha * R;
-    const double top = ro_sinh(aR);
+    const double top = coord == 1 ? ro_sinh(aR) : ro_cosh(aR) - 1.0;
     const double inv_alpha = 1.0 / alpha;
     const double below = nextafter(RO_TWO_PI, 0.0);
     for (uint64_t j = 0; j < count; ++j) {
@@ -833,7 +1091,15 @@ void ro_move(uint64_t count, const uint32_t *ids, double *phi, double *r, const 
         if (p < 0.0) p = 0.0;
         double tr = tau_r[i];
         double ar = alpha * r[i];
-        double x = ro_sinh(ar);
+        double x;
+        if (coord == 1) {
+            x = ro_sinh(ar);
+        } else {
+            double half = ar * 0.5;
+            double sh = ro_sinh(half);
+            double sq = sh * sh;
+            x = sq * 2.0;
+        }
         double y = x + tr;
         for (int it = 0; it < 64 && (y > top || y < 0.0); ++it) {
             if (y > top) {
@@ -846,7 +1112,16 @@ void ro_move(uint64_t count, const uint32_t *ids, double *phi, double *r, const 
         }
         if (y > top) y = top;
         if (y < 0.0) y = 0.0;
-        double z = ro_asinh(y) * inv_alpha;
+        double z;
+        if (coord == 1) {
+            z = ro_asinh(y) * inv_alpha;
+        } else {
+            double hy = y * 0.5;
+            double sy = sqrt(hy);
+            double as = ro_asinh(sy);
+            double two = as * 2.0;
+            z = two * inv_alpha;
+        }
         if (z > R) z = R;
         phi[i] = p;
         r[i] = z;

@@ -29,14 +29,16 @@ int64_t ro_band_edges(uint64_t n, const double *phi, const double *r, double R, 
                       uint32_t *pairs, uint64_t capacity, int64_t *stats);
 int ro_band_assign(uint64_t n, const double *r, double R, uint32_t B, double p, uint32_t *band);
 int64_t ro_band_count_subset(uint64_t n, const double *phi, const double *r, double R, uint32_t B, double p,
-                             const uint32_t *ids, uint64_t nids, int32_t *threads, double *unused);
+                             const uint32_t *ids, uint64_t nids, int32_t *threads, int64_t *stats);
 void *ro_prepare(uint64_t n, const double *phi, const double *r, double R, uint32_t B, double p);
-int64_t ro_prepared_count(void *handle, const uint32_t *ids, uint64_t nids, int32_t *threads);
+int64_t ro_prepared_count(void *handle, const uint32_t *ids, uint64_t nids, int32_t *threads, int64_t *stats);
+int64_t ro_prepared_upper_pairs(void *handle, uint64_t u0, uint64_t u1, uint32_t *pairs, uint64_t capacity);
+int ro_prepared_window_misses(void *handle, const uint32_t *ids, uint64_t nids, double theta_scale, int64_t *out);
 void ro_prepared_free(void *handle);
 void ro_draw_movement(uint64_t n, uint64_t seed, double phi_lo, double phi_hi, double r_lo, double r_hi,
                       double *tau_phi, double *tau_r);
 void ro_move(uint64_t count, const uint32_t *ids, double *phi, double *r, const double *tau_phi, double *tau_r,
-             double R, double alpha);
+             double R, double alpha, int32_t coord);
 void ro_constants(double *out);
 
 static int fails = 0;
@@ -60,7 +62,7 @@ static void graph_case(uint64_t n, double k, double alpha, uint64_t seed)
     CHECK(ro_brute_edges(n, phi, r, R, pairs, (uint64_t)m) == m);
     uint32_t B = ro_default_bands(n);
     for (uint32_t b = 1; b <= B + 2; b += 1 + B / 3) {
-        int64_t stats[3] = {0, 0, 0};
+        int64_t stats[6] = {0, 0, 0, 0, 0, 0};
         CHECK(ro_band_edges(n, phi, r, R, b, 0.9, pairs, (uint64_t)m / 2, stats) == m);  /* short room */
         CHECK(ro_band_edges(n, phi, r, R, b, 0.9, pairs, (uint64_t)m, stats) == m);
     }
@@ -69,11 +71,22 @@ static void graph_case(uint64_t n, double k, double alpha, uint64_t seed)
     for (uint64_t i = 0; i < n; ++i) CHECK(band[i] < B);
     for (uint64_t i = 0; i < n; ++i) ids[i] = (uint32_t)i;
     int32_t nt = 0;
+    int64_t st6[6];
     CHECK(ro_band_count_subset(n, phi, r, R, B, 0.9, ids, n, &nt, NULL) == m);
+    CHECK(ro_band_count_subset(n, phi, r, R, B, 0.9, ids, n, &nt, st6) == m);
     void *h = ro_prepare(n, phi, r, R, B, 0.9);
     CHECK(h != NULL);
     if (h) {
-        CHECK(ro_prepared_count(h, ids, n, &nt) == m);
+        CHECK(ro_prepared_count(h, ids, n, &nt, NULL) == m);
+        CHECK(ro_prepared_count(h, ids, n, &nt, st6) == m);
+        /* ordered pairs: short room first (nothing written), then the exact room, in two ranges */
+        CHECK(ro_prepared_upper_pairs(h, 0, n, pairs, (uint64_t)m / 2) == m);
+        int64_t m1 = ro_prepared_upper_pairs(h, 0, n / 2, pairs, (uint64_t)m);
+        CHECK(m1 >= 0 && m1 <= m);
+        CHECK(ro_prepared_upper_pairs(h, n / 2, n, pairs + 2 * (m1 > 0 ? m1 : 0), (uint64_t)(m - m1)) == m - m1);
+        CHECK(ro_prepared_upper_pairs(h, n, n + 1, pairs, 0) < 0);  /* range beyond n */
+        int64_t wm[4];
+        CHECK(ro_prepared_window_misses(h, ids, n < 50 ? n : 50, 1.0, wm) == 0 && wm[1] == 0);
         ro_prepared_free(h);
     }
     int64_t deg = 0;
@@ -86,7 +99,8 @@ static void graph_case(uint64_t n, double k, double alpha, uint64_t seed)
     CHECK(deg >= 0);
     double *tp = malloc(n * sizeof(double)), *tr = malloc(n * sizeof(double));
     ro_draw_movement(n, seed, -1.0, 1.0, -10.0, 1.0, tp, tr);
-    ro_move(n / 2, ids + n / 4, phi, r, tp, tr, R, alpha);
+    ro_move(n / 2, ids + n / 4, phi, r, tp, tr, R, alpha, 0);
+    ro_move(n / 2, ids + n / 4, phi, r, tp, tr, R, alpha, 1);
     for (uint64_t i = 0; i < n; ++i) CHECK(phi[i] >= 0.0 && r[i] >= 0.0 && r[i] <= R);
     free(tp);
     free(tr);

@@ -1,4 +1,4 @@
-"""Pins for the oracle's points (Alg. 1 "draw phi", "draw r"; Eq. 1) and bands
+"""Pins for the oracle's points (Alg. 1 sampling step; Eq. 1) and bands
 (Sec. III-A).  The radial coordinate is checked point by point against the
 inverse-CDF identity F(r_i) = U_i, with F from Eq. 1 evaluated by numpy and U_i
 from numpy's Philox, and in distribution by Kolmogorov-Smirnov tests."""
