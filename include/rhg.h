@@ -102,12 +102,15 @@ typedef struct rhg_result {
                                  contradicts (0 unless the filter's error bound fails) */
     uint32_t mode;            /* 1: FP32 filter + FP64 recheck; 0: FP64 predicate only */
     uint32_t heavy_chunks;    /* long candidate ranges split across warps (diagnostic)  */
+    uint64_t rounding_band;   /* candidates with |L - cosh R| <= 8 u cosh r_v cosh r_w
+                                 (u = 2^-53): the pairs whose decision the rounding of
+                                 Eq. 3 in FP64 can flip (diagnostic)                   */
 } rhg_result;
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char *rhg_status_str(int status);
 
-/* ABI version of this header: 1. */
+/* ABI version of this header: 2 (2 added rhg_result.rounding_band). */
 int rhg_version(void);
 
 /*
@@ -147,7 +150,7 @@ int rhg_plan(const rhg_params *p, void *d_workspace, size_t workspace_bytes, voi
 int rhg_workspace_bytes(const rhg_params *p, uint64_t capacity_entries, size_t *bytes);
 
 /*
- * rhg_sample_points -- the points of Alg. 1 ("draw phi", "draw r"), by id:
+ * rhg_sample_points -- the points of Alg. 1 (its sampling step), by id:
  * d_phi[i], d_r[i] for i < n (FP64; Philox4x64-10, inverse CDF of Eq. 1).
  * d_workspace must hold rhg_plan_workspace_bytes().  Writes R to *R_out and
  * synchronises the stream.
@@ -191,8 +194,11 @@ int rhg_generate_pairs_host(const rhg_params *p, void *d_workspace, size_t works
  * graph whose workspace (rhg_workspace_bytes) exceeds the scratch (a dense graph
  * that may run in FP64 mode, whose chunk list grows with n k), returns
  * RHG_ERR_INVALID_ARG before anything is launched.  The array's address is
- * looked up on the first call on each device (with that device current), so
- * that first call should come before any stream capture begins.  Nothing in the
+ * looked up by the first call in each CUDA context (the current device's primary
+ * context, or the caller's own; a context created again after cudaDeviceReset
+ * gets a new lookup), so that first call should come before any stream capture
+ * begins.  Like rhg_generate_pairs, every call ends with a synchronisation of
+ * `stream` to read back the edge count.  Nothing in the
  * scratch has to start at zero: the first kernel of every call resets the
  * counters it uses.  All calls on one device share the one array, so calls
  * that overlap in time (other host threads, or other streams before the
@@ -315,11 +321,15 @@ int rhg_batch_read_results(const rhg_batch_plan *plan, const void *d_workspace, 
 
 /*
  * Dynamic model (Sec. III-C): vertices move in discrete steps, each a rotation
- * phi + tau_phi (mod 2 pi) and the radial movement of Algorithm 2 in the
- * coordinate sinh(alpha r): y = sinh(alpha r) + tau_r, mirrored at sinh(alpha R)
- * or at 0 while outside (tau_r changes sign: the vertex bounces), then
- * r = asinh(y) / alpha (at most R).  All FP64, in the fixed operation order of
- * the library's deterministic functions.
+ * phi + tau_phi (mod 2 pi) and the radial movement of Algorithm 2 with
+ * reflection, taken in the coordinate x = cosh(alpha r) - 1 (computed as
+ * 2 sinh^2(alpha r / 2)): y = x + tau_r, mirrored at cosh(alpha R) - 1 or at 0
+ * while outside (tau_r changes sign: the vertex bounces), then
+ * r = 2 asinh(sqrt(y / 2)) / alpha (at most R).  Theorem 1 (the positions keep
+ * the density of Eq. 1) holds for a coordinate that is uniform under Eq. 1;
+ * x is (its CDF is x / (cosh(alpha R) - 1)), while the sinh(alpha r) printed in
+ * Algorithm 2 is not, and a walk in it drifts towards the centre.  All FP64, in
+ * the fixed operation order of the library's deterministic functions.
  *
  * rhg_draw_movement -- step values of vertices 0 .. n-1 from Philox counter
  * (i, 1, 0, 0), key (seed, 0): tau_phi uniform in [phi_lo, phi_hi), tau_r

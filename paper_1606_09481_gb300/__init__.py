@@ -43,7 +43,8 @@ class Params(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("m", _c_u64), ("R", _c_dbl), ("num_bands", _c_u32), ("cuda_error", ctypes.c_int32),
                 ("candidates", _c_u64), ("near_threshold", _c_u64), ("rechecks", _c_u64),
-                ("verify_failures", _c_u64), ("mode", _c_u32), ("heavy_chunks", _c_u32)]
+                ("verify_failures", _c_u64), ("mode", _c_u32), ("heavy_chunks", _c_u32),
+                ("rounding_band", _c_u64)]
 
     def asdict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -276,19 +277,26 @@ def allocate_pairs(params: Params, capacity: int | None = None) -> Workspace:
 
 
 def generate_pairs(n, k, alpha, seed, num_bands=0, band_ratio=0.0, flags=0, R_override=0.0,
-                   workspace: Workspace | None = None, stream=None):
+                   workspace: Workspace | None = None, stream=None, overflow_retry: bool = True):
     """Edges as an (m, 2) int32 CUDA tensor of uint32 ids (u < v), and the Result.
 
-    Allocates the output from n k / 2 with slack; on RHG_ERR_OVERFLOW it
-    reallocates to the exact size reported and calls again."""
+    Allocates the output from n k / 2 with slack.  On RHG_ERR_OVERFLOW (more
+    edges than room) it keeps the workspace, replaces the output by one of the
+    exact size reported and calls again; with overflow_retry=False it raises
+    RhgError(OVERFLOW) instead, whose result.m is the exact edge count."""
     p = make_params(n, k, alpha, seed, num_bands, band_ratio, R_override, flags)
     wsp = workspace or allocate_pairs(p)
     res = Result()
     L = load()
     rc = L.rhg_generate_pairs(ctypes.byref(p), wsp.ws.data_ptr(), wsp.ws.numel(), wsp.out.data_ptr(),
                               wsp.capacity, _stream(stream), ctypes.byref(res))
-    if rc == OVERFLOW:
-        wsp = allocate_pairs(p, int(res.m))
+    if rc == OVERFLOW and overflow_retry:
+        m = int(res.m)
+        out = wsp.out
+        if workspace is None:
+            wsp.out = None  # our own buffer: released before the larger one is made
+        del out
+        wsp = Workspace(wsp.ws, _torch().empty(max(2 * m, 2), dtype=_torch().int32, device="cuda"), m)
         rc = L.rhg_generate_pairs(ctypes.byref(p), wsp.ws.data_ptr(), wsp.ws.numel(), wsp.out.data_ptr(),
                                   wsp.capacity, _stream(stream), ctypes.byref(res))
     _check(rc, "rhg_generate_pairs", res)

@@ -10,6 +10,7 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "kernels.h"
@@ -59,23 +60,48 @@ struct Layout {
 
 constexpr uint64_t kMaxListEntries = 0x7fffffffull;
 
+// Eq. 22 (zeta = 1) in plain double arithmetic, for host-side sizing only (the
+// device plan computes the R the graph uses).
+double host_kbar(double R, double n, double a)
+{
+    const double pi = 3.14159265358979323846, xi = a / (a - 0.5);
+    const double inner = pi / (4.0 * a * a) - (pi - 1.0) / a + (pi - 2.0);
+    return 2.0 / pi * xi * xi * n * (std::exp(-R / 2.0) + std::exp(-a * R) * (a * R / 2.0 * inner - 1.0));
+}
+
+// R of Eq. 22 for sizing: the decreasing-branch solution by bisection, as the
+// device plan does it (largest integer j in [0, 255] with kbar(j) > k, then
+// bisection); within ~1e-12 of the device's R.  0 when there is no solution.
+double host_radius_estimate(const rhg_params &p)
+{
+    if (p.R_override > 0.0) return p.R_override;
+    const double n = static_cast<double>(p.n);
+    int j = -1;
+    for (int t = 0; t < 256; ++t)
+        if (host_kbar(t, n, p.alpha) > p.k) j = t;
+    if (j < 0 || j == 255) return 0.0;
+    double lo = j, hi = j + 1.0;
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (host_kbar(mid, n, p.alpha) > p.k) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
 // Chunk-list entries beyond n/4 + 65536 for a graph that may run in FP64 mode
 // (RHG_FLAG_FP64_ONLY, or R > 32 or alpha R > 44, which decide the mode on the
-// device): without a core every window is tested, and each tested piece longer
-// than 32 candidates becomes at least one chunk, so the list is sized by the
-// candidates, about 1.1-2 times the n k / 2 edges: n k / 20 entries.  For an
-// R_override the degree comes from Eq. 22 at that R.
+// device; R solved from Eq. 22 on the host, with a margin of 0.25 for the
+// difference to the device's R): without a core every window is tested, and
+// each tested piece longer than 32 candidates becomes at least one chunk, so the
+// list is sized by the candidates, about 1.1-2 times the n k / 2 edges:
+// n k / 20 entries, with k from Eq. 22 at R for an R_override.
 uint64_t fp64_chunk_extra(const rhg_params &p)
 {
-    bool fp64 = (p.flags & RHG_FLAG_FP64_ONLY) != 0 || p.alpha * kFilterMaxR > kFilterMaxAlphaR;
-    double k = p.k;
-    if (p.R_override > 0.0) {
-        fp64 = fp64 || p.R_override > kFilterMaxR || p.alpha * p.R_override > kFilterMaxAlphaR;
-        const double R = p.R_override, a = p.alpha, xi = a / (a - 0.5), pi = 3.14159265358979323846;
-        const double inner = pi / (4.0 * a * a) - (pi - 1.0) / a + (pi - 2.0);
-        k = 2.0 / pi * xi * xi * static_cast<double>(p.n) *
-            (std::exp(-R / 2.0) + std::exp(-a * R) * (a * R / 2.0 * inner - 1.0));
-    }
+    const double R = host_radius_estimate(p);
+    const bool fp64 = (p.flags & RHG_FLAG_FP64_ONLY) != 0 || R > kFilterMaxR - 0.25 ||
+                      p.alpha * R > kFilterMaxAlphaR - 0.25;
+    const double k = p.R_override > 0.0 ? host_kbar(p.R_override, static_cast<double>(p.n), p.alpha) : p.k;
     if (!fp64 || !(k > 0.0)) return 0;
     const double extra = std::ceil(static_cast<double>(p.n) * k / 20.0);
     return extra < static_cast<double>(kMaxListEntries) ? static_cast<uint64_t>(extra) : kMaxListEntries;
@@ -185,6 +211,7 @@ void fill_result(rhg_result *res, const Meta &h)
     res->num_bands = h.B;
     res->candidates = h.candidates;
     res->near_threshold = h.near_threshold;
+    res->rounding_band = h.rounding_band;
     res->rechecks = h.rechecks;
     res->verify_failures = h.verify_failures;
     res->mode = h.filter ? 1u : 0u;
@@ -613,6 +640,7 @@ int fill_batch_results(uint32_t count, const uint4 *res, const Meta &ctl, const 
         totals->m = total_m;
         totals->candidates = ctl.candidates;
         totals->near_threshold = ctl.near_threshold;
+        totals->rounding_band = ctl.rounding_band;
         totals->rechecks = ctl.rechecks;
         totals->verify_failures = ctl.verify_failures;
         totals->heavy_chunks = ctl.heavy_n;
@@ -655,27 +683,79 @@ UpdateLayout update_layout(uint64_t n, uint64_t moved, uint32_t B)
     return U;
 }
 
-// Scratch of rhg_generate_pairs_static: one array per device, found by symbol.
-constexpr int kMaxDevices = 64;
+// Scratch of rhg_generate_pairs_static: one array in the device image, found by
+// symbol.  Each CUDA context (the primary context of each device, a new primary
+// context after cudaDeviceReset, a caller's own context) loads its own copy of
+// the image, so the address is looked up once per context and cached under the
+// context's unique id (cuCtxGetId), reached through the runtime's driver entry
+// points so that the library needs no link to the driver library.
 __device__ __align__(256) unsigned char g_static_scratch[RHG_STATIC_SCRATCH_BYTES];
+constexpr int kMaxContexts = 64;
 std::mutex g_static_mu;
-void *g_static_ptr[kMaxDevices] = {};
+unsigned long long g_static_ctx[kMaxContexts] = {};  // context ids (0: unused slot)
+void *g_static_ptr[kMaxContexts] = {};
+int g_static_next = 0;
 
-// The current device's scratch address; the lookup runs once per device.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Id of the calling thread's current context (0 if there is none yet).
+int current_context_id(unsigned long long *id, cudaError_t *err)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {  // under g_static_mu
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        *err = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (*err == cudaSuccess)
+            *err = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (*err != cudaSuccess) return RHG_ERR_CUDA;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            *err = cudaErrorNotSupported;
+            return RHG_ERR_CUDA;
+        }
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext ctx = nullptr;
+    *id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS) {
+        *err = cudaErrorDeviceUninitialized;
+        return RHG_ERR_CUDA;
+    }
+    if (ctx && get_id(ctx, id) != CUDA_SUCCESS) {
+        *err = cudaErrorDeviceUninitialized;
+        return RHG_ERR_CUDA;
+    }
+    return RHG_OK;
+}
+
+// The current context's scratch address; the lookup runs once per context.
 int static_scratch(void **ptr, cudaError_t *err)
 {
-    int dev = -1;
-    *err = cudaGetDevice(&dev);
-    if (*err != cudaSuccess) return RHG_ERR_CUDA;
-    if (dev < 0 || dev >= kMaxDevices) return RHG_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        void *a = nullptr;
-        *err = cudaGetSymbolAddress(&a, g_static_scratch);
-        if (*err != cudaSuccess) return RHG_ERR_CUDA;
-        g_static_ptr[dev] = a;
+    unsigned long long id = 0;
+    int rc = current_context_id(&id, err);
+    if (rc) return rc;
+    for (int j = 0; id && j < kMaxContexts; ++j)
+        if (g_static_ctx[j] == id) {
+            *ptr = g_static_ptr[j];
+            return RHG_OK;
+        }
+    void *a = nullptr;
+    *err = cudaGetSymbolAddress(&a, g_static_scratch);  // makes the device's primary context current if none is
+    if (*err != cudaSuccess) return RHG_ERR_CUDA;
+    if (!id) {
+        rc = current_context_id(&id, err);
+        if (rc) return rc;
     }
-    *ptr = g_static_ptr[dev];
+    if (id) {  // slots are reused round robin once every slot has been taken
+        g_static_ctx[g_static_next] = id;
+        g_static_ptr[g_static_next] = a;
+        g_static_next = (g_static_next + 1) % kMaxContexts;
+    }
+    *ptr = a;
     return RHG_OK;
 }
 
@@ -710,7 +790,7 @@ const char *rhg_status_str(int status)
     }
 }
 
-int rhg_version(void) { return 1; }
+int rhg_version(void) { return 2; }
 
 int rhg_set_stage_events(void *const *events, uint32_t count)
 {

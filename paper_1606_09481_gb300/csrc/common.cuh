@@ -67,7 +67,8 @@ struct Meta {
     double k;
     uint64_t m;              // edges found (exact), also the output cursor
     uint64_t candidates;
-    uint64_t near_threshold;
+    uint64_t near_threshold;  // FP64-decided pairs with |L - cosh R| <= 1e-12 cosh R
+    uint64_t rounding_band;   // FP64-decided pairs with |L - cosh R| <= 8 u cosh r_v cosh r_w
     uint64_t rechecks;
     uint64_t verify_failures;
     uint32_t heavy_n, heavy_next;      // heavy-range chunk list

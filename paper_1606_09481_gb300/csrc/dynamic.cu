@@ -1,5 +1,6 @@
 // dynamic.cu -- the dynamic model (Sec. III-C): step values, one movement step
-// (rotation and the radial movement of Algorithm 2 with reflection at 0 and R)
+// (rotation and the radial movement of Algorithm 2 with reflection at 0 and R,
+// in the coordinate cosh(alpha r) - 1 under which Theorem 1 holds)
 // and the pieces of an edge-list update after a step: marking the moved
 // vertices, listing their sorted positions, a scan of per-vertex counts, and
 // keeping the old edges whose endpoints both stayed.
@@ -38,13 +39,17 @@ __global__ void draw_movement_kernel(uint64_t n, uint64_t seed, double phi_lo, d
 }
 
 // One movement step of the listed vertices, in place.  Rotation: phi + tau_phi
-// brought into [0, 2 pi).  Radial (Algorithm 2): y = sinh(alpha r) + tau_r,
-// mirrored at sinh(alpha R) or 0 while outside (tau_r changes sign each time),
-// r = asinh(y) / alpha, at most R.  Ids at or above n are skipped.
+// brought into [0, 2 pi).  Radial (Algorithm 2 in the coordinate that Theorem 1
+// needs, the one that is uniform under Eq. 1): x = cosh(alpha r) - 1, evaluated
+// as 2 sinh^2(alpha r / 2); y = x + tau_r, mirrored at top = cosh(alpha R) - 1 or
+// 0 while outside (tau_r changes sign each time); r = 2 asinh(sqrt(y / 2)) / alpha,
+// at most R.  (Algorithm 2 prints sinh(alpha r), which is not uniform under
+// Eq. 1, so a walk in it does not keep the density.)  Ids at or above n are
+// skipped.
 __global__ void move_kernel(const uint32_t *ids, uint64_t count, uint64_t n, double *phi, double *r,
                             const double *tau_phi, double *tau_r, double R, double alpha)
 {
-    const double top = dm::sinh(mul(alpha, R));
+    const double top = sub(dm::cosh(mul(alpha, R)), 1.0);
     const double inv_alpha = dm::div(1.0, alpha);
     for (uint64_t j = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; j < count;
          j += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
@@ -56,14 +61,15 @@ __global__ void move_kernel(const uint32_t *ids, uint64_t count, uint64_t n, dou
         if (p >= dm::kTwoPi) p = kBelowTwoPi;
         if (p < 0.0) p = 0.0;
         double tr = tau_r[i];
-        double y = add(dm::sinh(mul(alpha, r[i])), tr);
+        const double s = dm::sinh(mul(mul(alpha, r[i]), 0.5));
+        double y = add(mul(mul(s, s), 2.0), tr);
         for (int it = 0; it < 64 && (y > top || y < 0.0); ++it) {
             y = y > top ? sub(add(top, top), y) : -y;
             tr = -tr;
         }
         if (y > top) y = top;
         if (y < 0.0) y = 0.0;
-        double z = mul(dm::asinh(y), inv_alpha);
+        double z = mul(mul(dm::asinh(__dsqrt_rn(mul(y, 0.5))), 2.0), inv_alpha);
         if (z > R) z = R;
         phi[i] = p;
         r[i] = z;

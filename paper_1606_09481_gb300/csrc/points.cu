@@ -1,6 +1,6 @@
 // points.cu -- the point pipeline: disk radius R (Sec. III-B getTargetRadius),
 // band boundaries (Sec. III-A), Philox sampling of (phi, r) by inverse CDF
-// (Alg. 1 "draw phi" / "draw r", Eq. 1), band assignment (Alg. 1 "insert in b_i")
+// (Alg. 1 sampling step, Eq. 1), band assignment (Alg. 1 band insertion)
 // and the gather of the (band, angle)-sorted structure-of-arrays.
 #include "kernels.h"
 
@@ -176,6 +176,7 @@ __device__ void plan_block(Meta *M, const PlanArgs &a, int depth)
     M->m = 0;
     M->candidates = 0;
     M->near_threshold = 0;
+    M->rounding_band = 0;
     M->rechecks = 0;
     M->verify_failures = 0;
     M->heavy_n = 0;
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_batch_kernel(Meta *metas, c
     C->m = 0;
     C->candidates = 0;
     C->near_threshold = 0;
+    C->rounding_band = 0;
     C->rechecks = 0;
     C->verify_failures = 0;
     C->heavy_n = 0;

@@ -47,6 +47,28 @@ constexpr double kKeyPerRad = 683565275.57643158;
 constexpr float kWinE1 = 5e-6f;                  // window numerator error, relative to 1 + T
 constexpr float kNearMargin = 2e-12f;            // core pairs stay clear of |L/cosh R - 1| <= 1e-12
 
+// Diagnostics of a pair decided by the FP64 predicate (reported, never used to
+// decide): bit 0.. counts |L - cosh R| <= 1e-12 cosh R, bit 32.. counts
+// |L - cosh R| <= 8 u cosh r_v cosh r_w (the predicate's rounding band).  Every
+// pair inside the rounding band reaches the FP64 predicate: the filter and the
+// core decide only pairs farther than 32 u cosh r_v cosh r_w from the threshold.
+__device__ __forceinline__ uint64_t diag_count(double L, double coshR, double chv, double chw)
+{
+    const double dev = fabs(__dsub_rn(L, coshR));
+    return (dev <= 1e-12 * coshR ? 1ull : 0ull) + (dev <= 0x1p-50 * __dmul_rn(chv, chw) ? (1ull << 32) : 0ull);
+}
+
+// Adds a warp's diagnostic counts (lane sums in `near`) to the graph's counters.
+__device__ __forceinline__ void flush_diag(Meta *C, uint64_t near)
+{
+    for (int off = 16; off; off >>= 1) near += __shfl_down_sync(0xffffffffu, near, off);
+    if ((threadIdx.x & 31) == 0 && near) {
+        if (near & 0xffffffffull)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&C->near_threshold), near & 0xffffffffull);
+        if (near >> 32) atomicAdd(reinterpret_cast<unsigned long long *>(&C->rounding_band), near >> 32);
+    }
+}
+
 struct BandShared {
     uint32_t start[kMaxBands + 1];
     float P[kMaxBands + 1], Mm[kMaxBands + 1], S[kMaxBands + 1];     // inner radius c_i - dr
@@ -385,7 +407,7 @@ __device__ __noinline__ void verify_pair(const QueryArgs &a, const Meta *Mg, Met
 // compare every decided pair with the FP64 predicate.
 template <bool kFilter, bool kVerify>
 __device__ __forceinline__ int decide(const QueryArgs &a, const Meta *Mg, Meta *C, const WarpSmem &W, uint32_t o,
-                                      uint32_t q, bool in, double coshR, bool verify, uint32_t &near)
+                                      uint32_t q, bool in, double coshR, bool verify, uint64_t &near)
 {
     const unsigned full = 0xffffffffu;
     int dec = 0;
@@ -406,9 +428,10 @@ __device__ __forceinline__ int decide(const QueryArgs &a, const Meta *Mg, Meta *
         if (kVerify && verify && in && dec != 2) verify_pair(a, Mg, C, W.oid[o], a.P.id[q], dec, coshR);
     } else if (in) {
         const double2 v = W.od[o];
-        const double L = predicate_L(v.x, v.y, W.osh[o], a.P.phi[q], a.P.ch[q], a.P.sh[q]);
+        const double chw = a.P.ch[q];
+        const double L = predicate_L(v.x, v.y, W.osh[o], a.P.phi[q], chw, a.P.sh[q]);
         dec = L <= coshR;
-        near += fabs(L - coshR) <= 1e-12 * coshR;
+        near += diag_count(L, coshR, v.y, chw);
     }
     return dec;
 }
@@ -453,7 +476,7 @@ __device__ __forceinline__ void write_core_chunk(const QueryArgs &a, Meta *Mg, M
 // each lane then steps forward over the few entries its round crosses.
 template <bool kFilter, bool kCsr, bool kVerify>
 __device__ __forceinline__ void flush(const QueryArgs &a, Meta *Mg, Meta *C, uint64_t obase, uint64_t cap,
-                                      WarpSmem &W, int count, double coshR, bool verify, uint32_t &near)
+                                      WarpSmem &W, int count, double coshR, bool verify, uint64_t &near)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -581,7 +604,7 @@ __device__ __forceinline__ void test_fringe_chunk(const QueryArgs &a, Meta *Mg, 
 template <bool kFilter>
 __device__ __forceinline__ int decide_own(const QueryArgs &a, const Meta *Mg, Meta *C, float4 va, float4 vb,
                                           const OwnerRegs &v, double phv, uint32_t p, uint32_t idv, uint32_t q,
-                                          bool in, double coshR, bool verify, uint32_t &near)
+                                          bool in, double coshR, bool verify, uint64_t &near)
 {
     const unsigned full = 0xffffffffu;
     int dec = 0;
@@ -601,9 +624,10 @@ __device__ __forceinline__ int decide_own(const QueryArgs &a, const Meta *Mg, Me
         }
         if (verify && in && dec != 2) verify_pair(a, Mg, C, idv, a.P.id[q], dec, coshR);
     } else if (in) {
-        const double L = predicate_L(phv, v.ch, v.sh, a.P.phi[q], a.P.ch[q], a.P.sh[q]);
+        const double chw = a.P.ch[q];
+        const double L = predicate_L(phv, v.ch, v.sh, a.P.phi[q], chw, a.P.sh[q]);
         dec = L <= coshR;
-        near += fabs(L - coshR) <= 1e-12 * coshR;
+        near += diag_count(L, coshR, v.ch, chw);
     }
     return dec;
 }
@@ -642,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryA
     __shared__ uint8_t own_sm[kWarps][32];
     uint8_t *own = own_sm[threadIdx.x >> 5];
     unsigned long long cand = 0;
-    uint32_t near = 0;
+    uint64_t near = 0;
     // batches in sorted order from a shared counter: the costly inner-band batches
     // start first and the rest fill in around them
     for (;;) {
@@ -891,15 +915,9 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryA
             }
         }
     }
-    for (int off = 16; off; off >>= 1) {
-        cand += __shfl_down_sync(full, cand, off);
-        near += __shfl_down_sync(full, near, off);
-    }
-    if (lane == 0) {
-        if (cand) atomicAdd(reinterpret_cast<unsigned long long *>(&C->candidates), cand);
-        if (near) atomicAdd(reinterpret_cast<unsigned long long *>(&C->near_threshold),
-                            static_cast<unsigned long long>(near));
-    }
+    for (int off = 16; off; off >>= 1) cand += __shfl_down_sync(full, cand, off);
+    if (lane == 0 && cand) atomicAdd(reinterpret_cast<unsigned long long *>(&C->candidates), cand);
+    flush_diag(C, near);
 }
 
 // Heavy chunks: one warp per chunk of at most kChunk candidates of one owner,
@@ -914,7 +932,7 @@ __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmem &W = Wsm[warp];
     const uint32_t count = C->heavy_n < a.heavy_cap ? C->heavy_n : a.heavy_cap;
-    uint32_t near = 0;
+    uint64_t near = 0;
     for (;;) {
         uint32_t item = 0;
         if (lane == 0) item = atomicAdd(&C->heavy_next, 1u);
@@ -944,9 +962,7 @@ __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
         else flush<kFilter, kCsr, kVerify>(a, Mg, C, obase, cap, W, 1, coshR, verify, near);
         __syncwarp();
     }
-    for (int off = 16; off; off >>= 1) near += __shfl_down_sync(full, near, off);
-    if (lane == 0 && near)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&C->near_threshold), static_cast<unsigned long long>(near));
+    flush_diag(C, near);
 }
 
 // FP64 recheck of the pairs the filter left undecided: the predicate of Eq. 3 on
@@ -961,7 +977,7 @@ __global__ void __launch_bounds__(kThreads) recheck_kernel(QueryArgs a)
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t count = M->recheck_n < a.recheck_cap ? M->recheck_n : a.recheck_cap;
     const double coshR = M->coshR;
-    uint32_t near = 0;
+    uint64_t near = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; w0 < count; w0 += stride) {
         const uint32_t idx = w0 + lane;
@@ -976,7 +992,7 @@ __global__ void __launch_bounds__(kThreads) recheck_kernel(QueryArgs a)
             fp64_point(a, M, idw, pw, cw, sw);
             const double L = predicate_L(pv, cv, sv, pw, cw, sw);
             edge = L <= coshR;
-            near += fabs(L - coshR) <= 1e-12 * coshR;
+            near += diag_count(L, coshR, cv, cw);
         }
         const uint32_t word = __ballot_sync(full, edge);
         if (!word) continue;
@@ -985,9 +1001,7 @@ __global__ void __launch_bounds__(kThreads) recheck_kernel(QueryArgs a)
         base = __shfl_sync(full, base, 0);
         if (edge && base + __popc(word) <= a.capacity) write_edge<kCsr>(a, base + __popc(word & lt), idv, idw);
     }
-    for (int off = 16; off; off >>= 1) near += __shfl_down_sync(full, near, off);
-    if (lane == 0 && near)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&M->near_threshold), static_cast<unsigned long long>(near));
+    flush_diag(M, near);
     if (blockIdx.x == 0 && threadIdx.x == 0) M->rechecks = count;
 }
 
@@ -998,7 +1012,7 @@ __global__ void __launch_bounds__(kThreads) recheck_batch_kernel(QueryArgs a)
     Meta *C = a.M + a.bt.G;
     if (C->error) return;
     const uint32_t count = C->recheck_n < a.recheck_cap ? C->recheck_n : a.recheck_cap;
-    uint32_t near = 0;
+    uint64_t near = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += stride) {
         const uint2 pq = a.recheck[idx];
@@ -1015,16 +1029,14 @@ __global__ void __launch_bounds__(kThreads) recheck_batch_kernel(QueryArgs a)
         fp64_point(a, Mg, idw, pw, cw, sw);
         const double coshR = Mg->coshR;
         const double L = predicate_L(pv, cv, sv, pw, cw, sw);
-        near += fabs(L - coshR) <= 1e-12 * coshR;
+        near += diag_count(L, coshR, cv, cw);
         if (L <= coshR) {
             const unsigned long long at = atomicAdd(reinterpret_cast<unsigned long long *>(&Mg->m), 1ull);
             const uint64_t obase = a.bt.out_off[lo];
             if (at < a.bt.out_off[lo + 1] - obase) write_edge<false>(a, obase + at, idv, idw);
         }
     }
-    for (int off = 16; off; off >>= 1) near += __shfl_down_sync(0xffffffffu, near, off);
-    if ((threadIdx.x & 31) == 0 && near)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&C->near_threshold), static_cast<unsigned long long>(near));
+    flush_diag(C, near);
     if (blockIdx.x == 0 && threadIdx.x == 0) C->rechecks = count;
 }
 

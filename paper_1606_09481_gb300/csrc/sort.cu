@@ -1,6 +1,6 @@
 // sort.cu -- stable LSD radix sort of 64-bit keys with optional uint32 payload
-// (Alg. 1 "sort points in b by their angular coordinates": one global sort keyed
-// by (band, angle key) orders every band at once).
+// (Alg. 1, angular sort within each band: one global sort keyed by (band, angle
+// key) orders every band at once).
 //
 // One pass per 8-bit digit:
 //   upsweep   each CTA histograms the digit over its contiguous chunk;

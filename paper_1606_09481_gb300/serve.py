@@ -8,8 +8,17 @@ generations of different requests overlap on the device (the library calls
 release the interpreter lock while they wait for their stream).  A worker that
 takes a small request also takes the small requests queued directly behind it,
 as long as they fit, and generates them together with one rhg_generate_batch
-call.  Admission is first come, first served: a request that does not fit
-waits for memory, and the requests behind it wait too.
+call; it looks for them among the first `lookahead` queued requests, so a large
+request in between does not stop the grouping (the large one is still admitted
+in its turn).  Admission is first come, first served: a request that does not
+fit waits for memory, and the requests behind it wait too.
+
+The budget is a bound on what admitted work holds: the executor never
+allocates more than the estimate it was admitted with.  When a graph has more
+edges than its estimate has room for, the executor gives the request back with
+its exact edge count (Retry); the server releases the reservation and puts the
+request back at the head of the queue with that count, so that its next
+admission reserves exactly what it needs.
 
 The scheduling is independent of the GPU: the executor (estimate, single,
 batch) can be replaced, which the host tests do.
@@ -30,6 +39,15 @@ class Request:
     alpha: float
     seed: int
     arrival: float = 0.0  # seconds on the server's clock (time.perf_counter)
+    m_hint: int = 0       # exact edge count, known after an attempt that ran out of room
+    attempts: int = 0
+
+
+@dataclass
+class Retry:
+    """An executor's answer for a request whose graph had more edges (m) than the
+    room its estimate reserved."""
+    m: int
 
 
 @dataclass
@@ -50,29 +68,53 @@ class Completion:
 
 class GpuExecutor:
     """Runs requests with the library: one graph with rhg_generate_pairs, a group
-    of small graphs with rhg_generate_batch."""
+    of small graphs with rhg_generate_batch.  Device memory never exceeds the
+    estimate: the workspace and a pair buffer of capacity() pairs."""
 
     def __init__(self, keep_results: bool = False):
-        from . import (batch_params, batch_workspace_bytes, estimate_capacity, generate_batch, generate_pairs,
-                       make_params, workspace_bytes)
+        from . import (OVERFLOW, RhgError, allocate_batch, allocate_pairs, batch_params, batch_workspace_bytes,
+                       estimate_capacity, generate_pairs, make_params, run_batch, workspace_bytes)
         self._bp, self._bwb, self._est = batch_params, batch_workspace_bytes, estimate_capacity
-        self._gb, self._gp, self._mp, self._wb = generate_batch, generate_pairs, make_params, workspace_bytes
+        self._gp, self._mp, self._wb = generate_pairs, make_params, workspace_bytes
+        self._ap, self._ab, self._rb = allocate_pairs, allocate_batch, run_batch
+        self._err, self._overflow = RhgError, OVERFLOW
         self.keep = keep_results
 
+    def capacity(self, r: Request) -> int:
+        return max(self._est(r.n, r.k), int(r.m_hint))
+
     def estimate(self, r: Request) -> int:
-        return int(self._wb(self._mp(r.n, r.k, r.alpha, r.seed), 0)) + 8 * self._est(r.n, r.k)
+        return int(self._wb(self._mp(r.n, r.k, r.alpha, r.seed), 0)) + 8 * self.capacity(r)
 
     def estimate_batch(self, rs) -> int:
         return int(self._bwb(self._bp([(r.n, r.k, r.alpha, r.seed) for r in rs]))) + \
-            8 * sum(self._est(r.n, r.k) for r in rs)
+            8 * sum(self.capacity(r) for r in rs)
 
     def single(self, r: Request, stream):
-        pairs, res = self._gp(r.n, r.k, r.alpha, r.seed, stream=stream)
+        wsp = self._ap(self._mp(r.n, r.k, r.alpha, r.seed), self.capacity(r))
+        try:
+            pairs, res = self._gp(r.n, r.k, r.alpha, r.seed, workspace=wsp, stream=stream, overflow_retry=False)
+        except self._err as e:
+            if e.status == self._overflow and e.result is not None:
+                return [Retry(int(e.result.m))]
+            raise
         return [(int(res.m), float(res.R), pairs if self.keep else None)]
 
     def batch(self, rs, stream):
-        views, results, _ = self._gb([(r.n, r.k, r.alpha, r.seed) for r in rs], stream=stream)
-        return [(int(res.m), float(res.R), v if self.keep else None) for v, res in zip(views, results)]
+        params = self._bp([(r.n, r.k, r.alpha, r.seed) for r in rs])
+        buf = self._ab(params, [self.capacity(r) for r in rs])
+        rc, res, tot = self._rb(buf, stream)
+        out = []
+        for g, r in enumerate(rs):
+            st = res[g].status
+            if st == self._overflow:
+                out.append(Retry(int(res[g].m)))
+            elif st != 0:
+                raise self._err(st, "rhg_generate_batch", tot)
+            else:
+                view = buf.out[2 * buf.offsets[g]: 2 * (buf.offsets[g] + res[g].m)].view(-1, 2)
+                out.append((int(res[g].m), float(res[g].R), view if self.keep else None))
+        return out
 
 
 @dataclass
@@ -87,11 +129,14 @@ class Server:
     n <= small_n are grouped, up to batch_points points per group."""
 
     def __init__(self, executor=None, budget_bytes: int = 120 * 10**9, workers: int = 4, small_n: int = 100_000,
-                 batch_points: int = 4_000_000, batch_max: int = 256, use_cuda_streams: bool = True):
+                 batch_points: int = 4_000_000, batch_max: int = 256, use_cuda_streams: bool = True,
+                 lookahead: int = 1024):
         self.ex = executor if executor is not None else GpuExecutor()
         self.budget = int(budget_bytes)
         self.free = int(budget_bytes)
         self.small_n, self.batch_points, self.batch_max = small_n, batch_points, batch_max
+        self.lookahead = lookahead
+        self.retries = 0
         self.queue = deque()
         self.cv = threading.Condition()
         self.done: list[Completion] = []
@@ -125,31 +170,34 @@ class Server:
 
     # ------------------------------------------------------------- scheduling
     def _take(self):
-        """Admits the head of the queue (and small followers) if it fits; else None."""
+        """Admits the head of the queue (and small requests queued behind it) if it
+        fits; else None."""
         head = self.queue[0]
         need = self.ex.estimate(head)
         if need > self.free:
             return None
-        reqs = [head]
+        picked = [0]
         if head.n <= self.small_n:
             pts = head.n
-            i = 1
-            while i < len(self.queue) and len(reqs) < self.batch_max:
-                r = self.queue[i]
-                if r.n > self.small_n or pts + r.n > self.batch_points:
+            for i in range(1, min(len(self.queue), self.lookahead)):
+                if len(picked) >= self.batch_max or pts >= self.batch_points:
                     break
-                reqs.append(r)
-                pts += r.n
-                i += 1
-            if len(reqs) > 1:
+                r = self.queue[i]
+                if r.n <= self.small_n and pts + r.n <= self.batch_points:
+                    picked.append(i)
+                    pts += r.n
+            if len(picked) > 1:
+                reqs = [self.queue[i] for i in picked]
                 need = self.ex.estimate_batch(reqs)
-                while need > self.free and len(reqs) > 1:
-                    reqs.pop()
-                    need = self.ex.estimate_batch(reqs) if len(reqs) > 1 else self.ex.estimate(head)
+                while need > self.free and len(picked) > 1:
+                    picked.pop()
+                    reqs = [self.queue[i] for i in picked]
+                    need = self.ex.estimate_batch(reqs) if len(picked) > 1 else self.ex.estimate(head)
                 if need > self.free:
                     return None
-        for _ in reqs:
-            self.queue.popleft()
+        reqs = [self.queue[i] for i in picked]
+        for i in reversed(picked):
+            del self.queue[i]
         self.free -= need
         self.peak_reserved = max(self.peak_reserved, self.budget - self.free)
         self.admitted.append([r.rid for r in reqs])
@@ -187,8 +235,21 @@ class Server:
                 continue
             end = time.perf_counter()
             with self.cv:
-                for r, (m, R, pairs) in zip(work.reqs, out):
+                again = []
+                for r, res in zip(work.reqs, out):
+                    if isinstance(res, Retry):  # ran out of room: back to the head with its exact size
+                        r.m_hint = max(int(res.m), r.m_hint + 1)
+                        r.attempts += 1
+                        again.append(r)
+                        continue
+                    m, R, pairs = res
                     self.done.append(Completion(r.rid, m, R, r.arrival, start, end, len(work.reqs), pairs))
+                for r in reversed(again):
+                    if self.ex.estimate(r) > self.budget:  # its exact size can never be admitted
+                        self.errors.append(ValueError(f"request {r.rid} needs more than the budget {self.budget}"))
+                        continue
+                    self.queue.appendleft(r)
+                self.retries += len(again)
                 self.free += work.reserve
                 self.cv.notify_all()
 

@@ -39,12 +39,12 @@ def test_status_strings_and_version(rhg):
     assert rhg.status_str(0) == "RHG_OK"
     assert rhg.status_str(6) == "RHG_ERR_OVERFLOW"
     assert rhg.status_str(99) == "RHG_ERR_UNKNOWN"
-    assert rhg.load().rhg_version() == 1
+    assert rhg.load().rhg_version() == 2
 
 
 def test_params_layout_matches_header(rhg):
     assert ctypes.sizeof(rhg.Params) == 56
-    assert ctypes.sizeof(rhg.Result) == 64
+    assert ctypes.sizeof(rhg.Result) == 72
 
 
 def _ws_status(rhg, **kw):

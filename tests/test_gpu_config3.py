@@ -1,7 +1,10 @@
 """Paper-scale graph (n = 10^7, k = 200, alpha = 1, seed 3; ~1G edges), in the
-launch configuration bench.py times: exact edge count against the oracle's
-Alg. 1 (OpenMP over all vertices), brute-force neighbourhoods of sampled
-vertices (including the innermost hubs) and the global invariants."""
+launch configuration bench.py times, compared with the oracle pair by pair: the
+device pairs are sorted on the device by (u, v) and compared element by element
+with the oracle's ordered edge list (every edge (u, w), u < w, of a vertex range
+from a windowed search of all bands), one vertex range at a time, over all
+~10^9 pairs.  Also the exact edge count and rounding diagnostics of the oracle's
+Alg. 1 and the global invariants."""
 import numpy as np
 import pytest
 
@@ -10,6 +13,7 @@ from gpu_util import require_gpu
 pytestmark = pytest.mark.gpu
 
 N, K, ALPHA, SEED = 10**7, 200, 1.0, 3
+RANGE = 1 << 19  # vertices per compared range (~5e7 pairs)
 
 
 @pytest.fixture(scope="module")
@@ -44,28 +48,40 @@ def test_invariants(gpu_graph):
     torch.cuda.empty_cache()
 
 
-def test_edge_count_equals_oracle(O, gpu_graph, oracle_points):
+def test_edge_count_and_diagnostics_equal_oracle(O, gpu_graph, oracle_points):
     pairs, res = gpu_graph
     R, phi, r = oracle_points
     assert res.R == R
-    m_ref, _ = O.band_count_subset(phi, r, R, O.default_bands(N), 0.9, np.arange(N, dtype=np.uint32))
+    m_ref, _, st = O.band_count_subset(phi, r, R, O.default_bands(N), 0.9, np.arange(N, dtype=np.uint32),
+                                       with_stats=True)
     assert res.m == m_ref
+    assert res.rounding_band == st["rounding_band"]
+    assert res.near_threshold == st["near_threshold"]
 
 
-def test_sampled_neighbourhoods(O, gpu_graph, oracle_points):
+def test_every_pair_equals_oracle(O, gpu_graph, oracle_points):
+    """All ~10^9 pairs, element by element, in ranges of 2^19 vertices."""
     import torch
     pairs, res = gpu_graph
     R, phi, r = oracle_points
-    rng = np.random.default_rng(1)
-    sample = np.unique(np.concatenate([rng.integers(0, N, 24), np.argsort(r)[:8], np.argsort(-r)[:4]]))
-    s = torch.from_numpy(sample.astype(np.int64)).cuda()
-    u = pairs[:, 0].to(torch.int64) & 0xFFFFFFFF
-    v = pairs[:, 1].to(torch.int64) & 0xFFFFFFFF
-    hit_u = torch.isin(u, s)
-    hit_v = torch.isin(v, s)
-    a = torch.cat([torch.stack([u[hit_u], v[hit_u]], 1), torch.stack([v[hit_v], u[hit_v]], 1)]).cpu().numpy()
-    del u, v, hit_u, hit_v
-    for vid in sample:
-        got = np.sort(a[a[:, 0] == vid, 1])
-        ref = O.neighbors(int(vid), phi, r, R).astype(np.int64)
-        assert np.array_equal(got, ref), (vid, len(got), len(ref))
+    key = ((pairs[:, 0].to(torch.int64) & 0xFFFFFFFF) << 32) | (pairs[:, 1].to(torch.int64) & 0xFFFFFFFF)
+    key, _ = torch.sort(key)
+    bounds = torch.arange(0, N + RANGE, RANGE, dtype=torch.int64, device=key.device).clamp(max=N) << 32
+    at = torch.searchsorted(key, bounds).cpu().numpy()
+    prep = O.Prepared(phi, r, R, O.default_bands(N), 0.9)
+    compared = 0
+    try:
+        for j, u0 in enumerate(range(0, N, RANGE)):
+            u1 = min(u0 + RANGE, N)
+            got = key[at[j]:at[j + 1]].cpu().numpy()
+            ref = prep.upper_pairs(u0, u1, capacity=int(len(got) * 1.1) + 4096)
+            ref_key = (ref[:, 0].astype(np.int64) << 32) | ref[:, 1].astype(np.int64)
+            assert len(got) == len(ref_key), (u0, len(got), len(ref_key))
+            bad = np.flatnonzero(got != ref_key)
+            assert len(bad) == 0, (u0, [(int(got[b] >> 32), int(got[b] & 0xFFFFFFFF)) for b in bad[:4]])
+            compared += len(got)
+    finally:
+        prep.close()
+        del key
+        torch.cuda.empty_cache()
+    assert compared == res.m

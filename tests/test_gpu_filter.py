@@ -58,3 +58,17 @@ def test_seam_pairs_verified(O):
                                        flags=rhg.FLAG_VERIFY)
     assert res.mode == 1 and res.verify_failures == 0
     assert np.array_equal(sorted_pairs(pairs), O.brute_edges(phi, r, R))
+
+
+@pytest.mark.parametrize("n,k,alpha,seed", [(5 * 10**6, 8, 0.6, 21), (2 * 10**6, 4, 0.55, 22)])
+def test_solved_R_above_filter_range_runs_fp64_mode(O, n, k, alpha, seed):
+    """Graphs whose R solved from Eq. 22 is above 32 run in FP64 mode; the host
+    sizes their chunk list for it (no RHG_ERR_OOM) and the edge count is the
+    oracle's Alg. 1 count."""
+    rhg = require_gpu()
+    _, res = rhg.generate_pairs(n, k, alpha, seed)
+    R = O.target_radius(n, k, alpha)
+    assert R > 32 and res.R == R and res.mode == 0
+    phi, r = O.sample_points(n, alpha, R, seed)
+    m, _ = O.band_count_subset(phi, r, R, O.default_bands(n), 0.9, np.arange(n, dtype=np.uint32))
+    assert res.m == m
