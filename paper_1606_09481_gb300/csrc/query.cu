@@ -364,12 +364,15 @@ __device__ __forceinline__ void push_heavy(const QueryArgs &a, Meta *C, uint32_t
 template <bool kCsr>
 __device__ __forceinline__ void write_edge(const QueryArgs &a, uint64_t pos, uint32_t i1, uint32_t i2)
 {
+    // streaming stores (evict first): the output is written once and must not
+    // push the point arrays out of L2
     const uint32_t u = i1 < i2 ? i1 : i2, v = i1 < i2 ? i2 : i1;
     if (kCsr) {
-        a.csr_keys[2 * pos] = (static_cast<uint64_t>(u) << 32) | v;
-        a.csr_keys[2 * pos + 1] = (static_cast<uint64_t>(v) << 32) | u;
+        __stcs(reinterpret_cast<ulonglong2 *>(a.csr_keys) + pos,
+               make_ulonglong2((static_cast<unsigned long long>(u) << 32) | v,
+                               (static_cast<unsigned long long>(v) << 32) | u));
     } else {
-        reinterpret_cast<uint2 *>(a.pairs)[pos] = make_uint2(u, v);
+        __stcs(reinterpret_cast<uint2 *>(a.pairs) + pos, make_uint2(u, v));
     }
 }
 
@@ -599,17 +602,67 @@ __device__ __forceinline__ void test_fringe_chunk(const QueryArgs &a, Meta *Mg, 
     }
 }
 
-// Test one candidate of the lane's own point (owner values in registers):
-// 1 = edge, 0 = no edge, 2 = undecided (queued for the FP64 recheck).
+// Per-warp shared state of the batch kernel.  For each band the 32 lanes' candidate
+// pieces are laid end to end as two streams: the fringe stream (every lane's
+// tested pieces, lane after lane) and the core stream (every lane's certain
+// range, lane after lane).  own[] tabulates the owner lane of kOwn consecutive
+// stream elements, one byte each, so that a lane finds the owner of any element
+// with one shared-memory load; the owners' values are read from fr / cr / oa / ob
+// (or od / osh in FP64 mode).
+constexpr uint32_t kOwn = 1024;       // stream elements whose owners are tabulated at once
+constexpr int kMaxFringe = 64;        // fringe candidates a lane keeps (two pieces of at most 32)
+
 template <bool kFilter>
-__device__ __forceinline__ int decide_own(const QueryArgs &a, const Meta *Mg, Meta *C, float4 va, float4 vb,
-                                          const OwnerRegs &v, double phv, uint32_t p, uint32_t idv, uint32_t q,
-                                          bool in, double coshR, bool verify, uint64_t &near)
+struct BatchSmem {
+    uint32_t own[kOwn / 4];                  // owner lane of stream element j0 + e: byte e
+    uint32_t bits[32 * kMaxFringe / 32];     // fringe decisions, bit j of word j / 32
+    uint4 fr[32];                            // lane's fringe: stream start, f0, length of [f0, f1), f2
+    uint2 cr[32];                            // lane's core: c0 - stream start, vertex id
+    float4 oa[kFilter ? 32 : 1], ob[kFilter ? 32 : 1];  // filter values (as load_owner stores them)
+    double2 od[kFilter ? 1 : 32];            // FP64 mode: phi, cosh r
+    double osh[kFilter ? 1 : 32];            // FP64 mode: sinh r
+};
+
+// own bytes of the stream elements [j0, j0 + kOwn) inside [s, s + len) := lane.
+__device__ __forceinline__ void fill_owner(uint32_t *own, uint32_t j0, uint32_t s, uint32_t len, uint32_t lane)
+{
+    const uint32_t e = s + len;
+    uint32_t a = s > j0 ? s - j0 : 0u;
+    uint32_t b = e > j0 ? e - j0 : 0u;
+    if (b > kOwn) b = kOwn;
+    uint8_t *o = reinterpret_cast<uint8_t *>(own);
+    const uint32_t rep = lane * 0x01010101u;
+    while (a < b && (a & 3u)) o[a++] = static_cast<uint8_t>(lane);
+    while (a + 4 <= b) {
+        own[a >> 2] = rep;
+        a += 4;
+    }
+    while (a < b) o[a++] = static_cast<uint8_t>(lane);
+}
+
+__device__ __forceinline__ uint32_t owner_of(const uint32_t *own, uint32_t e)
+{
+    return reinterpret_cast<const uint8_t *>(own)[e];
+}
+
+// Sorted position of fringe stream element j (owner values r = fr[owner]).
+__device__ __forceinline__ uint32_t fringe_pos(uint4 r, uint32_t j)
+{
+    const uint32_t t = j - r.x;
+    return t < r.z ? r.y + t : r.w + (t - r.z);
+}
+
+// Decide fringe stream element j (owner lane L at sorted position p, candidate q):
+// 1 = edge, 0 = no edge, 2 = undecided (queued for the FP64 recheck).
+template <bool kFilter, bool kVerify>
+__device__ __forceinline__ int decide_stream(const QueryArgs &a, const Meta *Mg, Meta *C, const BatchSmem<kFilter> &W,
+                                             uint32_t L, uint32_t p, uint32_t q, bool in, double coshR, bool verify,
+                                             uint64_t &near)
 {
     const unsigned full = 0xffffffffu;
     int dec = 0;
     if (kFilter) {
-        if (in) dec = filter_decide(va, vb, a.P.ang[q], a.P.pms[q]);
+        if (in) dec = filter_decide(W.oa[L], W.ob[L], a.P.ang[q], a.P.pms[q]);
         const uint32_t um = __ballot_sync(full, dec == 2);
         if (um) {
             const int lane = threadIdx.x & 31;
@@ -622,19 +675,23 @@ __device__ __forceinline__ int decide_own(const QueryArgs &a, const Meta *Mg, Me
                 else atomicMax(&C->error, kErrListFull);
             }
         }
-        if (verify && in && dec != 2) verify_pair(a, Mg, C, idv, a.P.id[q], dec, coshR);
+        if (kVerify && verify && in && dec != 2) verify_pair(a, Mg, C, W.cr[L].y, a.P.id[q], dec, coshR);
     } else if (in) {
+        const double2 v = W.od[L];
         const double chw = a.P.ch[q];
-        const double L = predicate_L(phv, v.ch, v.sh, a.P.phi[q], chw, a.P.sh[q]);
-        dec = L <= coshR;
-        near += diag_count(L, coshR, v.ch, chw);
+        const double Lv = predicate_L(v.x, v.y, W.osh[L], a.P.phi[q], chw, a.P.sh[q]);
+        dec = Lv <= coshR;
+        near += diag_count(Lv, coshR, v.y, chw);
     }
     return dec;
 }
 
-// One warp per batch of 32 consecutive sorted points, lane = point; for each band
-// every lane tests its own few fringe candidates (decision bits in a register),
-// then one warp-wide reservation places each lane's core and fringe edges.
+// One warp per batch of 32 consecutive sorted points, lane = point.  For each band
+// every lane computes its window and core (Sec. III-B) and the candidate pieces;
+// the warp decides the fringe stream 32 candidates at a time (all lanes busy
+// whatever the split between the lanes), reserves the band's edges with one
+// atomic add, and writes the core stream and the fringe edges as contiguous,
+// coalesced blocks.
 // kMulti (a batch of graphs): batches are 32-point slices of the tiles, each warp
 // keeps the band table of its current graph in its own shared memory, and edges
 // go to the graph's output region and counter; lists and work counters live in
@@ -643,8 +700,11 @@ template <bool kFilter, bool kCsr, bool kMulti, bool kVerify>
 __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryArgs a)
 {
     __shared__ BandShared Sm[kMulti ? kWarps : 1];
+    __shared__ BatchSmem<kFilter> Wsm[kWarps];
     const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
     BandShared &S = Sm[kMulti ? (threadIdx.x >> 5) : 0];
+    BatchSmem<kFilter> &W = Wsm[threadIdx.x >> 5];
     Meta *C = kMulti ? a.M + a.bt.G : a.M;  // counters and lists
     Meta *M = a.M;                          // the current graph
     if (!kMulti) {
@@ -663,8 +723,6 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryA
     uint32_t cur_g = 0xffffffffu;
     bool skip = false;
     const uint32_t nbatch = kMulti ? a.bt.num_tiles * (kTilePoints / 32) : (n + 31) / 32;
-    __shared__ uint8_t own_sm[kWarps][32];
-    uint8_t *own = own_sm[threadIdx.x >> 5];
     unsigned long long cand = 0;
     uint64_t near = 0;
     // batches in sorted order from a shared counter: the costly inner-band batches
@@ -703,9 +761,8 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryA
         const uint32_t p = p0 + lane;
         const bool valid = static_cast<uint32_t>(lane) < cnt;
         OwnerRegs mine{};
-        float4 va = make_float4(0, 0, 0, 0), vb = va;
-        double phv = 0.0;
         uint32_t bv = B, akv = 0, idv = 0;
+        __syncwarp();  // the previous batch's readers of W are done
         if (valid) {
             idv = a.P.id[p];
             bv = static_cast<uint32_t>(a.P.key[p] >> 32);
@@ -718,13 +775,14 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryA
                 mine.S2 = 2.0f * q.z;
                 mine.PM = q.x + q.y;
                 mine.gam = q.w;
-                va = make_float4(an.x, an.y, q.x, q.y);
-                vb = make_float4(mine.S2, mine.PM, kCBase + q.w, 0.0f);
+                W.oa[kFilter ? lane : 0] = make_float4(an.x, an.y, q.x, q.y);
+                W.ob[kFilter ? lane : 0] = make_float4(mine.S2, mine.PM, kCBase + q.w, 0.0f);
             } else {
-                phv = a.P.phi[p];
                 mine.r = a.P.r[p];
                 mine.ch = a.P.ch[p];
                 mine.sh = a.P.sh[p];
+                W.od[kFilter ? 0 : lane] = make_double2(a.P.phi[p], mine.ch);
+                W.osh[kFilter ? 0 : lane] = mine.sh;
             }
         }
         const uint32_t bmin = __reduce_min_sync(full, bv);
@@ -769,7 +827,7 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryA
                 if (f3 < f2) f3 = f2;
                 if (c1 < c0) c1 = c0;
                 cand += (f1 - f0) + (f3 - f2) + (c1 - c0);
-                // a lane tests at most 32 + 32 fringe candidates itself; a batch keeps
+                // a lane keeps at most 32 + 32 fringe candidates; a batch keeps
                 // about kBatchBudget candidates; longer ranges become chunks that
                 // every warp shares
                 const uint32_t room = kept < kBatchBudget ? (kBatchBudget - kept) / 32 : 0;
@@ -789,129 +847,101 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryA
                 }
             }
             const uint32_t nl = f1 - f0, nf = nl + (f3 - f2), nc = c1 - c0;
-            // fringe tests, one candidate per lane per step
-            uint64_t mask = 0;
-            const uint32_t maxf = __reduce_max_sync(full, nf);
-            if (kFilter) {
-                // the next candidate's values are loaded while the current one is tested
-                float2 aw = make_float2(0.0f, 0.0f);
-                float4 pw = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (nf) {
-                    const uint32_t q = nl ? f0 : f2;
-                    aw = a.P.ang[q];
-                    pw = a.P.pms[q];
-                }
-                for (uint32_t t = 0; t < maxf; ++t) {
-                    const bool in = t < nf;
-                    const uint32_t q = t < nl ? f0 + t : f2 + (t - nl);
-                    const float2 ac = aw;
-                    const float4 pc = pw;
-                    if (t + 1 < nf) {
-                        const uint32_t qn = t + 1 < nl ? f0 + t + 1 : f2 + (t + 1 - nl);
-                        aw = a.P.ang[qn];
-                        pw = a.P.pms[qn];
-                    }
-                    const int dec = in ? filter_decide(va, vb, ac, pc) : 0;
-                    const uint32_t um = __ballot_sync(full, dec == 2);
-                    if (um) {
-                        uint32_t rb = 0;
-                        if (lane == 0) rb = atomicAdd(&C->recheck_n, static_cast<uint32_t>(__popc(um)));
-                        rb = __shfl_sync(full, rb, 0);
-                        if (dec == 2) {
-                            const uint32_t at = rb + __popc(um & ((1u << lane) - 1u));
-                            if (at < a.recheck_cap) a.recheck[at] = make_uint2(p, q);
-                            else atomicMax(&C->error, kErrListFull);
-                        }
-                    }
-                    if (kVerify && verify && in && dec != 2) verify_pair(a, M, C, idv, a.P.id[q], dec, coshR);
-                    if (dec == 1) mask |= 1ull << t;
-                }
-            } else {
-                for (uint32_t t = 0; t < maxf; ++t) {
-                    const bool in = t < nf;
-                    const uint32_t q = t < nl ? f0 + t : f2 + (t - nl);
-                    const int dec = decide_own<kFilter>(a, M, C, va, vb, mine, phv, p, idv, q, in, coshR,
-                                                        kVerify && verify, near);
-                    if (dec == 1) mask |= 1ull << t;
-                }
-            }
-            // one reservation for the warp's edges of this band: [base, base + T)
-            // holds the core edges of lanes 0..31 in lane order, then come the
-            // fringe edges
-            const uint32_t nfe = static_cast<uint32_t>(__popcll(mask));
-            uint32_t ci = nc, fi = nfe;  // inclusive scans over the lanes
+            uint32_t fi = nf, ci = nc;  // inclusive scans over the lanes
             for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t y = __shfl_up_sync(full, ci, off), z = __shfl_up_sync(full, fi, off);
+                const uint32_t y = __shfl_up_sync(full, fi, off), z = __shfl_up_sync(full, ci, off);
                 if (lane >= off) {
-                    ci += y;
-                    fi += z;
+                    fi += y;
+                    ci += z;
                 }
             }
-            const uint32_t T = __shfl_sync(full, ci, 31);
-            const uint32_t total = T + __shfl_sync(full, fi, 31);
+            const uint32_t F = __shfl_sync(full, fi, 31), T = __shfl_sync(full, ci, 31);
+            if (F + T == 0) continue;
+            const uint32_t fs = fi - nf, cs = ci - nc;  // the lane's stream starts
+            __syncwarp();  // the previous band's readers of W are done
+            W.fr[lane] = make_uint4(fs, f0, nl, f2);
+            W.cr[lane] = make_uint2(c0 - cs, idv);
+            // 1. the fringe stream, 32 candidates per step: one decision bit each
+            uint32_t nfe = 0;
+            for (uint32_t j0 = 0; j0 < F; j0 += kOwn) {
+                fill_owner(W.own, j0, fs, nf, lane);
+                __syncwarp();
+                const uint32_t jend = F - j0 > kOwn ? j0 + kOwn : F;
+                for (uint32_t jw = j0; jw < jend; jw += 32) {
+                    const uint32_t j = jw + lane;
+                    const bool in = j < jend;
+                    uint32_t L = 0, q = 0;
+                    if (in) {
+                        L = owner_of(W.own, j - j0);
+                        q = fringe_pos(W.fr[L], j);
+                    }
+                    const int dec = decide_stream<kFilter, kVerify>(a, M, C, W, L, p0 + L, q, in, coshR, verify, near);
+                    const uint32_t word = __ballot_sync(full, dec == 1);
+                    if (lane == 0) W.bits[jw >> 5] = word;
+                    nfe += __popc(word);
+                }
+                __syncwarp();
+            }
+            // one reservation for the band's edges: [base, base + T) holds the core
+            // stream, then come the fringe edges in stream order
+            const uint32_t total = T + nfe;
             kept += total;
-            if (total == 0) continue;
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(&M->m), total);
             base = __shfl_sync(full, base, 0);
             if (base + total > cap) continue;
             base += obase;
-            // core edges: element j of the concatenation goes to base + j (coalesced);
-            // its owner is the lane whose segment starts last at or before j: the
-            // segment starts inside each 32-element window are one OR-reduction and
-            // a table of which lane starts where
-            // Owners of kCoreGroup windows are found first, then their id loads
-            // are issued together, so that one memory latency covers the group.
-            const uint32_t start = ci - nc, delta = c0 - start;  // source position = j + delta
-            uint32_t L = 0;
-            for (uint32_t j0 = 0; j0 < T; j0 += 32 * kCoreGroup) {
-                uint32_t dl[kCoreGroup], u[kCoreGroup], w[kCoreGroup];
-#pragma unroll
-                for (int g = 0; g < kCoreGroup; ++g) {
-                    const uint32_t jw = j0 + 32 * g;
-                    dl[g] = 0;
-                    u[g] = 0;
-                    if (jw < T) {  // warp-uniform
-                        const bool starts = nc != 0 && start >= jw && start - jw < 32;
-                        if (starts) own[start - jw] = static_cast<uint8_t>(lane);
-                        const uint32_t bits = __reduce_or_sync(full, starts ? 1u << (start - jw) : 0u);
+            // 2. the fringe edges (the owner table still holds the last fringe chunk)
+            if (nfe) {
+                uint64_t pos = base + T;
+                for (uint32_t j0 = 0; j0 < F; j0 += kOwn) {
+                    if (F > kOwn) {
                         __syncwarp();
-                        const uint32_t upto = bits & (0xffffffffu >> (31 - lane));  // starts at offsets <= lane
-                        if (upto) L = own[31 - __clz(upto)];
-                        dl[g] = __shfl_sync(full, delta, L);
-                        u[g] = __shfl_sync(full, idv, L);
-                        L = __shfl_sync(full, L, 31);  // owner of the window's last element
+                        fill_owner(W.own, j0, fs, nf, lane);
                         __syncwarp();
                     }
-                }
-#pragma unroll
-                for (int g = 0; g < kCoreGroup; ++g) {
-                    const uint32_t j = j0 + 32 * g + lane;
-                    w[g] = j < T ? __ldg(a.P.id + (j + dl[g])) : 0u;
-                }
-#pragma unroll
-                for (int g = 0; g < kCoreGroup; ++g) {
-                    const uint32_t j = j0 + 32 * g + lane;
-                    if (j < T) {
-                        write_edge<kCsr>(a, base + j, u[g], w[g]);
-                        if (kVerify && verify) verify_pair(a, M, C, u[g], w[g], 1, coshR);
+                    const uint32_t jend = F - j0 > kOwn ? j0 + kOwn : F;
+                    for (uint32_t jw = j0; jw < jend; jw += 32) {
+                        const uint32_t word = W.bits[jw >> 5];
+                        if ((word >> lane) & 1u) {
+                            const uint32_t j = jw + lane;
+                            const uint32_t L = owner_of(W.own, j - j0);
+                            const uint32_t q = fringe_pos(W.fr[L], j);
+                            write_edge<kCsr>(a, pos + __popc(word & lt), W.cr[L].y, __ldg(a.P.id + q));
+                        }
+                        pos += __popc(word);
                     }
                 }
             }
-            // fringe edges, two per step with both id loads in flight
-            uint64_t pos = base + T + (fi - nfe);
-            while (mask) {
-                const uint32_t t0 = static_cast<uint32_t>(__ffsll(static_cast<long long>(mask)) - 1);
-                mask &= mask - 1;
-                const bool two = mask != 0;
-                const uint32_t t1 = two ? static_cast<uint32_t>(__ffsll(static_cast<long long>(mask)) - 1) : t0;
-                if (two) mask &= mask - 1;
-                const uint32_t q0 = t0 < nl ? f0 + t0 : f2 + (t0 - nl);
-                const uint32_t q1 = t1 < nl ? f0 + t1 : f2 + (t1 - nl);
-                const uint32_t w0 = __ldg(a.P.id + q0), w1 = __ldg(a.P.id + q1);
-                write_edge<kCsr>(a, pos, idv, w0);
-                if (two) write_edge<kCsr>(a, pos + 1, idv, w1);
-                pos += two ? 2 : 1;
+            // 3. the core stream: element j goes to base + j (coalesced); its owner
+            // from the table, the id loads of kCoreGroup windows issued together
+            for (uint32_t j0 = 0; j0 < T; j0 += kOwn) {
+                __syncwarp();
+                fill_owner(W.own, j0, cs, nc, lane);
+                __syncwarp();
+                const uint32_t jend = T - j0 > kOwn ? j0 + kOwn : T;
+                for (uint32_t jw = j0; jw < jend; jw += 32 * kCoreGroup) {
+                    uint2 o[kCoreGroup];
+                    uint32_t w[kCoreGroup];
+#pragma unroll
+                    for (int g = 0; g < kCoreGroup; ++g) {
+                        const uint32_t j = jw + 32 * g + lane;
+                        o[g] = make_uint2(0u, 0u);
+                        w[g] = 0u;
+                        if (j < jend) {
+                            o[g] = W.cr[owner_of(W.own, j - j0)];
+                            w[g] = __ldg(a.P.id + (j + o[g].x));
+                        }
+                    }
+#pragma unroll
+                    for (int g = 0; g < kCoreGroup; ++g) {
+                        const uint32_t j = jw + 32 * g + lane;
+                        if (j < jend) {
+                            write_edge<kCsr>(a, base + j, o[g].y, w[g]);
+                            if (kVerify && verify) verify_pair(a, M, C, o[g].y, w[g], 1, coshR);
+                        }
+                    }
+                }
             }
         }
     }
