@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--no-served", action="store_true", help="skip the served-workload measurement")
     ap.add_argument("--no-dynamic", action="store_true", help="skip the dynamic-model measurement")
+    ap.add_argument("--no-configs", action="store_true", help="skip the small-pairs and CSR configurations")
     ap.add_argument("--moved", type=float, default=0.12, help="fraction of vertices moved per dynamic step")
     ap.add_argument("--served-requests", type=int, default=400, help="requests per arrival rate")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
@@ -81,22 +82,33 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+TRAFFIC_SOURCES = ("paper_1606_09481_gb300/csrc/query.cu", "paper_1606_09481_gb300/csrc/common.cuh",
+                   "paper_1606_09481_gb300/csrc/kernels.h", "paper_1606_09481_gb300/csrc/detmath.cuh",
+                   "include/rhg.h")
+
+
+def sources_digest(paths=TRAFFIC_SOURCES) -> str:
+    """sha256 (16 hex digits) over the listed sources, in order: every file the
+    range query kernels are compiled from."""
+    h = hashlib.sha256()
+    for rel in paths:
+        h.update(rel.encode())
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source
-    has not changed since it was taken (else None)."""
+    """DRAM bytes per launch from the committed ncu summary, if none of the
+    sources the kernel is compiled from has changed since it was taken (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
     e = d.get(kernel)
-    if not e:
+    if not e or "sources_sha256_16" not in e:
         return None
-    src = os.path.join(ROOT, e["source"])
-    if not os.path.exists(src):
-        return None
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return e["dram_bytes_per_launch"] if digest == e["source_sha256_16"] else None
+    return e["dram_bytes_per_launch"] if sources_digest() == e["sources_sha256_16"] else None
 
 
 class ClockSampler:
@@ -151,8 +163,10 @@ class ClockSampler:
 
 def cpu_baseline(args, budget_s: float = 20.0, steps: int = 1):
     """The oracle (plain C, FP64) on this host: all points, the band structure,
-    and the outward range queries of a vertex sample; the O(n log n) set-up is
-    charged pro rata to the sample.  Returns (edges/s, info)."""
+    and the outward range queries of a vertex sample.  The O(n log n) set-up
+    (points and bands) runs once and is charged once, in full when the samples
+    cover at least n vertices, else pro rata to the vertices queried.
+    Returns (edges/s, info)."""
     import numpy as np
 
     import oracle
@@ -172,14 +186,17 @@ def cpu_baseline(args, budget_s: float = 20.0, steps: int = 1):
     prep.count_edges(probe)
     per_vertex = max((time.perf_counter() - t0) / len(probe), 1e-8)
     size = int(min(n, max(2000, budget_s / steps / per_vertex)))
-    total_edges, total_time, threads = 0, 0.0, 1
-    for _ in range(steps):
+    total_edges, query_time, threads = 0, 0.0, 1
+    diag = None
+    for step in range(steps):
         ids = np.sort(rng.choice(n, size=size, replace=False)).astype(np.uint32)
         t0 = time.perf_counter()
-        m_s, threads = prep.count_edges(ids)
-        t_q = time.perf_counter() - t0
+        m_s, threads, st = prep.count_edges(ids, with_stats=True)
+        query_time += max(time.perf_counter() - t0, 1e-9)
         total_edges += m_s
-        total_time += max(t_q, 1e-9) + (t_points + t_bands) * size / n
+        diag = diag or st
+    setup_charged = (t_points + t_bands) * min(1.0, steps * size / n)
+    total_time = query_time + setup_charged
     value = total_edges / total_time
     # the same queries on one thread, on a sample sized for about a tenth of the budget
     size1 = int(min(n, max(500, 0.1 * budget_s / max(per_vertex * threads, 1e-8))))
@@ -197,8 +214,10 @@ def cpu_baseline(args, budget_s: float = 20.0, steps: int = 1):
     info = {"value": value, "unit": "edges/s", "cores": threads, "kind": "oracle",
             "sample": (f"outward range queries of {size} random vertices per step x {steps} step(s) on the full "
                        f"n={n} point set ({total_edges} edges); point sampling ({t_points:.1f} s, 1 thread) and "
-                       f"band build ({t_bands:.1f} s, 1 thread) charged pro rata ({size}/{n} per step)"),
-            "seconds": total_time,
+                       f"band build ({t_bands:.1f} s, 1 thread) run once, charged once "
+                       f"({min(1.0, steps * size / n):.3f} of it: the fraction of n queried)"),
+            "seconds": total_time, "setup_seconds_charged": setup_charged, "query_seconds": query_time,
+            "diagnostics_first_step": diag,
             "single_thread": {"value": m1 / t1, "unit": "edges/s", "cores": 1,
                               "sample": f"outward range queries of {size1} random vertices ({m1} edges), set-up "
                                         f"charged pro rata"},
@@ -225,6 +244,90 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def bench_configs(args, rhg, torch, stream, reps1: int = 200, reps2: int = 20):
+    """The two other plain configurations, each with its own throughput and the
+    roofline of its range query:
+    - small pairs graph: n = 1e4, k = 6, alpha = 1, seed 1 (uint32 pairs);
+    - CSR graph: n = 1e6, k = 16, alpha = 0.75, seed 2 (row_ptr u64[n+1] +
+      col u32[2m]); its CSR stage (radix sort of the 2m directed keys the query
+      writes, then the row pointers) is timed on its own, with algorithmic bytes
+      = 16 B per directed key written and read by the query/sort boundary plus
+      the sort's passes (8 B read + 8 B written per key and pass) + 4 B per column
+      entry + 8 B per row pointer."""
+    import ctypes
+    L = rhg.load()
+    peak, peak_kind = measured_peaks()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    out = {}
+
+    def timed(call, reps):
+        for _ in range(5):
+            call()
+        torch.cuda.synchronize()
+        timer = rhg.StageTimer()
+        with timer:
+            e0.record(stream)
+            for _ in range(reps):
+                timer.reset_marks()
+                res = call()
+                timer.accumulate()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, {s_: timer.totals[s_] / reps for s_ in rhg.STAGES}, res
+
+    # small pairs graph
+    n, k, a, sd = 10_000, 6.0, 1.0, 1
+    p = rhg.make_params(n, k, a, sd)
+    wsp = rhg.allocate_pairs(p)
+    ms, st, res = timed(lambda: rhg.generate_pairs(n, k, a, sd, workspace=wsp, stream=stream)[1], reps1)
+    m = int(res.m)
+    alg = n * QUERY_BYTES_PER_POINT + m * QUERY_BYTES_PER_EDGE
+    out["small_pairs"] = {
+        "workload": "plain single graph: n=1e4, k=6, alpha=1.0, seed 1, uint32 pairs", "edges": m,
+        "value": m / (ms / 1e3), "unit": "edges/s", "ms_per_step": ms, "stages_ms": st, "reps": reps1,
+        "roofline": {"kernel": "range query", "bound": "hbm", "achieved": alg / (st["query"] / 1e3) / 1e9,
+                     "peak": peak, "unit": "GB/s", "frac": alg / (st["query"] / 1e3) / 1e9 / peak,
+                     "algorithmic_bytes_per_launch": alg, "peak_source": f"{peak_kind} hbm_gbs"},
+        "note": "launch- and latency-bound: ~28 kernel launches and one host synchronisation per call"}
+    del wsp
+    # CSR graph
+    n, k, a, sd = 10**6, 16.0, 0.75, 2
+    p = rhg.make_params(n, k, a, sd)
+    row_ptr, col, res0 = rhg.generate_csr(n, k, a, sd, stream=stream)
+    cap = int(col.numel()) + 4096
+    nb = ctypes.c_size_t(0)
+    L.rhg_workspace_bytes(ctypes.byref(p), cap, ctypes.byref(nb))
+    ws = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    colbuf = torch.empty(cap, dtype=torch.int32, device="cuda")
+    res = rhg.Result()
+
+    def csr_call():
+        rc = L.rhg_generate_csr(ctypes.byref(p), ws.data_ptr(), ws.numel(), row_ptr.data_ptr(), colbuf.data_ptr(),
+                                cap, sptr, ctypes.byref(res))
+        rhg._check(rc, "rhg_generate_csr", res)
+        return res
+
+    ms, st, res = timed(csr_call, reps2)
+    m = int(res.m)
+    q_alg = n * QUERY_BYTES_PER_POINT + m * 16
+    passes = 2 * ((max(n - 1, 1).bit_length() + 7) // 8)
+    csr_alg = 2 * m * (16 * passes + 8 + 4) + 8 * (n + 1)
+    out["csr"] = {
+        "workload": "plain single graph: n=1e6, k=16, alpha=0.75, seed 2, CSR (row_ptr u64[n+1], col u32[2m])",
+        "edges": m, "value": m / (ms / 1e3), "unit": "edges/s", "ms_per_step": ms, "stages_ms": st, "reps": reps2,
+        "roofline": {"kernel": "range query", "bound": "hbm", "achieved": q_alg / (st["query"] / 1e3) / 1e9,
+                     "peak": peak, "unit": "GB/s", "frac": q_alg / (st["query"] / 1e3) / 1e9 / peak,
+                     "algorithmic_bytes_per_launch": q_alg, "peak_source": f"{peak_kind} hbm_gbs",
+                     "bytes_note": "40 B per point read + 16 B per edge written (two 8-byte directed keys)"},
+        "csr_stage_roofline": {"kernel": f"radix sort of 2m keys ({passes} passes) + row pointers", "bound": "hbm",
+                               "achieved": csr_alg / (st["csr"] / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                               "frac": csr_alg / (st["csr"] / 1e3) / 1e9 / peak,
+                               "algorithmic_bytes_per_launch": csr_alg}}
+    del ws, colbuf, row_ptr, col
+    return out
 
 
 def batched_specs(count: int = 4096):
@@ -332,7 +435,15 @@ def bench_batched(args, rhg, torch, stream):
     tuned = {"value": int(ttot.m) / (tuned_ms / 1000.0), "ms_per_step": tuned_ms,
              "edges_equal_default": int(ttot.m) == m,
              "band_offsets": {f"{lo}-{hi}": table.offsets.get(c, 0) for c, (lo, hi) in enumerate(table.classes)}}
+    peak, peak_kind = measured_peaks()
+    q_ms = timer.totals["query"] / max(args.steps, 1)
+    alg = points * QUERY_BYTES_PER_POINT + m * QUERY_BYTES_PER_EDGE
+    roof = {"kernel": "batched range query (all graphs)", "bound": "hbm", "achieved": alg / (q_ms / 1e3) / 1e9,
+            "peak": peak, "unit": "GB/s", "frac": alg / (q_ms / 1e3) / 1e9 / peak, "algorithmic_bytes_per_launch": alg,
+            "avg_launch_ms": q_ms, "peak_source": f"{peak_kind} hbm_gbs",
+            "whole_call_frac": (alg / (ms / 1e3) / 1e9) / peak}
     return {"value": value, "unit": "edges/s", "ms_per_step": ms, "graphs": len(specs), "points": points,
+            "roofline": roof,
             "autotuned_bands": tuned, "graph_replay": graph_replay,
             "edges": m, "exact_edges_equal_plain": plain_m == m, "plain_per_graph_value": plain,
             "plain_per_graph_ms": plain_ms, "speedup_vs_plain": value / plain,
@@ -372,6 +483,9 @@ def bench_served(args, rhg, torch):
                       "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99), "edges_per_s": m / span,
                       "batched_fraction": sum(c.batch_size > 1 for c in done) / len(done),
                       "peak_reserved_gb": srv.peak_reserved / 1e9})
+    peak, _ = measured_peaks()
+    for r in rates:  # bytes the generations write (pairs) and read (sorted points) per second, vs the peak
+        r["hbm_frac_of_output_and_points"] = (r["edges_per_s"] * QUERY_BYTES_PER_EDGE) / 1e9 / peak
     best = max(r["edges_per_s"] for r in rates)
     return {"plain_capacity_rps": cap, "plain_edges_per_s": plain_m / plain_s, "best_edges_per_s": best,
             "speedup_vs_plain": best / (plain_m / plain_s), "rates": rates,
@@ -444,9 +558,17 @@ def bench_dynamic(args, rhg, torch, stream):
     full_ms = e0.elapsed_time(e1) / args.steps
     same = m_full == m
     del ws_full, ws_upd, bufs
+    peak, peak_kind = measured_peaks()
+    # per update, the bytes an update cannot avoid: the old pairs read once, the
+    # new pairs written once, the points' FP64 coordinates read once (16 B)
+    upd_alg = 8 * m + 8 * m + 16 * n
     return {"moved_fraction": args.moved, "moved_per_step": cnt, "edges": m, "update_ms": upd_ms,
             "regenerate_ms": full_ms, "update_edges_per_s": m / (upd_ms / 1000.0),
             "speedup_vs_regenerate": full_ms / upd_ms, "edge_count_equals_regeneration": same,
+            "roofline": {"kernel": "update step (keep old pairs, re-query moved vertices)", "bound": "hbm",
+                         "achieved": upd_alg / (upd_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": upd_alg / (upd_ms / 1e3) / 1e9 / peak, "algorithmic_bytes_per_launch": upd_alg,
+                         "peak_source": f"{peak_kind} hbm_gbs"},
             "workload": f"dynamic: n={n}, k={k}, alpha={alpha}, seed {args.seed}; per step {args.moved:.0%} of the "
                         "vertices (uniform random, torch generator) move with tau_phi in (-1, 1), tau_r in (-10, 1) "
                         "(Philox); step = move + update of the previous edge list"}
@@ -572,6 +694,9 @@ def run_ours(args):
                        "ms_per_step": 1000 * e2e_s,
                        "note": "parameters in, pairs out to pinned host memory; two metadata reads per call"}
         del host
+
+    if not args.no_configs:
+        line["configs"] = bench_configs(args, rhg, torch, stream)
 
     if not args.no_batched:
         del pairs

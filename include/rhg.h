@@ -114,6 +114,13 @@ const char *rhg_status_str(int status);
 int rhg_version(void);
 
 /*
+ * rhg_default_bands -- the band count used when rhg_params.num_bands is 0:
+ * ceil(log2 n), at least 1 (the "log n" bands of Sec. III-A).  Host-only; n = 0
+ * and 1 give 1.
+ */
+uint32_t rhg_default_bands(uint64_t n);
+
+/*
  * rhg_plan_workspace_bytes -- device workspace rhg_target_radius and rhg_plan
  * need (a few KB of per-graph metadata).  Host-only.
  */

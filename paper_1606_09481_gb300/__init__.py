@@ -128,6 +128,8 @@ def _load_locked() -> ctypes.CDLL:
     L.rhg_set_stage_events.argtypes = [_p, _c_u32]
     L.rhg_launch_count.restype = _c_u64
     L.rhg_launch_count.argtypes = []
+    L.rhg_default_bands.restype = _c_u32
+    L.rhg_default_bands.argtypes = [_c_u64]
     _lib = L
     return L
 
@@ -178,10 +180,8 @@ def status_str(status: int) -> str:
 
 
 def default_bands(n: int) -> int:
-    B = 0
-    while B < 63 and (1 << B) < n:
-        B += 1
-    return max(B, 1)
+    """The library's default band count for n points (rhg_default_bands)."""
+    return int(load().rhg_default_bands(int(n)))
 
 
 def make_params(n, k=0.0, alpha=1.0, seed=0, num_bands=0, band_ratio=0.0, R_override=0.0, flags=0):

@@ -10,7 +10,6 @@ points, claimed dynamically) is fixed and not tuned.
 """
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass, field
 
 DEFAULT_CLASSES = ((1_000, 10_000), (10_000, 100_000), (100_000, 10_000_000))
@@ -18,8 +17,10 @@ DEFAULT_OFFSETS = (-8, -6, -4, -2, 0, 2)
 
 
 def default_bands(n: int) -> int:
-    """ceil(log2 n), at least 1 (the library's default)."""
-    return max(1, math.ceil(math.log2(max(int(n), 2))))
+    """The library's default band count (rhg_default_bands), so that the tuner's
+    offsets are relative to what the library would use."""
+    from . import default_bands as lib_default_bands
+    return lib_default_bands(n)
 
 
 @dataclass

@@ -801,6 +801,8 @@ int rhg_set_stage_events(void *const *events, uint32_t count)
 
 uint64_t rhg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+uint32_t rhg_default_bands(uint64_t n) { return default_bands(n); }
+
 int rhg_workspace_bytes(const rhg_params *p, uint64_t capacity_entries, size_t *bytes)
 {
     uint32_t B;

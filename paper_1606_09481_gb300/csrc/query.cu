@@ -38,6 +38,8 @@ constexpr int kBitWords = 128;         // decision words per warp: kChunk / 32
 constexpr uint32_t kFull = 0x80000000u;  // window half-width meaning "whole band"
 constexpr int kBatchMinBlocks = 4;         // resident CTAs per SM the batch kernel is compiled for
 constexpr int kCoreGroup = 4;              // core-writer windows whose loads are issued together
+constexpr int kHeavyGroup = 16;            // the same in the heavy kernel's core chunks
+constexpr int kFringeRounds = 4;           // heavy fringe-chunk rounds whose values load together
 
 constexpr float kPiF = 3.14159265f;             // 3.14159274f, just above pi; sin^2(d/2) is even about pi
 constexpr float kTwoPiHiF = 6.28318548202514648f;
@@ -440,9 +442,10 @@ __device__ __forceinline__ int decide(const QueryArgs &a, const Meta *Mg, Meta *
 }
 
 // Write a core chunk: owner idv and the sorted positions [q0, q0 + total), all
-// certain edges; element j goes to base + j (coalesced), the id loads of four
-// 32-element windows issued together.  Output: graph Mg's edge counter, its
-// region starting at obase with room for cap pairs.
+// certain edges; element j goes to base + j (coalesced), the id loads of
+// kHeavyGroup 32-element windows issued together (one warp works a chunk on its
+// own, so the loads in flight are what hides the memory latency).  Output: graph
+// Mg's edge counter, its region starting at obase with room for cap pairs.
 template <bool kCsr, bool kVerify>
 __device__ __forceinline__ void write_core_chunk(const QueryArgs &a, Meta *Mg, Meta *C, uint64_t obase, uint64_t cap,
                                                  uint32_t idv, uint32_t q0, uint32_t total, double coshR, bool verify)
@@ -454,15 +457,15 @@ __device__ __forceinline__ void write_core_chunk(const QueryArgs &a, Meta *Mg, M
     base = __shfl_sync(full, base, 0);
     if (base + total > cap) return;
     base += obase;
-    for (uint32_t j0 = 0; j0 < total; j0 += 32 * kCoreGroup) {
-        uint32_t w[kCoreGroup];
+    for (uint32_t j0 = 0; j0 < total; j0 += 32 * kHeavyGroup) {
+        uint32_t w[kHeavyGroup];
 #pragma unroll
-        for (int g = 0; g < kCoreGroup; ++g) {
+        for (int g = 0; g < kHeavyGroup; ++g) {
             const uint32_t j = j0 + 32 * g + lane;
             w[g] = j < total ? __ldg(a.P.id + (q0 + j)) : 0u;
         }
 #pragma unroll
-        for (int g = 0; g < kCoreGroup; ++g) {
+        for (int g = 0; g < kHeavyGroup; ++g) {
             const uint32_t j = j0 + 32 * g + lane;
             if (j < total) {
                 write_edge<kCsr>(a, base + j, idv, w[g]);
@@ -531,10 +534,10 @@ __device__ __forceinline__ void flush(const QueryArgs &a, Meta *Mg, Meta *C, uin
 }
 
 // Filter-mode fringe chunk of the owner in slot 0: candidates at the sorted
-// positions [lo, lo + total) in rounds of 32, the next round's candidate values
-// loaded while the current round is tested; one decision bit per candidate, one
-// output reservation per segment of kBitWords rounds, then a replay of the set
-// bits.
+// positions [lo, lo + total) in rounds of 32, the candidate values of
+// kFringeRounds rounds loaded together before they are tested; one decision bit
+// per candidate, one output reservation per segment of kBitWords rounds, then a
+// replay of the set bits (the id loads of kFringeRounds words issued together).
 template <bool kCsr, bool kVerify>
 __device__ __forceinline__ void test_fringe_chunk(const QueryArgs &a, Meta *Mg, Meta *C, uint64_t obase, uint64_t cap,
                                                   WarpSmem &W, uint32_t lo, uint32_t total, double coshR, bool verify)
@@ -548,38 +551,42 @@ __device__ __forceinline__ void test_fringe_chunk(const QueryArgs &a, Meta *Mg, 
         const uint32_t seg_end = total - seg > kBitWords * 32 ? seg + kBitWords * 32 : total;
         int words = 0;
         uint32_t edges = 0;
-        float2 aw = make_float2(0.0f, 0.0f);
-        float4 pw = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (seg + lane < seg_end) {
-            aw = a.P.ang[lo + seg + lane];
-            pw = a.P.pms[lo + seg + lane];
-        }
-        for (uint32_t j0 = seg; j0 < seg_end; j0 += 32) {
-            const uint32_t j = j0 + lane;
-            const bool in = j < seg_end;
-            const float2 ac = aw;
-            const float4 pc = pw;
-            if (j + 32 < seg_end) {
-                aw = a.P.ang[lo + j + 32];
-                pw = a.P.pms[lo + j + 32];
-            }
-            const int dec = in ? filter_decide(va, vb, ac, pc) : 0;
-            const uint32_t um = __ballot_sync(full, dec == 2);
-            if (um) {
-                uint32_t rb = 0;
-                if (lane == 0) rb = atomicAdd(&C->recheck_n, static_cast<uint32_t>(__popc(um)));
-                rb = __shfl_sync(full, rb, 0);
-                if (dec == 2) {
-                    const uint32_t at = rb + __popc(um & lt);
-                    if (at < a.recheck_cap) a.recheck[at] = make_uint2(pv, lo + j);
-                    else atomicMax(&C->error, kErrListFull);
+        for (uint32_t j0 = seg; j0 < seg_end; j0 += 32 * kFringeRounds) {
+            float2 ac[kFringeRounds];
+            float4 pc[kFringeRounds];
+#pragma unroll
+            for (int r = 0; r < kFringeRounds; ++r) {
+                const uint32_t j = j0 + 32 * r + lane;
+                ac[r] = make_float2(0.0f, 0.0f);
+                pc[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (j < seg_end) {
+                    ac[r] = a.P.ang[lo + j];
+                    pc[r] = a.P.pms[lo + j];
                 }
             }
-            if (kVerify && verify && in && dec != 2) verify_pair(a, Mg, C, idv, a.P.id[lo + j], dec, coshR);
-            const uint32_t word = __ballot_sync(full, dec == 1);
-            if (lane == 0) W.bits[words] = word;
-            ++words;
-            edges += __popc(word);
+#pragma unroll
+            for (int r = 0; r < kFringeRounds; ++r) {
+                if (j0 + 32 * r >= seg_end) break;  // warp-uniform
+                const uint32_t j = j0 + 32 * r + lane;
+                const bool in = j < seg_end;
+                const int dec = in ? filter_decide(va, vb, ac[r], pc[r]) : 0;
+                const uint32_t um = __ballot_sync(full, dec == 2);
+                if (um) {
+                    uint32_t rb = 0;
+                    if (lane == 0) rb = atomicAdd(&C->recheck_n, static_cast<uint32_t>(__popc(um)));
+                    rb = __shfl_sync(full, rb, 0);
+                    if (dec == 2) {
+                        const uint32_t at = rb + __popc(um & lt);
+                        if (at < a.recheck_cap) a.recheck[at] = make_uint2(pv, lo + j);
+                        else atomicMax(&C->error, kErrListFull);
+                    }
+                }
+                if (kVerify && verify && in && dec != 2) verify_pair(a, Mg, C, idv, a.P.id[lo + j], dec, coshR);
+                const uint32_t word = __ballot_sync(full, dec == 1);
+                if (lane == 0) W.bits[words] = word;
+                ++words;
+                edges += __popc(word);
+            }
         }
         __syncwarp();
         unsigned long long base = 0;
@@ -588,14 +595,20 @@ __device__ __forceinline__ void test_fringe_chunk(const QueryArgs &a, Meta *Mg, 
         if (edges && base + edges <= cap) {
             base += obase;
             uint32_t run = 0;
-#pragma unroll 4
-            for (int wi = 0; wi < words; ++wi) {
-                const uint32_t word = W.bits[wi];
-                if ((word >> lane) & 1u) {
-                    const uint32_t j = seg + static_cast<uint32_t>(wi) * 32 + lane;
-                    write_edge<kCsr>(a, base + run + __popc(word & lt), idv, __ldg(a.P.id + (lo + j)));
+            for (int w0 = 0; w0 < words; w0 += kFringeRounds) {
+                uint32_t word[kFringeRounds], idw[kFringeRounds];
+#pragma unroll
+                for (int r = 0; r < kFringeRounds; ++r) {
+                    word[r] = w0 + r < words ? W.bits[w0 + r] : 0u;
+                    idw[r] = 0u;
+                    if ((word[r] >> lane) & 1u)
+                        idw[r] = __ldg(a.P.id + (lo + seg + static_cast<uint32_t>(w0 + r) * 32 + lane));
                 }
-                run += __popc(word);
+#pragma unroll
+                for (int r = 0; r < kFringeRounds; ++r) {
+                    if ((word[r] >> lane) & 1u) write_edge<kCsr>(a, base + run + __popc(word[r] & lt), idv, idw[r]);
+                    run += __popc(word[r]);
+                }
             }
         }
         __syncwarp();

@@ -139,3 +139,28 @@ def test_dense_graphs_in_fp64_mode(O):
     assert res.mode == 0 and alpha * R > 44
     phi, r = O.sample_points(n, alpha, R, seed)
     assert np.array_equal(sorted_pairs(pairs), O.band_edges(phi, r, R, O.default_bands(n)))
+
+
+@pytest.mark.parametrize("n,k,alpha,seed", [(20_000, 30, 0.8, 5), (3000, 200, 1.0, 6)])
+def test_output_buffer_at_odd_slot(O, n, k, alpha, seed):
+    """The C ABI asks only for an 8-byte aligned pair buffer: a buffer that starts
+    8 bytes past a 16-byte boundary gives the same edges (the core writer's
+    16-byte stores align themselves to the buffer's address)."""
+    import ctypes
+
+    import torch
+    rhg = require_gpu()
+    p = rhg.make_params(n, k, alpha, seed)
+    wsp = rhg.allocate_pairs(p)
+    out = torch.empty(2 * wsp.capacity + 4, dtype=torch.int32, device="cuda")
+    assert out.data_ptr() % 16 == 0
+    res = rhg.Result()
+    rc = rhg.load().rhg_generate_pairs(ctypes.byref(p), wsp.ws.data_ptr(), wsp.ws.numel(), out.data_ptr() + 8,
+                                       wsp.capacity, None, ctypes.byref(res))
+    assert rc == rhg.OK
+    torch.cuda.synchronize()
+    got = sorted_pairs(out[2: 2 + 2 * res.m].view(-1, 2))
+    R = O.target_radius(n, k, alpha)
+    phi, r = O.sample_points(n, alpha, R, seed)
+    assert np.array_equal(got, O.brute_edges(phi, r, R))
+    assert res.m > 0
