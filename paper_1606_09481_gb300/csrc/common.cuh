@@ -18,6 +18,7 @@ constexpr int kMaxBands = static_cast<int>(RHG_MAX_BANDS);
 constexpr uint32_t kBucketPoints = 1;
 __host__ __device__ constexpr uint64_t index_entries(uint64_t n) { return n / kBucketPoints + 3 * kMaxBands + 1; }
 constexpr int kExpTab = 64;  // e^k table for k = -64..64 (FP32 filter values)
+constexpr uint32_t kClaimCounters = 16;  // work-claim counters of the range query (Meta::claim)
 
 // ---------------------------------------------------------------------------
 // FP32 filter: error model.  The filter evaluates X = L / cosh R in the
@@ -73,7 +74,11 @@ struct Meta {
     uint64_t verify_failures;
     uint32_t heavy_n, heavy_next;      // heavy-range chunk list
     uint32_t recheck_n, pad0;          // FP64 recheck list
-    uint64_t work_counter;             // next warp batch of the range query
+    uint64_t work_counter;             // dynamic model: moved vertices listed
+    // work claims of the range query: counter c hands out the warp batches
+    // c, c + kClaimCounters, ... (one counter per 128-byte line, so that the claims
+    // of different warps do not queue on one address)
+    uint32_t claim[kClaimCounters * 32];
 };
 
 // device-side error codes (Meta::error)

@@ -183,6 +183,7 @@ __device__ void plan_block(Meta *M, const PlanArgs &a, int depth)
     M->heavy_next = 0;
     M->recheck_n = 0;
     M->work_counter = 0;
+    for (uint32_t c = 0; c < kClaimCounters; ++c) M->claim[c * 32] = 0;
 }
 
 __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, PlanArgs a) { plan_block(M, a, 8); }
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_batch_kernel(Meta *metas, c
     C->heavy_next = 0;
     C->recheck_n = 0;
     C->work_counter = 0;
+    for (uint32_t c = 0; c < kClaimCounters; ++c) C->claim[c * 32] = 0;
 }
 
 constexpr int kSampleThreads = 256;

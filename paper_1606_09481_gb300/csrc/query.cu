@@ -738,14 +738,21 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryA
     const uint32_t nbatch = kMulti ? a.bt.num_tiles * (kTilePoints / 32) : (n + 31) / 32;
     unsigned long long cand = 0;
     uint64_t near = 0;
-    // batches in sorted order from a shared counter: the costly inner-band batches
-    // start first and the rest fill in around them
+    // batches in sorted order from kClaimCounters interleaved counters (counter c
+    // hands out batches c, c + kClaimCounters, ...): the costly inner-band batches
+    // start first and the rest fill in around them.  A warp starts on its own
+    // counter and moves to the next one when it is used up; it stops when all are.
+    uint32_t ci = (blockIdx.x * kWarps + (threadIdx.x >> 5)) % kClaimCounters, misses = 0;
     for (;;) {
         uint32_t batch = 0;
-        if (lane == 0)
-            batch = static_cast<uint32_t>(atomicAdd(reinterpret_cast<unsigned long long *>(&C->work_counter), 1ull));
+        if (lane == 0) batch = atomicAdd(&C->claim[ci * 32], 1u) * kClaimCounters + ci;
         batch = __shfl_sync(full, batch, 0);
-        if (batch >= nbatch) break;
+        if (batch >= nbatch) {
+            if (++misses == kClaimCounters) break;
+            ci = ci + 1 == kClaimCounters ? 0 : ci + 1;
+            continue;
+        }
+        misses = 0;
         uint32_t p0, cnt;  // first sorted position and points of this batch
         if (kMulti) {
             const uint4 T = a.bt.tiles[batch / (kTilePoints / 32)];
@@ -971,16 +978,14 @@ __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
     __shared__ WarpSmem Wsm[kWarps];
     Meta *C = kMulti ? a.M + a.bt.G : a.M;
     if (C->error || (!kMulti && (C->filter != 0) != kFilter)) return;
-    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmem &W = Wsm[warp];
     const uint32_t count = C->heavy_n < a.heavy_cap ? C->heavy_n : a.heavy_cap;
     uint64_t near = 0;
-    for (;;) {
-        uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(&C->heavy_next, 1u);
-        item = __shfl_sync(full, item, 0);
-        if (item >= count) break;
+    // chunks round robin over the warps (all chunks hold at most kChunk candidates
+    // and most hold exactly that): no claim traffic on a shared counter
+    const uint32_t gwarps = gridDim.x * kWarps;
+    for (uint32_t item = blockIdx.x * kWarps + warp; item < count; item += gwarps) {
         const uint4 h = a.heavy[item];
         const uint32_t g = h.w >> 1;
         Meta *Mg = kMulti ? a.M + g : a.M;
@@ -1089,6 +1094,7 @@ __global__ void reset_phase_kernel(Meta *C)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         C->work_counter = 0;
+        for (uint32_t c = 0; c < kClaimCounters; ++c) C->claim[c * 32] = 0;
         C->heavy_n = 0;
         C->heavy_next = 0;
     }
