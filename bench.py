@@ -388,6 +388,7 @@ def bench_batched(args, rhg, torch, stream):
     graph_ms = e0.elapsed_time(e1) / args.steps
     graph_replay = {"value": int(gtot.m) / (graph_ms / 1000.0), "ms_per_step": graph_ms,
                     "edges_equal_default": grc == rhg.OK and int(gtot.m) == m}
+    device_stages = rhg.batch_stage_times(plan, buf, stream)  # of the last replay
     del graph
     del buf
     # the plain path, one call per graph, reusing one workspace sized for the most
@@ -413,8 +414,12 @@ def bench_batched(args, rhg, torch, stream):
     # the band count per size class chosen by the autotuner, then the same timing
     from paper_1606_09481_gb300.autotune import gpu_runner, tune
     table = tune(specs, gpu_runner(stream))
-    tuned_params = (rhg.Params * len(specs))(*[rhg.make_params(n, kk, a, sd, table.bands(n))
-                                                for (n, kk, a, sd) in specs])
+
+    def tuned_one(n, kk, a, sd):
+        b, bb, ch, fl = table.params(n)
+        return rhg.make_params(n, kk, a, sd, b, batch_budget=bb, core_heavy=ch, fringe_limit=fl)
+
+    tuned_params = (rhg.Params * len(specs))(*[tuned_one(*sp) for sp in specs])
     tbuf = rhg.allocate_batch(tuned_params)
     rc, tres, ttot = rhg.run_batch(tbuf, stream)
     if rc == rhg.OVERFLOW:
@@ -434,9 +439,9 @@ def bench_batched(args, rhg, torch, stream):
     del tbuf
     tuned = {"value": int(ttot.m) / (tuned_ms / 1000.0), "ms_per_step": tuned_ms,
              "edges_equal_default": int(ttot.m) == m,
-             "band_offsets": {f"{lo}-{hi}": table.offsets.get(c, 0) for c, (lo, hi) in enumerate(table.classes)}}
+             "tuned_per_size_class": table.describe()}
     peak, peak_kind = measured_peaks()
-    q_ms = timer.totals["query"] / max(args.steps, 1)
+    q_ms = sum(v for s_, v in device_stages.items() if s_.startswith(("query", "heavy", "recheck")))
     alg = points * QUERY_BYTES_PER_POINT + m * QUERY_BYTES_PER_EDGE
     roof = {"kernel": "batched range query (all graphs)", "bound": "hbm", "achieved": alg / (q_ms / 1e3) / 1e9,
             "peak": peak, "unit": "GB/s", "frac": alg / (q_ms / 1e3) / 1e9 / peak, "algorithmic_bytes_per_launch": alg,
@@ -444,10 +449,10 @@ def bench_batched(args, rhg, torch, stream):
             "whole_call_frac": (alg / (ms / 1e3) / 1e9) / peak}
     return {"value": value, "unit": "edges/s", "ms_per_step": ms, "graphs": len(specs), "points": points,
             "roofline": roof,
-            "autotuned_bands": tuned, "graph_replay": graph_replay,
+            "autotuned": tuned, "graph_replay": graph_replay,
             "edges": m, "exact_edges_equal_plain": plain_m == m, "plain_per_graph_value": plain,
             "plain_per_graph_ms": plain_ms, "speedup_vs_plain": value / plain,
-            "stages_ms": {s: timer.totals[s] / max(args.steps, 1) for s in rhg.STAGES if s != "csr"},
+            "stages_ms": device_stages, "launches_per_call": "1 (persistent, cooperative)",
             "workload": "batched: 4096 graphs, n log-uniform in [1e3, 1e5], k uniform in 6..32, alpha uniform "
                         "in [0.55, 1.5], seeds 1000..5095 (numpy PCG64 seed 4096), FP32 filter + FP64 recheck, "
                         "B = ceil(log2 n) per graph"}

@@ -87,6 +87,16 @@ typedef struct rhg_params {
     uint32_t flags;      /* RHG_FLAG_*                                                */
     double band_ratio;   /* 0 = 0.9; otherwise > 0 (Sec. III-A, ratio p)              */
     double R_override;   /* > 0: use this disk radius instead of solving Eq. 22       */
+    /* Work mapping of the range query (performance only, never the edge set);
+     * 0 = the library default:                                                   */
+    uint32_t batch_budget; /* candidates one warp batch of 32 points keeps before
+                              its longer ranges go to the shared chunk list
+                              (default 65536; 1024 .. 2^24)                        */
+    uint32_t core_heavy;   /* longest certain range a warp batch writes itself
+                              (default 4096; 64 .. 65536)                          */
+    uint32_t fringe_limit; /* longest tested range a lane tests itself
+                              (default 32; 1 .. 32)                                */
+    uint32_t reserved;     /* must be 0                                           */
 } rhg_params;
 
 /* Per-call report, filled on the host when the pointer is non-NULL. */
@@ -110,7 +120,8 @@ typedef struct rhg_result {
 /* Human-readable name of a status code (static string, never NULL). */
 const char *rhg_status_str(int status);
 
-/* ABI version of this header: 2 (2 added rhg_result.rounding_band). */
+/* ABI version of this header: 3 (2 added rhg_result.rounding_band, 3 the work
+ * mapping fields of rhg_params). */
 int rhg_version(void);
 
 /*
@@ -325,6 +336,36 @@ int rhg_batch_prepare(const rhg_params *graphs, uint32_t count, const uint64_t *
 int rhg_batch_launch(const rhg_batch_plan *plan, void *d_workspace, uint32_t *d_pairs, void *stream);
 int rhg_batch_read_results(const rhg_batch_plan *plan, const void *d_workspace, void *stream,
                            rhg_batch_graph *results, rhg_result *totals);
+
+/*
+ * The batch runs as one persistent, cooperative kernel launch: all its stages,
+ * one after another, each spread over every resident CTA, separated by grid
+ * barriers.  A barrier wait gives up after 20 s of device time; the batch then
+ * reports RHG_ERR_TIMEOUT (for every graph) instead of hanging the device.
+ *
+ * rhg_batch_stage_times -- device time of each stage of the last launch in
+ * d_workspace (after the launch has completed), in ms, RHG_BATCH_STAGE_COUNT
+ * values in this order: plan, sampling, band offsets, then 5 sort passes x
+ * (digit counts, scan, scatter), gather, bucket index, range query (filter
+ * graphs), heavy chunks (filter graphs), FP64 rechecks, phase reset, range query
+ * (FP64 graphs), heavy chunks (FP64 graphs), results.  Synchronises the stream.
+ * Errors: INVALID_ARG (no plan, count too small), CUDA.
+ */
+#define RHG_BATCH_STAGE_COUNT 27u
+int rhg_batch_stage_times(const rhg_batch_plan *plan, const void *d_workspace, void *stream, double *ms,
+                          uint32_t count);
+
+/*
+ * rhg_grid_barrier_test -- the grid barrier of the persistent batch launch on
+ * its own, for testing its timeout: a cooperative launch of 2 CTAs per SM whose
+ * barrier expects `missing` more CTAs than there are.  missing = 0: the barrier
+ * completes, RHG_OK.  missing > 0: no CTA can pass, every wait gives up after
+ * timeout_ns (at most 10 s) and the call returns RHG_ERR_TIMEOUT; the device
+ * stays usable.  d_workspace: rhg_plan_workspace_bytes() + 256 bytes, 256-byte
+ * aligned.  Synchronises the stream.
+ */
+int rhg_grid_barrier_test(uint32_t missing, uint64_t timeout_ns, void *d_workspace, size_t workspace_bytes,
+                          void *stream);
 
 /*
  * Dynamic model (Sec. III-C): vertices move in discrete steps, each a rotation

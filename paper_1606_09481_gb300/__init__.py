@@ -21,6 +21,7 @@ __all__ = [
     "edges_from_points", "batch_params", "batch_workspace_bytes", "allocate_batch", "run_batch", "generate_batch",
     "BatchPlan", "batch_prepare", "batch_launch", "batch_read_results", "capture_batch",
     "draw_movement", "move_points", "update_edges", "dm_eval", "default_bands", "make_params", "estimate_capacity",
+    "batch_stage_times", "grid_barrier_test",
     "StageTimer", "launch_count", "FLAG_FP64_ONLY", "FLAG_VERIFY", "MAX_BANDS", "STATIC_MAX_POINTS", "build",
 ]
 
@@ -37,7 +38,8 @@ _c_u64, _c_u32, _c_dbl, _c_size, _p = (ctypes.c_uint64, ctypes.c_uint32, ctypes.
 class Params(ctypes.Structure):
     _fields_ = [("n", _c_u64), ("k", _c_dbl), ("alpha", _c_dbl), ("seed", _c_u64),
                 ("num_bands", _c_u32), ("flags", _c_u32), ("band_ratio", _c_dbl),
-                ("R_override", _c_dbl)]
+                ("R_override", _c_dbl), ("batch_budget", _c_u32), ("core_heavy", _c_u32),
+                ("fringe_limit", _c_u32), ("reserved", _c_u32)]
 
 
 class Result(ctypes.Structure):
@@ -113,6 +115,8 @@ def _load_locked() -> ctypes.CDLL:
     L.rhg_batch_launch.argtypes = [ctypes.POINTER(BatchPlan), _p, _p, _p]
     L.rhg_batch_read_results.argtypes = [ctypes.POINTER(BatchPlan), _p, _p, ctypes.POINTER(BatchGraph),
                                          ctypes.POINTER(Result)]
+    L.rhg_batch_stage_times.argtypes = [ctypes.POINTER(BatchPlan), _p, _p, ctypes.POINTER(_c_dbl), _c_u32]
+    L.rhg_grid_barrier_test.argtypes = [_c_u32, _c_u64, _p, _c_size, _p]
     L.rhg_draw_movement.argtypes = [_c_u64, _c_u64, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _p, _p, _p]
     L.rhg_move_points.argtypes = [_p, _c_u64, _c_u64, _p, _p, _p, _p, _c_dbl, _c_dbl, _p]
     L.rhg_workspace_bytes_update.argtypes = [_c_u64, _c_u64, _c_u32, ctypes.POINTER(_c_size)]
@@ -184,9 +188,11 @@ def default_bands(n: int) -> int:
     return int(load().rhg_default_bands(int(n)))
 
 
-def make_params(n, k=0.0, alpha=1.0, seed=0, num_bands=0, band_ratio=0.0, R_override=0.0, flags=0):
+def make_params(n, k=0.0, alpha=1.0, seed=0, num_bands=0, band_ratio=0.0, R_override=0.0, flags=0,
+                batch_budget=0, core_heavy=0, fringe_limit=0):
+    """rhg_params; the last three set the range query's work mapping (0: default)."""
     return Params(int(n), float(k), float(alpha), int(seed), int(num_bands), int(flags), float(band_ratio),
-                  float(R_override))
+                  float(R_override), int(batch_budget), int(core_heavy), int(fringe_limit), 0)
 
 
 # ---------------------------------------------------------------- torch plumbing
@@ -370,6 +376,28 @@ def batch_read_results(plan: BatchPlan, buf: BatchBuffers, stream=None):
     rc = load().rhg_batch_read_results(ctypes.byref(plan), buf.ws.data_ptr(), _stream(stream), res,
                                        ctypes.byref(tot))
     return rc, res, tot
+
+
+BATCH_STAGES = ("plan", "sample", "band_offsets") + tuple(
+    f"sort{p}_{part}" for p in range(5) for part in ("counts", "scan", "scatter")) + (
+    "gather", "bucket_index", "query_filter", "heavy_filter", "recheck", "phase_reset", "query_fp64", "heavy_fp64",
+    "results")
+
+
+def batch_stage_times(plan: BatchPlan, buf: BatchBuffers, stream=None) -> dict:
+    """rhg_batch_stage_times: device time (ms) of each stage of the last launch."""
+    arr = (_c_dbl * len(BATCH_STAGES))()
+    _check(load().rhg_batch_stage_times(ctypes.byref(plan), buf.ws.data_ptr(), _stream(stream), arr,
+                                        len(BATCH_STAGES)), "rhg_batch_stage_times")
+    return dict(zip(BATCH_STAGES, (float(v) for v in arr)))
+
+
+def grid_barrier_test(missing: int, timeout_ns: int, stream=None) -> int:
+    """rhg_grid_barrier_test: the persistent launch's grid barrier with `missing`
+    CTAs that never arrive; returns the status (OK or TIMEOUT)."""
+    ws = _empty_bytes(plan_workspace_bytes() + 256)
+    return int(load().rhg_grid_barrier_test(int(missing), int(timeout_ns), ws.data_ptr(), ws.numel(),
+                                            _stream(stream)))
 
 
 def capture_batch(plan: BatchPlan, buf: BatchBuffers):

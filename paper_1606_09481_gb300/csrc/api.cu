@@ -60,6 +60,9 @@ struct Layout {
 
 constexpr uint64_t kMaxListEntries = 0x7fffffffull;
 
+// Work mapping of the range query: rhg_params' fields, 0 meaning these defaults.
+constexpr uint32_t kDefaultBatchBudget = 65536, kDefaultCoreHeavy = 4096, kDefaultFringeLimit = 32;
+
 // Eq. 22 (zeta = 1) in plain double arithmetic, for host-side sizing only (the
 // device plan computes the R the graph uses).
 double host_kbar(double R, double n, double a)
@@ -76,6 +79,12 @@ double host_radius_estimate(const rhg_params &p)
 {
     if (p.R_override > 0.0) return p.R_override;
     const double n = static_cast<double>(p.n);
+    // the e^{-R/2} term alone gives R to within a few units; far from the filter's
+    // limits that decides the sizing without the bisection (a batch sizes
+    // thousands of graphs on the host)
+    const double pi = 3.14159265358979323846, xi = p.alpha / (p.alpha - 0.5);
+    const double lead = 2.0 * std::log(2.0 / pi * xi * xi * n / p.k);
+    if (lead < kFilterMaxR - 6.0 && p.alpha * lead < kFilterMaxAlphaR - 6.0 * p.alpha) return lead;
     int j = -1;
     for (int t = 0; t < 256; ++t)
         if (host_kbar(t, n, p.alpha) > p.k) j = t;
@@ -105,6 +114,31 @@ uint64_t fp64_chunk_extra(const rhg_params &p)
     if (!fp64 || !(k > 0.0)) return 0;
     const double extra = std::ceil(static_cast<double>(p.n) * k / 20.0);
     return extra < static_cast<double>(kMaxListEntries) ? static_cast<uint64_t>(extra) : kMaxListEntries;
+}
+
+// Chunk-list entries beyond the defaults' sizing for a graph whose work mapping
+// sends more pieces to the chunk list: every piece pushed holds more candidates
+// than its limit, and the candidates are at most about 1.2 times the n k / 2
+// edges, so each smaller limit L adds 0.6 n k / (L + 1) entries.
+uint64_t mapping_chunk_extra(const rhg_params &p)
+{
+    double k = p.k;
+    if (p.R_override > 0.0) k = host_kbar(p.R_override, static_cast<double>(p.n), p.alpha);
+    if (!(k > 0.0)) return 0;
+    const double nk = 0.6 * static_cast<double>(p.n) * k;
+    double extra = 0.0;
+    if (p.fringe_limit && p.fringe_limit < kDefaultFringeLimit) extra += nk / (p.fringe_limit + 1.0);
+    uint32_t core = p.core_heavy ? p.core_heavy : kDefaultCoreHeavy;
+    if (p.batch_budget && p.batch_budget / 32 < core) core = p.batch_budget / 32 > 64 ? p.batch_budget / 32 : 64;
+    if (core < kDefaultCoreHeavy) extra += nk / (core + 1.0);
+    extra = std::ceil(extra);
+    return extra < static_cast<double>(kMaxListEntries) ? static_cast<uint64_t>(extra) : kMaxListEntries;
+}
+
+uint64_t chunk_extra(const rhg_params &p)
+{
+    const uint64_t e = fp64_chunk_extra(p) + mapping_chunk_extra(p);
+    return e < kMaxListEntries ? e : kMaxListEntries;
 }
 
 Layout make_layout(uint64_t n, uint64_t csr_entries, uint64_t chunk_extra = 0)
@@ -160,6 +194,20 @@ uint32_t default_bands(uint64_t n)
 
 constexpr uint32_t kKnownFlags = RHG_FLAG_FP64_ONLY | RHG_FLAG_VERIFY;
 
+
+PlanArgs with_mapping(PlanArgs pa, uint32_t budget, uint32_t core_heavy, uint32_t fringe)
+{
+    pa.batch_budget = budget ? budget : kDefaultBatchBudget;
+    pa.core_heavy = core_heavy ? core_heavy : kDefaultCoreHeavy;
+    pa.fringe_limit = fringe ? fringe : kDefaultFringeLimit;
+    return pa;
+}
+
+PlanArgs with_mapping(PlanArgs pa, const rhg_params &p)
+{
+    return with_mapping(pa, p.batch_budget, p.core_heavy, p.fringe_limit);
+}
+
 // Host-side validation of rhg_params; fills B and p.
 int check_params(const rhg_params *p, uint32_t *B, double *ratio)
 {
@@ -172,6 +220,10 @@ int check_params(const rhg_params *p, uint32_t *B, double *ratio)
     if (p->num_bands > RHG_MAX_BANDS) return RHG_ERR_INVALID_ARG;
     if (p->band_ratio < 0.0 || !std::isfinite(p->band_ratio)) return RHG_ERR_INVALID_ARG;
     if (p->flags & ~kKnownFlags) return RHG_ERR_INVALID_ARG;
+    if (p->reserved) return RHG_ERR_INVALID_ARG;
+    if (p->batch_budget && (p->batch_budget < 1024 || p->batch_budget > (1u << 24))) return RHG_ERR_INVALID_ARG;
+    if (p->core_heavy && (p->core_heavy < 64 || p->core_heavy > 65536)) return RHG_ERR_INVALID_ARG;
+    if (p->fringe_limit > 32) return RHG_ERR_INVALID_ARG;
     *B = p->num_bands ? p->num_bands : default_bands(p->n);
     *ratio = p->band_ratio > 0.0 ? p->band_ratio : 0.9;
     return RHG_OK;
@@ -351,12 +403,14 @@ int generate(const rhg_params *p, void *d_ws, size_t ws_bytes, Output kind, uint
     if (kind == Output::Pairs && capacity && (!d_pairs || (reinterpret_cast<uintptr_t>(d_pairs) & 7)))
         return RHG_ERR_INVALID_ARG;
     if (kind == Output::Csr && (!d_row_ptr || (capacity && !d_col))) return RHG_ERR_INVALID_ARG;
-    const Layout L = make_layout(p->n, kind == Output::Csr ? capacity : 0, fp64_chunk_extra(*p));
+    const Layout L = make_layout(p->n, kind == Output::Csr ? capacity : 0, chunk_extra(*p));
     if (ws_bytes < L.total) return RHG_ERR_OOM;
     if (reinterpret_cast<uintptr_t>(d_ws) & 255) return RHG_ERR_INVALID_ARG;
     Pipeline pl{d_ws, L, p->n};
-    PlanArgs pa{p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override,
-                (p->flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u, (p->flags & RHG_FLAG_VERIFY) ? 1u : 0u};
+    PlanArgs pa = with_mapping(PlanArgs{p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override,
+                                        (p->flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u,
+                                        (p->flags & RHG_FLAG_VERIFY) ? 1u : 0u},
+                               *p);
     const uint64_t cap_edges = kind == Output::Pairs ? capacity : capacity / 2;
     Meta h;
     Status st = run_pipeline(pl, pa, nullptr, nullptr, kind, d_pairs, cap_edges, &h, stream);
@@ -392,6 +446,9 @@ int generate(const rhg_params *p, void *d_ws, size_t ws_bytes, Output kind, uint
 
 // ------------------------------------------------------------------ batch
 constexpr uint32_t kMaxBatch = 1u << 20;
+// A grid barrier of the persistent batch launch that waits longer than this
+// gives up: the batch then returns RHG_ERR_TIMEOUT instead of hanging the device.
+constexpr uint64_t kBatchTimeoutNs = 20ull * 1000 * 1000 * 1000;
 
 // Host-side tables of a batch (uploaded once per call).
 struct BatchHost {
@@ -407,7 +464,7 @@ struct BatchHost {
 
 struct BatchLayout {
     size_t metas, args, tiles, tile_first, pt_off, idx_base, out_off, tables_end, results, keys0, keys1, ids0, ids1,
-        r_by_pos, akey, id, ang, pms, phi, r, ch, sh, bidx, heavy, recheck, sort_tmp, total;
+        r_by_pos, akey, id, ang, pms, phi, r, ch, sh, bidx, heavy, recheck, sort_tmp, bar, total;
     uint32_t heavy_cap, recheck_cap;
 };
 
@@ -428,8 +485,10 @@ int batch_host(const rhg_params *graphs, uint32_t count, const uint64_t *pair_of
         double ratio;
         const int rc = check_params(&q, &B, &ratio);
         if (rc) return rc;
-        h.args[g] = PlanArgs{q.n, q.k, q.alpha, q.seed, B, ratio, q.R_override,
-                             (q.flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u, (q.flags & RHG_FLAG_VERIFY) ? 1u : 0u};
+        h.args[g] = with_mapping(PlanArgs{q.n, q.k, q.alpha, q.seed, B, ratio, q.R_override,
+                                          (q.flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u,
+                                          (q.flags & RHG_FLAG_VERIFY) ? 1u : 0u},
+                                 q);
         h.tile_first[g] = static_cast<uint32_t>(h.tiles.size());
         for (uint64_t s0 = 0; s0 < q.n; s0 += kTilePoints) {
             const uint64_t c = q.n - s0 < kTilePoints ? q.n - s0 : kTilePoints;
@@ -437,7 +496,7 @@ int batch_host(const rhg_params *graphs, uint32_t count, const uint64_t *pair_of
         }
         pos += q.n;
         idx += index_entries(q.n);
-        h.chunk_extra += fp64_chunk_extra(q);
+        h.chunk_extra += chunk_extra(q);
         if (pos >= 0xFFFFFFFFull || idx >= 0xFFFFFFFFull) return RHG_ERR_INVALID_ARG;  // 32-bit positions
         h.pt_off[g + 1] = static_cast<uint32_t>(pos);
         h.idx_base[g + 1] = static_cast<uint32_t>(idx);
@@ -503,6 +562,7 @@ BatchLayout batch_layout(uint64_t G, uint64_t N, uint64_t num_tiles, uint64_t id
     L.heavy = take(static_cast<size_t>(L.heavy_cap) * 16);
     L.recheck = take(static_cast<size_t>(L.recheck_cap) * 8);
     L.sort_tmp = take(segmented_temp_bytes(static_cast<uint32_t>(num_tiles)));
+    L.bar = take(256);
     L.total = o;
     return L;
 }
@@ -544,39 +604,26 @@ BatchTables batch_tables(void *ws, const BatchLayout &L, uint32_t G, uint64_t nu
     return bt;
 }
 
-// Every stage of the batch on the stream: plan (all graphs), sample, band
-// offsets, segmented sort, gather, bucket index and range query, results.  Only
-// kernel launches (and stage events when timing is on): no host memory, no
-// synchronisation, so the sequence can be captured into a CUDA graph.
+// Every stage of the batch on the stream, in one persistent cooperative launch
+// (plan of all graphs, sampling, band offsets, segmented sort, gather, bucket
+// index, range query, results; launch_batch_persistent).  No host memory and no
+// synchronisation, so the launch can be captured into a CUDA graph.
 Status enqueue_batch(void *ws, const BatchLayout &L, uint32_t G, uint64_t N, uint64_t num_tiles, bool verify,
                      uint32_t *d_pairs, cudaStream_t stream)
 {
-    Status st;
-    Meta *metas = at<Meta>(ws, L.metas);
-    const BatchTables bt = batch_tables(ws, L, G, num_tiles);
-    mark(RHG_STAGE_PLAN, false, stream);
-    st = launch_plan_batch(metas, at<PlanArgs>(ws, L.args), G, stream);
-    if (st.code) return st;
-    mark(RHG_STAGE_PLAN, true, stream);
-    uint64_t *k0 = at<uint64_t>(ws, L.keys0), *k1 = at<uint64_t>(ws, L.keys1);
-    uint32_t *i0 = at<uint32_t>(ws, L.ids0), *i1 = at<uint32_t>(ws, L.ids1);
-    double *rpos = at<double>(ws, L.r_by_pos);
-    mark(RHG_STAGE_SAMPLE, false, stream);
-    st = launch_sample_batch(metas, bt, k0, i0, rpos, stream);
-    if (st.code) return st;
-    mark(RHG_STAGE_SAMPLE, true, stream);
-    mark(RHG_STAGE_SORT, false, stream);
-    st = launch_band_offsets_batch(metas, bt, stream);
-    if (st.code) return st;
-    const int shifts[5] = {0, 8, 16, 24, 32};
-    uint64_t *ks = nullptr;
-    uint32_t *is = nullptr;
-    st = segmented_radix_sort(bt, k0, k1, i0, i1, shifts, 5, at<void>(ws, L.sort_tmp), &ks, &is, stream);
-    if (st.code) return st;
-    mark(RHG_STAGE_SORT, true, stream);
-    SortedPoints P;
+    PersistBuffers b{};
+    b.metas = at<Meta>(ws, L.metas);
+    b.args = at<PlanArgs>(ws, L.args);
+    b.bt = batch_tables(ws, L, G, num_tiles);
+    b.keys0 = at<uint64_t>(ws, L.keys0);
+    b.keys1 = at<uint64_t>(ws, L.keys1);
+    b.ids0 = at<uint32_t>(ws, L.ids0);
+    b.ids1 = at<uint32_t>(ws, L.ids1);
+    b.r_by_pos = at<double>(ws, L.r_by_pos);
+    b.sort_counts = at<uint32_t>(ws, L.sort_tmp);
+    SortedPoints &P = b.P;
     P.n = N;
-    P.key = ks;
+    P.key = kBatchSortPasses % 2 ? b.keys1 : b.keys0;  // where the sort passes leave the keys
     P.akey = at<uint32_t>(ws, L.akey);
     P.id = at<uint32_t>(ws, L.id);
     P.ang = at<float2>(ws, L.ang);
@@ -585,26 +632,16 @@ Status enqueue_batch(void *ws, const BatchLayout &L, uint32_t G, uint64_t N, uin
     P.r = at<double>(ws, L.r);
     P.ch = at<double>(ws, L.ch);
     P.sh = at<double>(ws, L.sh);
-    mark(RHG_STAGE_GATHER, false, stream);
-    st = launch_gather_batch(metas, bt, ks, is, rpos, P, stream);
-    if (st.code) return st;
-    mark(RHG_STAGE_GATHER, true, stream);
-    QueryArgs q{};
-    q.M = metas;
-    q.bt = bt;
-    q.P = P;
-    q.pairs = d_pairs;
-    q.heavy = at<uint4>(ws, L.heavy);
-    q.heavy_cap = L.heavy_cap;
-    q.recheck = at<uint2>(ws, L.recheck);
-    q.recheck_cap = L.recheck_cap;
-    q.bidx = at<uint32_t>(ws, L.bidx);
-    q.verify = verify;
-    mark(RHG_STAGE_QUERY, false, stream);
-    st = launch_query_batch(q, stream);
-    if (st.code) return st;
-    mark(RHG_STAGE_QUERY, true, stream);
-    return launch_batch_results(metas, G, at<uint4>(ws, L.results), stream);
+    b.pairs = d_pairs;
+    b.heavy = at<uint4>(ws, L.heavy);
+    b.heavy_cap = L.heavy_cap;
+    b.recheck = at<uint2>(ws, L.recheck);
+    b.recheck_cap = L.recheck_cap;
+    b.bidx = at<uint32_t>(ws, L.bidx);
+    b.results = at<uint4>(ws, L.results);
+    b.bar = at<uint32_t>(ws, L.bar);
+    b.timeout_ns = kBatchTimeoutNs;
+    return launch_batch_persistent(b, verify, stream);
 }
 
 bool any_verify(const BatchHost &h)
@@ -790,7 +827,7 @@ const char *rhg_status_str(int status)
     }
 }
 
-int rhg_version(void) { return 2; }
+int rhg_version(void) { return 3; }
 
 int rhg_set_stage_events(void *const *events, uint32_t count)
 {
@@ -810,7 +847,7 @@ int rhg_workspace_bytes(const rhg_params *p, uint64_t capacity_entries, size_t *
     const int rc = check_params(p, &B, &ratio);
     if (rc) return rc;
     if (!bytes) return RHG_ERR_INVALID_ARG;
-    *bytes = make_layout(p->n, capacity_entries, fp64_chunk_extra(*p)).total;
+    *bytes = make_layout(p->n, capacity_entries, chunk_extra(*p)).total;
     return RHG_OK;
 }
 
@@ -834,7 +871,7 @@ int rhg_plan(const rhg_params *p, void *d_workspace, size_t workspace_bytes, voi
     if (workspace_bytes < sizeof(Meta)) return RHG_ERR_OOM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Meta *d = static_cast<Meta *>(d_workspace);
-    const PlanArgs pa{p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override, 1u, 0u};
+    const PlanArgs pa = with_mapping(PlanArgs{p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override, 1u, 0u}, *p);
     const Status st = launch_plan(d, pa, s);
     if (st.code) return st.code;
     Meta h;
@@ -871,7 +908,7 @@ int rhg_sample_points(const rhg_params *p, void *d_workspace, size_t workspace_b
     if (workspace_bytes < sizeof(Meta)) return RHG_ERR_OOM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Meta *M = static_cast<Meta *>(d_workspace);
-    const PlanArgs pa{p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override, 1u, 0u};
+    const PlanArgs pa = with_mapping(PlanArgs{p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override, 1u, 0u}, *p);
     Status st = launch_plan(M, pa, s);
     if (st.code) return st.code;
     st = launch_points_by_id(M, p->n, p->seed, d_phi, d_r, s);
@@ -942,8 +979,9 @@ int rhg_edges_from_points(const double *d_phi, const double *d_r, uint64_t n, do
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Pipeline pl{d_workspace, L, n};
     // alpha and k only enter the sampler and the R solve, which are not used here
-    const PlanArgs pa{n, 1.0, 1.0, 0, B, ratio, R, (flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u,
-                      (flags & RHG_FLAG_VERIFY) ? 1u : 0u};
+    const PlanArgs pa = with_mapping(PlanArgs{n, 1.0, 1.0, 0, B, ratio, R, (flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u,
+                                              (flags & RHG_FLAG_VERIFY) ? 1u : 0u},
+                                     0, 0, 0);
     Meta h;
     const Status st = run_pipeline(pl, pa, d_phi, d_r, Output::Pairs, d_pairs, capacity_edges, &h, s);
     if (st.code) return finish(st, result);
@@ -958,7 +996,7 @@ int rhg_generate_pairs_static(const rhg_params *p, uint32_t *d_pairs, uint64_t c
 {
     if (result) std::memset(result, 0, sizeof(*result));
     if (!p || p->n > RHG_STATIC_MAX_POINTS) return RHG_ERR_INVALID_ARG;
-    const size_t need = make_layout(p->n, 0, fp64_chunk_extra(*p)).total;
+    const size_t need = make_layout(p->n, 0, chunk_extra(*p)).total;
     if (need > RHG_STATIC_SCRATCH_BYTES) return RHG_ERR_INVALID_ARG;
     void *ws = nullptr;
     cudaError_t err = cudaSuccess;
@@ -1080,6 +1118,45 @@ int rhg_batch_read_results(const rhg_batch_plan *plan, const void *d_workspace, 
     return fill_batch_results(count, res.data(), ctl, out_off.data(), results, totals);
 }
 
+int rhg_batch_stage_times(const rhg_batch_plan *plan, const void *d_workspace, void *stream, double *ms,
+                          uint32_t count)
+{
+    BatchLayout L;
+    if (!plan_layout(plan, L) || !d_workspace || !ms || count < RHG_BATCH_STAGE_COUNT) return RHG_ERR_INVALID_ARG;
+    static_assert(RHG_BATCH_STAGE_COUNT + 1 == kBatchStages, "one duration between consecutive stage marks");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Meta ctl;
+    const char *ws = static_cast<const char *>(d_workspace);
+    if (cudaMemcpyAsync(&ctl, ws + L.metas + plan->count * sizeof(Meta), sizeof(Meta), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return RHG_ERR_CUDA;
+    for (uint32_t k = 0; k < RHG_BATCH_STAGE_COUNT; ++k)
+        ms[k] = ctl.stage_ns[k + 1] > ctl.stage_ns[k] ? 1e-6 * static_cast<double>(ctl.stage_ns[k + 1] - ctl.stage_ns[k])
+                                                       : 0.0;
+    return RHG_OK;
+}
+
+int rhg_grid_barrier_test(uint32_t missing, uint64_t timeout_ns, void *d_workspace, size_t workspace_bytes,
+                          void *stream)
+{
+    if (!d_workspace || missing > 1024 || timeout_ns == 0 || timeout_ns > 10ull * 1000 * 1000 * 1000)
+        return RHG_ERR_INVALID_ARG;
+    if (workspace_bytes < align_up(sizeof(Meta)) + 256) return RHG_ERR_OOM;
+    if (reinterpret_cast<uintptr_t>(d_workspace) & 255) return RHG_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Meta *M = static_cast<Meta *>(d_workspace);
+    uint32_t *bar = at<uint32_t>(d_workspace, align_up(sizeof(Meta)));
+    if (cudaMemsetAsync(M, 0, sizeof(Meta), s) != cudaSuccess) return RHG_ERR_CUDA;
+    const Status st = launch_barrier_test(M, bar, missing, timeout_ns, s);
+    if (st.code) return st.code;
+    uint32_t err = 0;
+    if (cudaMemcpyAsync(&err, &M->error, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return RHG_ERR_CUDA;
+    return error_from_meta(err);
+}
+
 int rhg_draw_movement(uint64_t n, uint64_t seed, double phi_lo, double phi_hi, double r_lo, double r_hi,
                       double *d_tau_phi, double *d_tau_r, void *stream)
 {
@@ -1130,7 +1207,8 @@ int rhg_update_edges(const double *d_phi, const double *d_r, uint64_t n, double 
     if (workspace_bytes < U.total) return RHG_ERR_OOM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double ratio = band_ratio > 0.0 ? band_ratio : 0.9;
-    const PlanArgs pa{n, 1.0, 1.0, 0, B, ratio, R, (flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u, 0u};
+    const PlanArgs pa =
+        with_mapping(PlanArgs{n, 1.0, 1.0, 0, B, ratio, R, (flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u, 0u}, 0, 0, 0);
     Pipeline pl{d_workspace, U.L, n};
     Meta *M = pl.meta();
     SortedPoints P;

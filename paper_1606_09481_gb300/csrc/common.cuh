@@ -19,6 +19,7 @@ constexpr uint32_t kBucketPoints = 1;
 __host__ __device__ constexpr uint64_t index_entries(uint64_t n) { return n / kBucketPoints + 3 * kMaxBands + 1; }
 constexpr int kExpTab = 64;  // e^k table for k = -64..64 (FP32 filter values)
 constexpr uint32_t kClaimCounters = 16;  // work-claim counters of the range query (Meta::claim)
+constexpr int kMaxStageMarks = 32;       // stage timestamps of the persistent batch launch
 
 // ---------------------------------------------------------------------------
 // FP32 filter: error model.  The filter evaluates X = L / cosh R in the
@@ -60,6 +61,7 @@ struct Meta {
     float band_Po[kMaxBands + 1], band_Mo[kMaxBands + 1], band_So[kMaxBands + 1];  // at the outer radius
     float etab[2 * kExpTab + 1];    // e^k rounded to float
     uint32_t B;
+    uint32_t batch_budget, core_heavy, fringe_limit;  // work mapping of the range query
     uint32_t error;          // nonzero: a device-side check failed (see kErr*)
     uint32_t filter;         // 1: FP32 filter + FP64 recheck; 0: FP64 predicate per candidate
     uint32_t verify;         // 1: check every filter decision against the FP64 predicate
@@ -79,6 +81,9 @@ struct Meta {
     // c, c + kClaimCounters, ... (one counter per 128-byte line, so that the claims
     // of different warps do not queue on one address)
     uint32_t claim[kClaimCounters * 32];
+    // persistent batch launch (control block): the device time (globaltimer, ns)
+    // at the start and after each stage's grid barrier
+    uint64_t stage_ns[kMaxStageMarks];
 };
 
 // device-side error codes (Meta::error)

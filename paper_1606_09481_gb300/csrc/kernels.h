@@ -14,6 +14,7 @@ struct PlanArgs {
     double R_override;
     uint32_t allow_filter;  // FP32 filter permitted (the plan still requires R, alpha R in range)
     uint32_t verify;        // check every filter decision against the FP64 predicate
+    uint32_t batch_budget, core_heavy, fringe_limit;  // work mapping of the range query (resolved, nonzero)
 };
 
 // Sorted, structure-of-arrays view of the points: position p is the p-th point in
@@ -86,15 +87,6 @@ Status launch_dm_eval(int fn, const double *in, double *out, uint64_t count, cud
 Status launch_points_by_id(const Meta *d_meta, uint64_t n, uint64_t seed, double *phi, double *r,
                            cudaStream_t stream);
 
-// batch versions (rhg_generate_batch): one launch each for all graphs
-Status launch_plan_batch(Meta *metas, const PlanArgs *d_args, uint32_t G, cudaStream_t stream);
-Status launch_sample_batch(Meta *metas, const BatchTables &bt, uint64_t *keys, uint32_t *ids, double *r_by_pos,
-                           cudaStream_t stream);
-Status launch_band_offsets_batch(Meta *metas, const BatchTables &bt, cudaStream_t stream);
-Status launch_gather_batch(const Meta *metas, const BatchTables &bt, const uint64_t *sorted_keys,
-                           const uint32_t *sorted_ids, const double *r_by_pos, SortedPoints P, cudaStream_t stream);
-// per-graph results: {m, R bits, B | error << 32, 0}
-Status launch_batch_results(const Meta *metas, uint32_t G, uint4 *d_out, cudaStream_t stream);
 
 // ---- sort.cu ----
 // LSD radix sort of 64-bit keys (optionally with uint32 values) over the 8-bit
@@ -105,12 +97,9 @@ Status radix_sort(uint64_t n, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals
                   uint32_t *vals_alt, const int *shifts, int num_shifts, void *temp,
                   uint64_t **keys_out, uint32_t **vals_out, cudaStream_t stream);
 
-// Segmented version for a batch: every graph's positions are sorted among
-// themselves (tiles of kTilePoints positions, per-tile digit counts).
+// Temporary storage of the segmented sort of a batch (tiles of one graph each;
+// the sort itself runs inside the persistent batch launch).
 size_t segmented_temp_bytes(uint32_t num_tiles);
-Status segmented_radix_sort(const BatchTables &bt, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals,
-                            uint32_t *vals_alt, const int *shifts, int num_shifts, void *temp, uint64_t **keys_out,
-                            uint32_t **vals_out, cudaStream_t stream);
 
 // ---- query.cu ----
 // Range query (Alg. 1): windows, search, candidate test, output; then the heavy
@@ -118,8 +107,43 @@ Status segmented_radix_sort(const BatchTables &bt, uint64_t *keys, uint64_t *key
 // so the pair order is unspecified; Meta::m is the exact edge count.  The kernels
 // of both modes are launched; each returns at once unless Meta::filter selects it.
 Status launch_query(const QueryArgs &a, bool csr, cudaStream_t stream);
-// The same for a batch (pairs only): per-graph windows, outputs and counters.
-Status launch_query_batch(const QueryArgs &a, cudaStream_t stream);
+// The whole batch in one persistent, cooperative launch: plan, sampling, band
+// offsets, the segmented radix sort, gather, bucket index, both query phases and
+// the per-graph results, separated by grid barriers whose waits give up after
+// timeout_ns (the control block's error becomes kErrTimeout).  bar: 256 bytes of
+// device memory, cleared here before the launch.  The caller's stage events
+// cannot bracket stages inside one kernel; the control block records the device
+// time of each stage instead (Meta::stage_ns, kBatchStageMarks entries).
+struct PersistBuffers {
+    Meta *metas;                 // G + 1 blocks (control block last)
+    const PlanArgs *args;        // G
+    BatchTables bt;
+    uint64_t *keys0, *keys1;     // sort key double buffer
+    uint32_t *ids0, *ids1;       // id double buffer
+    double *r_by_pos;            // FP64 radius by position (FP64 mode)
+    uint32_t *sort_counts;       // segmented_temp_bytes(num_tiles)
+    SortedPoints P;              // gather output (P.key: the sorted keys)
+    uint32_t *pairs;
+    uint4 *heavy;
+    uint32_t heavy_cap;
+    uint2 *recheck;
+    uint32_t recheck_cap;
+    uint32_t *bidx;
+    uint4 *results;              // 2 G
+    uint32_t *bar;               // grid barrier words
+    uint64_t timeout_ns;
+};
+// stage marks a persistent launch records: start, plan, sampling, band offsets,
+// 5 sort passes x (counts, scan, scatter), gather, bucket index, filter-mode
+// query, its heavy chunks, rechecks, phase reset, FP64-mode query, its heavy
+// chunks, results (the last mark is CTA 0's end)
+constexpr int kBatchStages = 28;
+constexpr int kBatchSortPasses = 5;
+Status launch_batch_persistent(const PersistBuffers &b, bool verify, cudaStream_t stream);
+// One grid barrier on its own, for the test of the timeout: `missing` CTAs more
+// than the launch has are expected, so with missing > 0 every wait runs out.
+Status launch_barrier_test(Meta *C, uint32_t *bar, uint32_t missing, uint64_t timeout_ns, cudaStream_t stream);
+
 // Bucket index alone (the subset query needs it without the full query).
 Status launch_bucket_index(const QueryArgs &a, cudaStream_t stream);
 // Neighbours of the moved vertices (dynamic model): counts (emit = false) or

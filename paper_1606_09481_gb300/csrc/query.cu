@@ -24,6 +24,7 @@
 // predicate itself; undecided pairs are queued and the third kernel evaluates the
 // FP64 predicate on them.  FP64 mode tests every candidate with the FP64 predicate.
 #include "kernels.h"
+#include "stages.cuh"
 
 namespace rhg {
 namespace {
@@ -31,8 +32,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kChunk = 4096;      // candidates per heavy chunk
-constexpr uint32_t kCoreHeavy = 4096;  // core ranges longer than this become core chunks
-constexpr uint32_t kBatchBudget = 65536;  // candidates a warp batch keeps; beyond, ranges become chunks
 constexpr int kListCap = 64;           // queued fringe entries per warp (>= 2 per lane)
 constexpr int kBitWords = 128;         // decision words per warp: kChunk / 32
 constexpr uint32_t kFull = 0x80000000u;  // window half-width meaning "whole band"
@@ -78,6 +77,7 @@ struct BandShared {
     float PMn[kMaxBands + 1];
     double c[kMaxBands + 1], sinh_c[kMaxBands + 1], cosh_c[kMaxBands + 1];
     uint32_t ioff[kMaxBands + 1], ishift[kMaxBands + 1];  // bucket index of each band
+    uint32_t budget, core_heavy, fringe_limit;              // work mapping (Meta)
 };
 
 __device__ __forceinline__ void load_bands_from(BandShared &S, const Meta *M, int first, int stride)
@@ -96,6 +96,11 @@ __device__ __forceinline__ void load_bands_from(BandShared &S, const Meta *M, in
         S.cosh_c[j] = M->cosh_c[j];
         S.ioff[j] = M->idx_off[j];
         S.ishift[j] = j < kMaxBands ? M->idx_shift[j] : 32u;
+    }
+    if (first == 0) {
+        S.budget = M->batch_budget;
+        S.core_heavy = M->core_heavy;
+        S.fringe_limit = M->fringe_limit;
     }
 }
 
@@ -710,10 +715,8 @@ __device__ __forceinline__ int decide_stream(const QueryArgs &a, const Meta *Mg,
 // go to the graph's output region and counter; lists and work counters live in
 // the control block.
 template <bool kFilter, bool kCsr, bool kMulti, bool kVerify>
-__global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryArgs a)
+__device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, BatchSmem<kFilter> *Wsm)
 {
-    __shared__ BandShared Sm[kMulti ? kWarps : 1];
-    __shared__ BatchSmem<kFilter> Wsm[kWarps];
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     BandShared &S = Sm[kMulti ? (threadIdx.x >> 5) : 0];
@@ -847,17 +850,17 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryA
                 if (f3 < f2) f3 = f2;
                 if (c1 < c0) c1 = c0;
                 cand += (f1 - f0) + (f3 - f2) + (c1 - c0);
-                // a lane keeps at most 32 + 32 fringe candidates; a batch keeps
-                // about kBatchBudget candidates; longer ranges become chunks that
-                // every warp shares
-                const uint32_t room = kept < kBatchBudget ? (kBatchBudget - kept) / 32 : 0;
-                const uint32_t hc = kCoreHeavy < (room > 64 ? room : 64) ? kCoreHeavy : (room > 64 ? room : 64);
+                // a lane keeps at most fringe_limit (<= 32) candidates of each of its
+                // two fringe pieces; a batch keeps about the budget's candidates;
+                // longer ranges become chunks that every warp shares
+                const uint32_t room = kept < S.budget ? (S.budget - kept) / 32 : 0;
+                const uint32_t hc = S.core_heavy < (room > 64 ? room : 64) ? S.core_heavy : (room > 64 ? room : 64);
                 const uint32_t gtag = kMulti ? cur_g << 1 : 0u;
-                if (f1 - f0 > 32) {
+                if (f1 - f0 > S.fringe_limit) {
                     push_heavy(a, C, p, f0, f1, gtag);
                     f1 = f0;
                 }
-                if (f3 - f2 > 32) {
+                if (f3 - f2 > S.fringe_limit) {
                     push_heavy(a, C, p, f2, f3, gtag);
                     f3 = f2;
                 }
@@ -970,12 +973,19 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryA
     flush_diag(C, near);
 }
 
+template <bool kFilter, bool kCsr, bool kMulti, bool kVerify>
+__global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryArgs a)
+{
+    __shared__ BandShared Sm[kMulti ? kWarps : 1];
+    __shared__ BatchSmem<kFilter> Wsm[kWarps];
+    batch_body<kFilter, kCsr, kMulti, kVerify>(a, Sm, Wsm);
+}
+
 // Heavy chunks: one warp per chunk of at most kChunk candidates of one owner,
 // tested (type 0) or a core chunk of certain edges (type 1).
 template <bool kFilter, bool kCsr, bool kMulti, bool kVerify>
-__global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
+__device__ __forceinline__ void heavy_body(const QueryArgs &a, WarpSmem *Wsm)
 {
-    __shared__ WarpSmem Wsm[kWarps];
     Meta *C = kMulti ? a.M + a.bt.G : a.M;
     if (C->error || (!kMulti && (C->filter != 0) != kFilter)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1011,6 +1021,13 @@ __global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
         __syncwarp();
     }
     flush_diag(C, near);
+}
+
+template <bool kFilter, bool kCsr, bool kMulti, bool kVerify>
+__global__ void __launch_bounds__(kThreads) heavy_kernel(QueryArgs a)
+{
+    __shared__ WarpSmem Wsm[kWarps];
+    heavy_body<kFilter, kCsr, kMulti, kVerify>(a, Wsm);
 }
 
 // FP64 recheck of the pairs the filter left undecided: the predicate of Eq. 3 on
@@ -1054,8 +1071,8 @@ __global__ void __launch_bounds__(kThreads) recheck_kernel(QueryArgs a)
 }
 
 // Batch recheck: each pair's graph from the owner position; one output slot per
-// edge from the graph's counter (the pairs are few).
-__global__ void __launch_bounds__(kThreads) recheck_batch_kernel(QueryArgs a)
+// edge from the graph's counter (the pairs are few).  Grid-stride over the list.
+__device__ __forceinline__ void recheck_batch_body(const QueryArgs &a)
 {
     Meta *C = a.M + a.bt.G;
     if (C->error) return;
@@ -1090,7 +1107,7 @@ __global__ void __launch_bounds__(kThreads) recheck_batch_kernel(QueryArgs a)
 
 // Between the filter and the FP64 phase of a batch: the work counters and the
 // heavy list start again (the recheck list and the statistics carry over).
-__global__ void reset_phase_kernel(Meta *C)
+__device__ __forceinline__ void reset_phase(Meta *C)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         C->work_counter = 0;
@@ -1099,6 +1116,7 @@ __global__ void reset_phase_kernel(Meta *C)
         C->heavy_next = 0;
     }
 }
+
 
 // ------------------------------------------------------------------ subset query
 // Neighbours of the moved vertices (dynamic model, Sec. III-C), for the update of
@@ -1355,11 +1373,11 @@ __global__ void __launch_bounds__(kThreads) bucket_index_kernel(const Meta *M, c
     }
 }
 
-// Batch: CTA per tile, the tile's graph's bands and index region.
-__global__ void __launch_bounds__(kThreads) bucket_index_batch_kernel(const Meta *metas, BatchTables bt,
-                                                                       const uint64_t *keys, uint32_t *idx)
+// Batch: tile t (one CTA), the tile's graph's bands and index region.
+__device__ __forceinline__ void bucket_index_tile(const Meta *metas, const BatchTables &bt, const uint64_t *keys,
+                                                  uint32_t *idx, uint32_t t)
 {
-    const uint4 T = bt.tiles[blockIdx.x];
+    const uint4 T = bt.tiles[t];
     const Meta *M = metas + T.x;
     if (M->error || metas[bt.G].error) return;
     const uint32_t B = M->B;
@@ -1386,6 +1404,154 @@ __global__ void __launch_bounds__(kThreads) bucket_index_batch_kernel(const Meta
             for (uint32_t j = cur + 1; j <= nb; ++j) idx[off + j] = static_cast<uint32_t>(e);
         }
     }
+}
+
+// ------------------------------------------------------------ persistent batch
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier of a cooperative launch: every CTA arrives on bar[0]; the last one
+// resets it and advances the generation bar[32]; the others wait for the
+// generation to change.  A wait gives up after timeout_ns of device time, records
+// kErrTimeout in C->error and returns false (so does every CTA that returns
+// early: the caller stops).  All threads of the CTA call it.
+__device__ bool grid_sync(uint32_t *bar, uint32_t expected, uint64_t timeout_ns, Meta *C)
+{
+    __shared__ int passed;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t *gen = bar + 32;
+        const uint32_t g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) + 1u == expected) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 32, 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (*gen == g) {
+                if (global_ns() - t0 > timeout_ns) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+        if (!ok) atomicMax(&C->error, kErrTimeout);
+        passed = ok;
+    }
+    __syncthreads();
+    return passed != 0;
+}
+
+// Shared memory of the persistent kernel: one stage at a time.
+union PersistSmem {
+    stg::PlanSmem plan;
+    stg::SampleSmem sample;
+    uint32_t hist[stg::kRadix];
+    uint32_t warp_sum[stg::kWarps];
+    struct {
+        stg::TileSmem sm;
+        uint32_t sval[stg::kTile];
+    } down;
+    float etab[2 * kExpTab + 1];
+    struct {
+        BandShared S[kWarps];
+        BatchSmem<true> W[kWarps];
+    } qf;
+    struct {
+        BandShared S[kWarps];
+        BatchSmem<false> W[kWarps];
+    } qd;
+    WarpSmem heavy[kWarps];
+};
+
+constexpr int kPersistMinBlocks = 3;
+
+// The whole batch in one launch (see launch_batch_persistent): stage after stage,
+// each spread over all CTAs (tiles and graphs handed out round robin, the range
+// query's warp batches from its work counters), separated by grid_sync.
+template <bool kVerify>
+__global__ void __launch_bounds__(kThreads, kPersistMinBlocks) batch_persistent_kernel(PersistBuffers b, QueryArgs q)
+{
+    extern __shared__ __align__(16) unsigned char persist_smem[];
+    PersistSmem &U = *reinterpret_cast<PersistSmem *>(persist_smem);
+    const BatchTables &bt = b.bt;
+    const uint32_t G = bt.G, tiles = bt.num_tiles, nblocks = gridDim.x;
+    Meta *C = b.metas + G;
+    int mark = 0;
+    auto sync = [&]() -> bool {
+        if (!grid_sync(b.bar, nblocks, b.timeout_ns, C)) return false;
+        ++mark;
+        if (blockIdx.x == 0 && threadIdx.x == 0 && mark < kMaxStageMarks) C->stage_ns[mark] = global_ns();
+        return true;
+    };
+    const uint64_t t_start = global_ns();
+    // plan (one CTA per graph; the last item clears the control block)
+    for (uint32_t vb = blockIdx.x; vb <= G; vb += nblocks) stg::plan_batch_item(b.metas, b.args, G, vb, U.plan);
+    if (!sync()) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) C->stage_ns[0] = t_start;  // after the plan cleared the block
+    for (uint32_t vb = blockIdx.x; vb < tiles; vb += nblocks)
+        stg::sample_tile(b.metas, bt, b.keys0, b.ids0, b.r_by_pos, vb, U.sample);
+    if (!sync()) return;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += nblocks * blockDim.x)
+        stg::band_offsets_one(b.metas + g, bt.pt_off[g], bt.idx_base[g]);
+    if (!sync()) return;
+    // segmented radix sort of (band << 32 | angle key) with the ids, 8-bit digits
+    uint64_t *kin = b.keys0, *kout = b.keys1;
+    uint32_t *vin = b.ids0, *vout = b.ids1;
+    for (int pass = 0; pass < kBatchSortPasses; ++pass) {
+        const int shift = 8 * pass;
+        for (uint32_t vb = blockIdx.x; vb < tiles; vb += nblocks)
+            stg::seg_upsweep_tile(kin, bt, shift, b.sort_counts, vb, U.hist);
+        if (!sync()) return;
+        for (uint32_t vb = blockIdx.x; vb < G; vb += nblocks) stg::seg_scan_graph(bt, b.sort_counts, vb, U.warp_sum);
+        if (!sync()) return;
+        for (uint32_t vb = blockIdx.x; vb < tiles; vb += nblocks)
+            stg::seg_downsweep_tile<true>(kin, kout, vin, vout, bt, shift, b.sort_counts, vb, U.down.sm, U.down.sval);
+        if (!sync()) return;
+        uint64_t *tk = kin;
+        kin = kout;
+        kout = tk;
+        uint32_t *tv = vin;
+        vin = vout;
+        vout = tv;
+    }
+    // gather (a tile's graph is in filter or in FP64 mode: one of the two writes)
+    for (uint32_t vb = blockIdx.x; vb < tiles; vb += nblocks) {
+        stg::gather_filter_tile(b.metas, bt, kin, vin, b.P, vb, U.etab);
+        stg::gather_fp64_tile(b.metas, bt, kin, vin, b.r_by_pos, b.P, vb);
+    }
+    if (!sync()) return;
+    for (uint32_t vb = blockIdx.x; vb < tiles; vb += nblocks) bucket_index_tile(b.metas, bt, kin, b.bidx, vb);
+    if (!sync()) return;
+    // range query: the filter graphs, then the FP64 graphs
+    batch_body<true, false, true, kVerify>(q, U.qf.S, U.qf.W);
+    if (!sync()) return;
+    heavy_body<true, false, true, kVerify>(q, U.heavy);
+    if (!sync()) return;
+    recheck_batch_body(q);
+    if (!sync()) return;
+    reset_phase(C);
+    if (!sync()) return;
+    batch_body<false, false, true, kVerify>(q, U.qd.S, U.qd.W);
+    if (!sync()) return;
+    heavy_body<false, false, true, kVerify>(q, U.heavy);
+    if (!sync()) return;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += nblocks * blockDim.x)
+        stg::batch_result_one(b.metas, g, b.results);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && mark + 1 < kMaxStageMarks) C->stage_ns[mark + 1] = global_ns();
+}
+
+__global__ void barrier_test_kernel(Meta *C, uint32_t *bar, uint32_t expected, uint64_t timeout_ns)
+{
+    grid_sync(bar, expected, timeout_ns, C);
 }
 
 template <typename K>
@@ -1416,8 +1582,7 @@ Status run(const QueryArgs &a, cudaStream_t stream)
     else heavy_kernel<kFilter, kCsr, kMulti, false><<<static_cast<unsigned>(grid_h), kThreads, 0, stream>>>(a);
     RHG_LAUNCH_CHECK();
     if (kFilter) {
-        if (kMulti) recheck_batch_kernel<<<static_cast<unsigned>(num_sms() * 4), kThreads, 0, stream>>>(a);
-        else recheck_kernel<kCsr><<<static_cast<unsigned>(num_sms() * 4), kThreads, 0, stream>>>(a);
+        recheck_kernel<kCsr><<<static_cast<unsigned>(num_sms() * 4), kThreads, 0, stream>>>(a);
         RHG_LAUNCH_CHECK();
     }
     return st;
@@ -1438,19 +1603,6 @@ Status launch_query(const QueryArgs &a, bool csr, cudaStream_t stream)
     st = csr ? run<true, true, false>(a, stream) : run<true, false, false>(a, stream);
     if (st.code) return st;
     return csr ? run<false, true, false>(a, stream) : run<false, false, false>(a, stream);
-}
-
-Status launch_query_batch(const QueryArgs &a, cudaStream_t stream)
-{
-    Status st;
-    if (!a.bt.num_tiles) return st;
-    bucket_index_batch_kernel<<<a.bt.num_tiles, kThreads, 0, stream>>>(a.M, a.bt, a.P.key, a.bidx);
-    RHG_LAUNCH_CHECK();
-    st = run<true, false, true>(a, stream);
-    if (st.code) return st;
-    reset_phase_kernel<<<1, 32, 0, stream>>>(a.M + a.bt.G);
-    RHG_LAUNCH_CHECK();
-    return run<false, false, true>(a, stream);
 }
 
 Status launch_bucket_index(const QueryArgs &a, cudaStream_t stream)
@@ -1496,6 +1648,63 @@ Status launch_subset_query(const QueryArgs &a, const uint32_t *owners, uint64_t 
         RHG_LAUNCH_CHECK();
         subset_chunk_kernel<false, false><<<gw, kThreads, 0, stream>>>(a, sa);
     }
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+namespace {
+
+template <bool kVerify>
+Status persistent_launch(const PersistBuffers &b, cudaStream_t stream)
+{
+    Status st;
+    auto kernel = batch_persistent_kernel<kVerify>;
+    const int smem = static_cast<int>(sizeof(PersistSmem));
+    static std::atomic<int> grid_cache{0};  // filled once; racing threads agree
+    int grid = grid_cache.load(std::memory_order_relaxed);
+    if (!grid) {
+        RHG_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int per_sm = 0;
+        RHG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem));
+        grid = (per_sm > 0 ? per_sm : 1) * num_sms();
+        grid_cache.store(grid, std::memory_order_relaxed);
+    }
+    QueryArgs q{};
+    q.M = b.metas;
+    q.bt = b.bt;
+    q.P = b.P;
+    q.pairs = b.pairs;
+    q.heavy = b.heavy;
+    q.heavy_cap = b.heavy_cap;
+    q.recheck = b.recheck;
+    q.recheck_cap = b.recheck_cap;
+    q.bidx = b.bidx;
+    q.verify = kVerify;
+    void *args[] = {const_cast<PersistBuffers *>(&b), &q};
+    RHG_CUDA_TRY(cudaMemsetAsync(b.bar, 0, 256, stream));
+    RHG_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(kernel), dim3(grid), dim3(kThreads), args,
+                                             smem, stream));
+    RHG_LAUNCH_CHECK();
+    return st;
+}
+
+}  // namespace
+
+Status launch_batch_persistent(const PersistBuffers &b, bool verify, cudaStream_t stream)
+{
+    if (b.bt.num_tiles == 0 || b.bt.G == 0) return Status{};
+    return verify ? persistent_launch<true>(b, stream) : persistent_launch<false>(b, stream);
+}
+
+Status launch_barrier_test(Meta *C, uint32_t *bar, uint32_t missing, uint64_t timeout_ns, cudaStream_t stream)
+{
+    Status st;
+    const int grid = 2 * num_sms();  // two CTAs of 32 threads per SM are always co-resident
+    const uint32_t expected = static_cast<uint32_t>(grid) + missing;
+    void *args[] = {&C, &bar, const_cast<uint32_t *>(&expected), &timeout_ns};
+    RHG_CUDA_TRY(cudaMemsetAsync(bar, 0, 256, stream));
+    RHG_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(barrier_test_kernel), dim3(grid), dim3(32),
+                                             args, 0, stream));
     RHG_LAUNCH_CHECK();
     return st;
 }

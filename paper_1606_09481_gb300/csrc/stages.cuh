@@ -1,0 +1,550 @@
+// stages.cuh -- device bodies of the point pipeline's stages that both the
+// per-stage kernels and the persistent batch kernel run: the plan (R and band
+// boundaries, Sec. III-A/B), sampling (Alg. 1 sampling step, Eq. 1), band
+// offsets, the filter values and gathers, the stable radix-sort tile passes
+// (Alg. 1, angular sort within each band) and the per-graph results.  A body that
+// works on one tile or graph takes its index and its shared memory from the
+// caller, so that one CTA can run several items one after another.
+#pragma once
+#include "kernels.h"
+
+namespace rhg {
+namespace {
+namespace stg {
+
+using dm::add;
+using dm::div;
+using dm::mul;
+using dm::sub;
+
+// Eq. 22 of Krioukov et al. with zeta = 1 (Sec. III-B), in the fixed operation order
+// of the deterministic definition:
+//   kbar = ((2/pi) xi^2 n) * (e^{-R/2} + e^{-alpha R} ((alpha R / 2) inner - 1)),
+//   inner = (pi/4)/alpha^2 - (pi-1)/alpha + (pi-2),  xi = alpha/(alpha - 1/2).
+__device__ double kbar(double R, double nd, double alpha)
+{
+    const double xi = div(alpha, sub(alpha, 0.5));
+    const double pre = mul(mul(div(2.0, dm::kPi), mul(xi, xi)), nd);
+    const double e1 = dm::exp(-mul(R, 0.5));
+    const double e2 = dm::exp(-mul(alpha, R));
+    const double ta = mul(mul(dm::kPi, 0.25), div(1.0, mul(alpha, alpha)));
+    const double tb = div(sub(dm::kPi, 1.0), alpha);
+    const double inner = add(sub(ta, tb), sub(dm::kPi, 2.0));
+    const double br = sub(mul(mul(mul(alpha, R), 0.5), inner), 1.0);
+    return mul(pre, add(e1, mul(e2, br)));
+}
+
+constexpr int kPlanThreads = 256;  // grid points j = 0..255 of the bracket search
+
+// Shared state of plan_block.
+struct PlanSmem {
+    double R_sh, lo_sh, hi_sh;
+    int jstar, fail, walk_done;
+    uint8_t above[kPlanThreads];  // node t of a round's tree: kbar(its midpoint) > k
+};
+
+// R, boundaries and the band constants of one graph, by one CTA of kPlanThreads.
+// depth: bisection steps taken per round (2^depth - 1 speculative evaluations;
+// 8 when one graph wants the lowest latency, fewer when many graphs share the
+// FP64 units).  All threads of the CTA call it (it synchronises the CTA).
+__device__ void plan_block(Meta *M, const PlanArgs &a, int depth, PlanSmem &PS)
+{
+    int &jstar = PS.jstar;
+    double &R_sh = PS.R_sh, &lo_sh = PS.lo_sh, &hi_sh = PS.hi_sh;
+    int &fail = PS.fail, &walk_done = PS.walk_done;
+    uint8_t *above = PS.above;
+    const int t = threadIdx.x;
+    const double nd = static_cast<double>(a.n);
+    const double alpha = a.alpha, k = a.k;
+    if (t == 0) {
+        jstar = -1;
+        fail = 0;
+        R_sh = a.R_override;
+    }
+    __syncthreads();
+    if (!(a.R_override > 0.0)) {
+        // bracket: the largest integer grid point j with kbar(j) > k
+        if (kbar(static_cast<double>(t), nd, alpha) > k) atomicMax(&jstar, t);
+        __syncthreads();
+        if (t == 0) {
+            fail = (jstar < 0 || jstar == kPlanThreads - 1) ? 1 : 0;
+            walk_done = fail;
+            lo_sh = static_cast<double>(jstar);
+            hi_sh = static_cast<double>(jstar + 1);
+        }
+        __syncthreads();
+        // binary search: mid = (lo + hi) / 2, kbar(mid) > k ? lo = mid : hi = mid, until
+        // lo and hi are adjacent (at most 200 steps); R = hi.  Each round takes
+        // `depth` steps at once: thread t (heap order, root 1) replays the path its
+        // index spells from (lo, hi) and evaluates kbar at its midpoint, then thread
+        // 0 follows the comparisons: the same midpoints and decisions as one step
+        // at a time.
+        const int nodes = 1 << depth;
+        int steps = 0;
+        for (int round = 0; round < 200; ++round) {
+            if (walk_done) break;
+            if (t >= 1 && t < nodes) {
+                double lo = lo_sh, hi = hi_sh;
+                const int depth = 31 - __clz(t);
+                bool live = true;
+                for (int d = depth - 1; d >= 0 && live; --d) {
+                    const double mid = mul(add(lo, hi), 0.5);
+                    if (mid == lo || mid == hi) live = false;
+                    else if ((t >> d) & 1) lo = mid;
+                    else hi = mid;
+                }
+                uint8_t b = 0;
+                if (live) {
+                    const double mid = mul(add(lo, hi), 0.5);
+                    if (mid != lo && mid != hi) b = kbar(mid, nd, alpha) > k ? 1 : 0;
+                }
+                above[t] = b;
+            }
+            __syncthreads();
+            if (t == 0) {
+                double lo = lo_sh, hi = hi_sh;
+                int node = 1;
+                for (int d = 0; d < depth; ++d) {
+                    const double mid = mul(add(lo, hi), 0.5);
+                    if (mid == lo || mid == hi || steps == 200) {
+                        walk_done = 1;
+                        break;
+                    }
+                    ++steps;
+                    if (above[node]) {
+                        lo = mid;
+                        node = 2 * node + 1;
+                    } else {
+                        hi = mid;
+                        node = 2 * node;
+                    }
+                }
+                lo_sh = lo;
+                hi_sh = hi;
+            }
+            __syncthreads();
+        }
+        if (t == 0 && !fail) R_sh = hi_sh;
+    }
+    __syncthreads();
+    const double R = fail ? 1.0 : R_sh;
+    const double coshR = dm::cosh(R);
+    const double G = 0.5 * ::log(2.0 * coshR);
+    // e^k table (threads 0..128)
+    if (t <= 2 * kExpTab) M->etab[t] = static_cast<float>(::exp(static_cast<double>(t - kExpTab)));
+    const uint32_t B = a.B;
+    if (t == 0) {  // scalars and the boundaries (a short recurrence)
+        M->error = fail ? kErrNoSolution : kErrNone;
+        M->R = R;
+        M->coshR = coshR;
+        M->G = G;
+        M->alpha = alpha;
+        M->inv_alpha = div(1.0, alpha);
+        M->cm1 = sub(dm::cosh(mul(alpha, R)), 1.0);
+        const double p = a.p;
+        M->B = B;
+        M->batch_budget = a.batch_budget;
+        M->core_heavy = a.core_heavy;
+        M->fringe_limit = a.fringe_limit;
+        M->n = a.n;
+        M->seed = a.seed;
+        M->k = k;
+        M->filter = (a.allow_filter && R <= kFilterMaxR && alpha * R <= kFilterMaxAlphaR) ? 1u : 0u;
+        M->verify = a.verify;
+        // Sec. III-A: c_0 = 0, c_{j+1} - c_j = c_1 p^j, c_1 = (1-p) R / (1 - p^B), c_B = R
+        M->c[0] = 0.0;
+        if (p == 1.0) {
+            for (uint32_t j = 1; j < B; ++j) M->c[j] = div(mul(R, static_cast<double>(j)), static_cast<double>(B));
+        } else {
+            double pw = 1.0;
+            for (uint32_t j = 0; j < B; ++j) pw = mul(pw, p);
+            const double c1 = div(mul(sub(1.0, p), R), sub(1.0, pw));
+            double step = c1;
+            for (uint32_t j = 1; j < B; ++j) {
+                const double next = add(M->c[j - 1], step);
+                M->c[j] = next < R ? next : R;
+                step = mul(step, p);
+            }
+        }
+        M->c[B] = R;
+    }
+    __syncthreads();
+    // FP32 window constants, one band per thread: the filter's radii carry an error
+    // up to kDeltaR, so band i is bounded by c_i - kDeltaR (inner) and c_{i+1} +
+    // kDeltaR (outer)
+    const double sq = ::exp(-G);
+    for (uint32_t j = t; j <= B; j += blockDim.x) {
+        M->cosh_c[j] = ::cosh(M->c[j]);
+        M->sinh_c[j] = ::sinh(M->c[j]);
+        const double ci = M->c[j] - kDeltaR > 0.0 ? M->c[j] - kDeltaR : 0.0;
+        M->band_P[j] = static_cast<float>(::exp(ci) * sq);
+        M->band_M[j] = static_cast<float>(::exp(-ci) * sq);
+        M->band_S[j] = static_cast<float>(::sinh(ci) * sq * 1.4142135623730951);
+        const double co = (j < B ? M->c[j + 1] : R) + kDeltaR;
+        M->band_PMn[j] = static_cast<float>(2.0 * ::cosh(co) * sq * (1.0 + 1e-6));
+        M->band_Po[j] = static_cast<float>(::exp(co) * sq);
+        M->band_Mo[j] = static_cast<float>(::exp(-co) * sq);
+        M->band_So[j] = static_cast<float>(::sinh(co) * sq * 1.4142135623730951);
+    }
+    if (t < kMaxBands) M->band_count[t] = 0;
+    if (t != 0) return;
+    M->m = 0;
+    M->candidates = 0;
+    M->near_threshold = 0;
+    M->rounding_band = 0;
+    M->rechecks = 0;
+    M->verify_failures = 0;
+    M->heavy_n = 0;
+    M->heavy_next = 0;
+    M->recheck_n = 0;
+    M->work_counter = 0;
+    for (uint32_t c = 0; c < kClaimCounters; ++c) M->claim[c * 32] = 0;
+}
+
+// Batch, item vb of G + 1 (one CTA each): item g < G plans graph g; item G
+// clears the control block's counters.
+__device__ void plan_batch_item(Meta *metas, const PlanArgs *args, uint32_t G, uint32_t vb, PlanSmem &PS)
+{
+    if (vb < G) {
+        const PlanArgs a = args[vb];
+        plan_block(metas + vb, a, 3, PS);
+        return;
+    }
+    if (threadIdx.x != 0) return;
+    Meta *C = metas + G;
+    C->error = kErrNone;
+    C->filter = 0;
+    C->verify = 0;
+    C->m = 0;
+    C->candidates = 0;
+    C->near_threshold = 0;
+    C->rounding_band = 0;
+    C->rechecks = 0;
+    C->verify_failures = 0;
+    C->heavy_n = 0;
+    C->heavy_next = 0;
+    C->recheck_n = 0;
+    C->work_counter = 0;
+    for (uint32_t c = 0; c < kClaimCounters; ++c) C->claim[c * 32] = 0;
+}
+
+
+constexpr int kSampleThreads = 256;
+
+struct SampleSmem {
+    double c[kMaxBands + 1];
+    unsigned int hist[kMaxBands];
+};
+
+// Batch, tile t (one CTA): position p of graph g holds vertex p - pt_off[g]; the
+// FP64 radius (FP64 mode) is stored by position.
+__device__ void sample_tile(Meta *metas, const BatchTables &bt, uint64_t *keys, uint32_t *ids, double *r_by_pos,
+                            uint32_t t, SampleSmem &SS)
+{
+    double *c = SS.c;
+    unsigned int *hist = SS.hist;
+    __syncthreads();  // the CTA's previous item is done with the shared arrays
+    const uint4 T = bt.tiles[t];
+    Meta *M = metas + T.x;
+    const uint32_t B = M->B;
+    const bool filter = M->filter != 0;
+    const double R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
+    const uint64_t seed = M->seed;
+    if (threadIdx.x <= B) c[threadIdx.x] = M->c[threadIdx.x];
+    if (threadIdx.x < kMaxBands) hist[threadIdx.x] = 0;
+    __syncthreads();
+    if (M->error) return;
+    const uint32_t first_id = T.y - bt.pt_off[T.x];
+    for (uint32_t j = threadIdx.x; j < T.z; j += blockDim.x) {
+        const uint32_t id = first_id + j, pos = T.y + j;
+        const U64x4 x = draw(id, seed);
+        double r;
+        if (filter) {
+            r = radius_approx(x.x1 >> 11, R, cm1, inv_alpha);
+        } else {
+            r = radius_from_u53(x.x1 >> 11, R, cm1, inv_alpha);
+            r_by_pos[pos] = r;
+        }
+        const uint32_t b = band_of(r, c, B);
+        keys[pos] = (static_cast<uint64_t>(b) << 32) | static_cast<uint32_t>(x.x0 >> 32);
+        ids[pos] = id;
+        atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < B && hist[threadIdx.x]) atomicAdd(&M->band_count[threadIdx.x], hist[threadIdx.x]);
+}
+
+// Band starts (sorted positions) and bucket-index offsets of one graph whose
+// positions start at pos0 and whose index entries start at idx0.
+__device__ void band_offsets_one(Meta *M, uint64_t pos0, uint32_t idx0)
+{
+    uint64_t s = pos0;
+    uint32_t off = idx0;
+    for (uint32_t j = 0; j < M->B; ++j) {
+        M->band_start[j] = s;
+        s += M->band_count[j];
+        // 2^b buckets, the largest power of two <= count / kBucketPoints, b >= 1
+        uint32_t b = 1;
+        while (b < 31 && (uint64_t{2} << b) * kBucketPoints <= M->band_count[j]) ++b;
+        M->idx_off[j] = off;
+        M->idx_shift[j] = 32 - b;
+        off += (1u << b) + 1;
+    }
+    M->band_start[M->B] = s;
+    M->idx_off[M->B] = off;
+}
+
+// e^x in FP32 with relative error <= 4 * 2^-24 for |x| <= kExpTab + 1/2:
+// x = k + f with integer k, |f| <= 1/2 exact in FP64, e^k from the table.
+__device__ __forceinline__ float exp_split(double x, const float *etab)
+{
+    const double kd = rint(x);
+    const int k = static_cast<int>(kd);
+    const float f = static_cast<float>(x - kd);
+    return etab[k + kExpTab] * expf(f);
+}
+
+// Filter-mode values of a point from its FP64 angle and (approximate) radius.
+__device__ __forceinline__ void filter_values(double ph, double r, double G, const float *etab, float2 *ang,
+                                              float4 *pms)
+{
+    const float hi = static_cast<float>(ph);
+    const float lo = static_cast<float>(ph - static_cast<double>(hi));
+    *ang = make_float2(hi, lo);
+    const float P = exp_split(r - G, etab);
+    const float Mv = exp_split(-r - G, etab);
+    float S, gam;
+    if (r >= 1.0) {
+        S = (P - Mv) * 0.70710678118654752f;
+        gam = kEpsPM * ((P + Mv) / (P - Mv)) + 2.0f * kEps32;
+    } else if (r > 0.0) {
+        S = static_cast<float>(::sinh(r) * ::exp(-G) * 1.4142135623730951);
+        gam = kEpsPM * static_cast<float>(::cosh(r) / ::sinh(r)) + 2.0f * kEps32;
+    } else {
+        S = 0.0f;
+        gam = 0.0f;
+    }
+    *pms = make_float4(P, Mv, S, gam);
+}
+
+// Batch gathers, tile t (one CTA); ids are local, the FP64 radius is by position.
+__device__ void gather_filter_tile(const Meta *metas, const BatchTables &bt, const uint64_t *keys,
+                                   const uint32_t *sids, const SortedPoints &P, uint32_t t, float *etab)
+{
+    __syncthreads();  // the CTA's previous item is done with etab
+    const uint4 T = bt.tiles[t];
+    const Meta *M = metas + T.x;
+    for (int j = threadIdx.x; j <= 2 * kExpTab; j += blockDim.x) etab[j] = M->etab[j];
+    __syncthreads();
+    if (M->error || !M->filter) return;
+    const double G = M->G, R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
+    const uint64_t seed = M->seed;
+    for (uint32_t j = threadIdx.x; j < T.z; j += blockDim.x) {
+        const uint32_t p = T.y + j;
+        const uint32_t id = sids[p];
+        const U64x4 x = draw(id, seed);
+        const double ph = phi_from_u53(x.x0 >> 11);
+        const double r = radius_approx(x.x1 >> 11, R, cm1, inv_alpha);
+        float2 a;
+        float4 q;
+        filter_values(ph, r, G, etab, &a, &q);
+        P.akey[p] = static_cast<uint32_t>(keys[p]);
+        P.ang[p] = a;
+        P.pms[p] = q;
+        P.id[p] = id;
+    }
+}
+
+__device__ void gather_fp64_tile(const Meta *metas, const BatchTables &bt, const uint64_t *keys,
+                                 const uint32_t *sids, const double *r_by_pos, const SortedPoints &P, uint32_t t)
+{
+    const uint4 T = bt.tiles[t];
+    const Meta *M = metas + T.x;
+    if (M->error || M->filter) return;
+    const uint64_t seed = M->seed;
+    const uint32_t pos0 = bt.pt_off[T.x];
+    for (uint32_t j = threadIdx.x; j < T.z; j += blockDim.x) {
+        const uint32_t p = T.y + j;
+        const uint32_t id = sids[p];
+        const double ph = phi_from_u53(draw(id, seed).x0 >> 11);
+        const double r = r_by_pos[pos0 + id];
+        P.phi[p] = ph;
+        P.r[p] = r;
+        P.ch[p] = dm::cosh(r);
+        P.sh[p] = dm::sinh(r);
+        P.akey[p] = static_cast<uint32_t>(keys[p]);
+        P.id[p] = id;
+    }
+}
+
+// Per-graph results of a batch: {m low, m high, R low, R high} and {B, error}.
+__device__ void batch_result_one(const Meta *metas, uint32_t g, uint4 *out)
+{
+    const Meta *M = metas + g;
+    const uint64_t m = M->m;
+    const uint64_t Rb = static_cast<uint64_t>(__double_as_longlong(M->R));
+    out[2 * g] = make_uint4(static_cast<uint32_t>(m), static_cast<uint32_t>(m >> 32), static_cast<uint32_t>(Rb),
+                            static_cast<uint32_t>(Rb >> 32));
+    out[2 * g + 1] = make_uint4(M->B, M->error, M->filter, 0u);
+}
+
+
+// ---- radix sort (stable LSD, 8-bit digits)
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 8;
+constexpr int kTile = kThreads * kItems;  // keys per tile
+constexpr int kRadix = 256;
+
+struct TileSmem {
+    uint32_t digit_base[kRadix];  // output position of the next key of each digit
+    uint32_t warp_count[kWarps][kRadix];
+    uint32_t tile_start[kRadix];
+    uint32_t warp_sum[kWarps];
+    uint64_t skey[kTile];
+};
+
+// Exclusive scan of one value per thread over the CTA (kThreads = 8 warps);
+// warp_sum is scratch.  Ends with a barrier.
+__device__ __forceinline__ uint32_t block_exclusive(uint32_t v, uint32_t *warp_sum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += warp_sum[w];
+    __syncthreads();
+    return before + incl - v;
+}
+
+// One tile [tile, tile + cnt) of a pass: every warp ranks its 32 x kItems keys
+// with __match_any_sync, warps are combined by a per-digit prefix over warps, so
+// the order of equal digits is the input order (stable); the tile is staged in
+// shared memory in digit order and written out from there, one contiguous run
+// per digit, at sm.digit_base (which then advances by the tile's counts).
+template <bool kValues>
+__device__ __forceinline__ void tile_pass(const uint64_t *keys_in, uint64_t *keys_out, const uint32_t *vals_in,
+                                          uint32_t *vals_out, uint64_t tile, uint32_t cnt, int shift, TileSmem &sm,
+                                          uint32_t *sval)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lanemask_lt = (1u << lane) - 1u;
+    for (int w = 0; w < kWarps; ++w) sm.warp_count[w][threadIdx.x] = 0;
+    __syncthreads();
+    // rank within the warp's sub-tile: element (i, lane) = i*32 + lane of the sub-tile
+    const uint32_t sub = static_cast<uint32_t>(warp) * 32 * kItems;
+    uint64_t key[kItems];
+    uint32_t val[kItems];
+    uint32_t rank[kItems];
+    int digit[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const uint32_t local = sub + static_cast<uint32_t>(i) * 32 + lane;
+        const bool valid = local < cnt;
+        key[i] = valid ? keys_in[tile + local] : 0;
+        if (kValues) val[i] = valid ? vals_in[tile + local] : 0;
+        digit[i] = static_cast<int>((key[i] >> shift) & (kRadix - 1));
+        const uint32_t active = __ballot_sync(0xffffffffu, valid);
+        rank[i] = 0xffffffffu;
+        if (valid) {
+            const uint32_t peers = __match_any_sync(active, digit[i]);
+            const uint32_t base = sm.warp_count[warp][digit[i]];
+            rank[i] = base + __popc(peers & lanemask_lt);
+            __syncwarp(active);
+            if ((peers & lanemask_lt) == 0) sm.warp_count[warp][digit[i]] = base + __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps and the tile total; the digits'
+    // starts in the tile are the exclusive scan of the totals
+    const int d = threadIdx.x;
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = sm.warp_count[w][d];
+        sm.warp_count[w][d] = run;
+        run += c;
+    }
+    sm.tile_start[d] = block_exclusive(run, sm.warp_sum);
+    __syncthreads();
+    // the tile in digit order (stable) in shared memory ...
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        if (rank[i] != 0xffffffffu) {
+            const uint32_t local = sm.tile_start[digit[i]] + sm.warp_count[warp][digit[i]] + rank[i];
+            sm.skey[local] = key[i];
+            if (kValues) sval[local] = val[i];
+        }
+    }
+    __syncthreads();
+    // ... then written out in that order: each digit's keys land on consecutive
+    // positions, so neighbouring threads write neighbouring addresses
+    for (uint32_t j = threadIdx.x; j < cnt; j += kThreads) {
+        const uint64_t k = sm.skey[j];
+        const int dg = static_cast<int>((k >> shift) & (kRadix - 1));
+        const uint32_t pos = sm.digit_base[dg] + (j - sm.tile_start[dg]);
+        keys_out[pos] = k;
+        if (kValues) vals_out[pos] = sval[j];
+    }
+    __syncthreads();
+    sm.digit_base[d] += run;
+    __syncthreads();
+}
+
+// ---- segmented (batch): tiles of one graph each, per-tile digit counts
+static_assert(kTile == static_cast<int>(kTilePoints), "batch tiles are sort tiles");
+
+// Tile t (one CTA of kThreads): the digit counts of the tile.
+__device__ void seg_upsweep_tile(const uint64_t *keys, const BatchTables &bt, int shift, uint32_t *counts,
+                                 uint32_t t, uint32_t *hist)
+{
+    __syncthreads();  // the CTA's previous item is done with hist
+    hist[threadIdx.x] = 0;
+    __syncthreads();
+    const uint4 T = bt.tiles[t];
+    for (uint32_t j = threadIdx.x; j < T.z; j += kThreads) atomicAdd(&hist[(keys[T.y + j] >> shift) & (kRadix - 1)], 1u);
+    __syncthreads();
+    counts[static_cast<uint64_t>(t) * kRadix + threadIdx.x] = hist[threadIdx.x];
+}
+
+// CTA per graph: counts[t][d] of the graph's tiles become the output position of
+// tile t's first key of digit d (graph start + keys of smaller digits + keys of
+// digit d in earlier tiles of the graph).
+__device__ void seg_scan_graph(const BatchTables &bt, uint32_t *counts, uint32_t g, uint32_t *warp_sum)
+{
+    __syncthreads();  // the CTA's previous item is done with warp_sum
+    const uint32_t d = threadIdx.x;
+    const uint32_t t0 = bt.tile_first[g], t1 = bt.tile_first[g + 1];
+    uint32_t run = 0;
+    for (uint32_t t = t0; t < t1; ++t) {
+        uint32_t &c = counts[static_cast<uint64_t>(t) * kRadix + d];
+        const uint32_t v = c;
+        c = run;
+        run += v;
+    }
+    const uint32_t base = bt.pt_off[g] + block_exclusive(run, warp_sum);
+    for (uint32_t t = t0; t < t1; ++t) counts[static_cast<uint64_t>(t) * kRadix + d] += base;
+}
+
+template <bool kValues>
+__device__ void seg_downsweep_tile(const uint64_t *keys_in, uint64_t *keys_out, const uint32_t *vals_in,
+                                   uint32_t *vals_out, const BatchTables &bt, int shift, const uint32_t *offsets,
+                                   uint32_t t, TileSmem &sm, uint32_t *sval)
+{
+    __syncthreads();  // the CTA's previous item is done with sm
+    const uint4 T = bt.tiles[t];
+    sm.digit_base[threadIdx.x] = offsets[static_cast<uint64_t>(t) * kRadix + threadIdx.x];
+    __syncthreads();
+    tile_pass<kValues>(keys_in, keys_out, vals_in, vals_out, T.y, T.z, shift, sm, sval);
+}
+
+
+}  // namespace stg
+}  // namespace
+}  // namespace rhg

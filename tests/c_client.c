@@ -26,7 +26,7 @@ int main(void)
     rhg_batch_graph res[2];
     rhg_result totals;
 
-    CHECK(rhg_version() == 2);
+    CHECK(rhg_version() == 3);
     CHECK(strcmp(rhg_status_str(RHG_OK), "RHG_OK") == 0);
     CHECK(strcmp(rhg_status_str(RHG_ERR_OVERFLOW), "RHG_ERR_OVERFLOW") == 0);
 
@@ -53,7 +53,7 @@ int main(void)
     memset(&plan, 0, sizeof(plan));
     CHECK(rhg_batch_launch(&plan, NULL, NULL, NULL) == RHG_ERR_INVALID_ARG);
     CHECK(rhg_batch_read_results(&plan, NULL, NULL, res, &totals) == RHG_ERR_INVALID_ARG);
-    CHECK(sizeof(rhg_params) == 56 && sizeof(rhg_result) == 72 && sizeof(rhg_batch_plan) == 56);
+    CHECK(sizeof(rhg_params) == 72 && sizeof(rhg_result) == 72 && sizeof(rhg_batch_plan) == 56);
 
     if (fails) fprintf(stderr, "%d checks failed\n", fails);
     else printf("c client ok\n");

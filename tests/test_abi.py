@@ -39,11 +39,11 @@ def test_status_strings_and_version(rhg):
     assert rhg.status_str(0) == "RHG_OK"
     assert rhg.status_str(6) == "RHG_ERR_OVERFLOW"
     assert rhg.status_str(99) == "RHG_ERR_UNKNOWN"
-    assert rhg.load().rhg_version() == 2
+    assert rhg.load().rhg_version() == 3
 
 
 def test_params_layout_matches_header(rhg):
-    assert ctypes.sizeof(rhg.Params) == 56
+    assert ctypes.sizeof(rhg.Params) == 72
     assert ctypes.sizeof(rhg.Result) == 72
 
 
@@ -64,6 +64,17 @@ def test_host_validation(rhg):
         assert _ws_status(rhg, **kw)[0] == rhg.INVALID_ARG, kw
     # an R given directly replaces k
     assert _ws_status(rhg, n=100, k=0, alpha=1.0, R_override=12.0)[0] == 0
+    # the range query's work mapping: 0 = default, else within its documented range
+    for kw in (dict(batch_budget=1023), dict(batch_budget=(1 << 24) + 1), dict(core_heavy=63),
+               dict(core_heavy=65537), dict(fringe_limit=33)):
+        assert _ws_status(rhg, n=100, k=6, alpha=1.0, **kw)[0] == rhg.INVALID_ARG, kw
+    for kw in (dict(batch_budget=1024), dict(batch_budget=1 << 24), dict(core_heavy=64), dict(core_heavy=65536),
+               dict(fringe_limit=1), dict(fringe_limit=32)):
+        assert _ws_status(rhg, n=100, k=6, alpha=1.0, **kw)[0] == 0, kw
+    p = rhg.make_params(n=100, k=6, alpha=1.0)
+    p.reserved = 1
+    out = ctypes.c_size_t(0)
+    assert rhg.load().rhg_workspace_bytes(ctypes.byref(p), 0, ctypes.byref(out)) == rhg.INVALID_ARG
 
 
 def test_invalid_arguments_rejected_before_device_work(rhg):
@@ -130,3 +141,16 @@ def test_library_loads_once_across_threads(rhg):
         assert len(got) == 8 and len({id(x) for x in got}) == 1
     finally:
         rhg._lib = saved if saved is not None else rhg._lib
+
+
+def test_chunk_list_sized_for_fp64_mode_when_solved_R_exceeds_the_filter(rhg):
+    """A graph whose R solved from Eq. 22 is above the filter's range runs in FP64
+    mode on the device: its workspace is sized like an FP64-only graph's.  One
+    whose R is well inside the range is sized like a filter graph."""
+    fp64 = rhg.FLAG_FP64_ONLY
+    # n = 5e6, k = 8, alpha = 0.6: R = 32.7 > 32
+    assert _ws_status(rhg, n=5_000_000, k=8, alpha=0.6)[1] == _ws_status(rhg, n=5_000_000, k=8, alpha=0.6,
+                                                                          flags=fp64)[1]
+    # n = 5e6, k = 8, alpha = 1: R = 28.6, filter mode
+    assert _ws_status(rhg, n=5_000_000, k=8, alpha=1.0)[1] < _ws_status(rhg, n=5_000_000, k=8, alpha=1.0,
+                                                                         flags=fp64)[1]

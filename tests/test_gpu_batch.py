@@ -96,21 +96,31 @@ def test_p4_shaped_batch_sample():
     assert tot.m == sum(r.m for r in results)
 
 
-def test_autotuned_band_counts_give_the_same_graphs():
-    """The autotuner only changes band counts: every graph stays the same."""
+def test_autotuned_parameters_give_the_same_graphs():
+    """The autotuner only changes band counts and the query's work mapping: every
+    graph stays the same, also with extreme mappings (tiny budget, fringe limit 1)."""
     rhg = require_gpu()
     from paper_1606_09481_gb300.autotune import gpu_runner, tune
     rng = np.random.default_rng(77)
     specs = [(int(10 ** rng.uniform(3, 5)), int(rng.integers(6, 33)), float(rng.uniform(0.55, 1.5)), 3000 + j)
              for j in range(48)]
-    table = tune(specs, gpu_runner(), per_class=16, repeats=1)
+    table = tune(specs, gpu_runner(), per_class=16, repeats=1, offsets=(-2, 0), budgets=(16_384, 65_536),
+                 cores=(1_024, 4_096), fringes=(16, 32))
     assert set(table.offsets) <= {0, 1}
-    tuned = rhg.batch_params([rhg.make_params(n, k, a, s, table.bands(n)) for (n, k, a, s) in specs])
+
+    def tuned_one(n, k, a, s):
+        b, bb, ch, fl = table.params(n)
+        return rhg.make_params(n, k, a, s, b, batch_budget=bb, core_heavy=ch, fringe_limit=fl)
+
     v1, r1, _ = rhg.generate_batch(rhg.batch_params(specs))
-    v2, r2, _ = rhg.generate_batch(tuned)
+    v2, r2, _ = rhg.generate_batch(rhg.batch_params([tuned_one(*sp) for sp in specs]))
+    extreme = rhg.batch_params([rhg.make_params(n, k, a, s, batch_budget=1024, core_heavy=64, fringe_limit=1)
+                                for (n, k, a, s) in specs])
+    v3, r3, _ = rhg.generate_batch(extreme)
     for g in range(len(specs)):
         assert r2[g].num_bands == table.bands(specs[g][0])
         assert np.array_equal(sorted_pairs(v1[g]), sorted_pairs(v2[g])), g
+        assert np.array_equal(sorted_pairs(v1[g]), sorted_pairs(v3[g])), g
 
 
 def test_captured_batch_replays_the_same_graphs():
@@ -140,3 +150,39 @@ def test_captured_batch_replays_the_same_graphs():
         buf.out.fill_(-1)
         graph.replay()
         check()
+
+
+def test_persistent_barrier_gives_up_and_the_device_stays_usable():
+    """The persistent batch launch's grid barrier: it completes when every CTA
+    arrives; when one never does (the test asks for one CTA more than the launch
+    has), every wait gives up after its limit and the call reports
+    RHG_ERR_TIMEOUT, and the device runs the next batch normally."""
+    import time
+    rhg = require_gpu()
+    assert rhg.grid_barrier_test(0, 10**9) == rhg.OK
+    t0 = time.perf_counter()
+    assert rhg.grid_barrier_test(1, 20 * 10**6) == rhg.TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    params = rhg.batch_params(MIXED[:9])
+    views, results, _ = rhg.generate_batch(params)
+    _check_against_single(rhg, params, views, results)
+
+
+def test_batch_stage_times():
+    """The persistent launch records the device time of each of its stages."""
+    rhg = require_gpu()
+    import torch
+    params = rhg.batch_params(MIXED)
+    buf = rhg.allocate_batch(params)
+    plan = rhg.batch_prepare(buf)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rhg.batch_launch(plan, buf)
+    e1.record()
+    torch.cuda.synchronize()
+    st = rhg.batch_stage_times(plan, buf)
+    assert list(st) == list(rhg.BATCH_STAGES) and len(st) == 27
+    assert all(v >= 0.0 for v in st.values())
+    total = sum(st.values())
+    assert 0.0 < total <= e0.elapsed_time(e1) * 1.05 + 0.05

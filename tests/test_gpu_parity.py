@@ -164,3 +164,27 @@ def test_output_buffer_at_odd_slot(O, n, k, alpha, seed):
     phi, r = O.sample_points(n, alpha, R, seed)
     assert np.array_equal(got, O.brute_edges(phi, r, R))
     assert res.m > 0
+
+
+@pytest.mark.parametrize("budget,core,fringe", [(1024, 64, 1), (1024, 65536, 32), (1 << 24, 64, 16)])
+def test_work_mapping_does_not_change_edges(O, budget, core, fringe):
+    """The range query's work mapping (batch budget, core chunk limit, fringe
+    limit) moves work between the batch and the heavy-chunk kernels, never changes
+    the edges."""
+    import ctypes
+
+    import torch
+    rhg = require_gpu()
+    n, k, alpha, seed = 30_000, 120, 0.9, 41
+    base, res0 = rhg.generate_pairs(n, k, alpha, seed)
+    want = sorted_pairs(base)
+    p = rhg.make_params(n, k, alpha, seed, batch_budget=budget, core_heavy=core, fringe_limit=fringe)
+    wsp = rhg.allocate_pairs(p, int(res0.m) + 16)
+    res = rhg.Result()
+    rc = rhg.load().rhg_generate_pairs(ctypes.byref(p), wsp.ws.data_ptr(), wsp.ws.numel(), wsp.out.data_ptr(),
+                                       wsp.capacity, None, ctypes.byref(res))
+    assert rc == rhg.OK
+    torch.cuda.synchronize()
+    assert np.array_equal(sorted_pairs(wsp.out[: 2 * res.m].view(-1, 2)), want)
+    if fringe == 1:
+        assert res.heavy_chunks > res0.heavy_chunks
