@@ -84,7 +84,7 @@ def measured_peaks():
 
 TRAFFIC_SOURCES = ("paper_1606_09481_gb300/csrc/query.cu", "paper_1606_09481_gb300/csrc/common.cuh",
                    "paper_1606_09481_gb300/csrc/kernels.h", "paper_1606_09481_gb300/csrc/detmath.cuh",
-                   "include/rhg.h")
+                   "paper_1606_09481_gb300/csrc/stages.cuh", "include/rhg.h")
 
 
 def sources_digest(paths=TRAFFIC_SOURCES) -> str:
