@@ -71,6 +71,7 @@ def lib() -> ctypes.CDLL:
             L.ro_default_bands.restype = _u32
             L.ro_boundaries.argtypes = [_dbl, _u32, _dbl, _p]
             L.ro_sample_points.argtypes = [_u64, _dbl, _dbl, _u64, _u64, _p, _p]
+            L.ro_radius_from_u53.argtypes = [_p, _u64, _dbl, _dbl, _p]
             L.ro_edge.argtypes = [_dbl, _dbl, _dbl, _dbl, _dbl]
             L.ro_edge_L.argtypes = [_dbl, _dbl, _dbl, _dbl]
             L.ro_edge_L.restype = _dbl
@@ -189,6 +190,17 @@ def sample_points(n: int, alpha: float, R: float, seed: int, first: int = 0):
     r = np.zeros(n, dtype=np.float64)
     lib().ro_sample_points(n, alpha, R, seed, first, _ptr(phi), _ptr(r))
     return phi, r
+
+
+def radius_from_u53(u, alpha: float, R: float) -> np.ndarray:
+    """The sampler's radius (inverse CDF of Eq. 1, FP64 definition) of given
+    53-bit variates: the radial step of sample_points alone."""
+    u = np.ascontiguousarray(u, dtype=np.uint64)
+    r = np.zeros(u.size, dtype=np.float64)
+    st = lib().ro_radius_from_u53(_ptr(u), u.size, alpha, R, _ptr(r))
+    if st != STATUS_OK:
+        raise ValueError(f"radius_from_u53 status {st}")
+    return r
 
 
 def asinh(y: float) -> float:

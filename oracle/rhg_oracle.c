@@ -334,11 +334,27 @@ int ro_boundaries(double R, uint32_t B, double p, double *c)
 /* r = acosh(1 + U (cosh(alpha R) - 1)) / alpha, acosh(1+w) = ln(1 + w +      */
 /* sqrt(w (w + 2))).                                                          */
 /* ------------------------------------------------------------------------- */
+/* The radius of the 53-bit uniform variate ur (cm1 = cosh(alpha R) - 1). */
+static double ro_radius_of(uint64_t ur, double R, double cm1, double inv_alpha)
+{
+    const double U53 = 0x1.0p-53;
+    double U = (double)ur * U53;
+    double w = U * cm1;
+    double w2 = w + 2.0;
+    double ww = w * w2;
+    double sq = sqrt(ww);
+    double y = 1.0 + w;
+    y = y + sq;
+    double lg = ro_log(y);
+    double rr = lg * inv_alpha;
+    if (rr > R) rr = R;
+    return rr;
+}
+
 int ro_sample_points(uint64_t n, double alpha, double R, uint64_t seed, uint64_t first,
                      double *phi, double *r)
 {
     const double S = 0x1.921fb54442d18p-51;   /* TWO_PI * 2^-53, exact */
-    const double U53 = 0x1.0p-53;
     double aR = alpha * R;
     double cm1 = ro_cosh(aR) - 1.0;
     double inv_alpha = 1.0 / alpha;
@@ -349,18 +365,21 @@ int ro_sample_points(uint64_t n, double alpha, double R, uint64_t seed, uint64_t
         uint64_t uphi = x[0] >> 11, ur = x[1] >> 11;
         double ph = (double)uphi * S;
         if (ph >= RO_TWO_PI) ph = nextafter(RO_TWO_PI, 0.0);
-        double U = (double)ur * U53;
-        double w = U * cm1;
-        double w2 = w + 2.0;
-        double ww = w * w2;
-        double sq = sqrt(ww);
-        double y = 1.0 + w;
-        y = y + sq;
-        double lg = ro_log(y);
-        double rr = lg * inv_alpha;
-        if (rr > R) rr = R;
         phi[i] = ph;
-        r[i] = rr;
+        r[i] = ro_radius_of(ur, R, cm1, inv_alpha);
+    }
+    return RO_OK;
+}
+
+/* The sampler's radius of given 53-bit variates (the radial step of
+ * ro_sample_points alone): r[i] for u[i] < 2^53. */
+int ro_radius_from_u53(const uint64_t *u, uint64_t n, double alpha, double R, double *r)
+{
+    double cm1 = ro_cosh(alpha * R) - 1.0;
+    double inv_alpha = 1.0 / alpha;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (u[i] >> 53) return RO_ERR_INVALID_ARG;
+        r[i] = ro_radius_of(u[i], R, cm1, inv_alpha);
     }
     return RO_OK;
 }

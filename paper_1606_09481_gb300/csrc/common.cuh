@@ -18,6 +18,7 @@ constexpr int kMaxBands = static_cast<int>(RHG_MAX_BANDS);
 constexpr uint32_t kBucketPoints = 1;
 __host__ __device__ constexpr uint64_t index_entries(uint64_t n) { return n / kBucketPoints + 3 * kMaxBands + 1; }
 constexpr int kExpTab = 64;  // e^k table for k = -64..64 (FP32 filter values)
+constexpr int kYTab = 66;    // 2^(+-e/alpha) e^-G tables for the exponents e = 0..65 of y (filter_values_u53)
 constexpr uint32_t kClaimCounters = 16;  // work-claim counters of the range query (Meta::claim)
 constexpr int kMaxStageMarks = 32;       // stage timestamps of the persistent batch launch
 
@@ -28,8 +29,10 @@ constexpr int kMaxStageMarks = 32;       // stage timestamps of the persistent b
 // all FP32, and decides only when |X - 1| exceeds a bound on every error
 // between X and the rounded FP64 predicate (Eq. 3); other pairs are rechecked
 // with the FP64 predicate itself.
-constexpr double kDeltaR = 1e-6;        // |r_approx - r| (FP32-assisted radius, proven <= 5.4e-7)
-constexpr float kEpsPM = 2e-6f;          // relative error of stored P and M (analysis: <= 8.4e-7)
+constexpr double kDeltaR = 1e-6;        // slack on the band radii of the FP32 windows (band members
+                                         // are within 1e-13 of their band: see band_of_u53)
+constexpr float kEpsPM = 2e-6f;          // relative error of stored P and M (analysis: <= 1.2e-6,
+                                         // filter_values_u53; <= 8.4e-7 from an FP64 radius)
 constexpr float kEps32 = 5.9604645e-8f;  // 2^-24
 constexpr float kCBase = 6e-6f;          // 2 kEpsPM + 8 eps32 + 2 eps_sin, rounded up
 constexpr float kAngAbs = 2e-13f;        // absolute error of |phi_v - phi_w| from the hi/lo split, x2
@@ -60,6 +63,15 @@ struct Meta {
     float band_PMn[kMaxBands + 1];  // P + M at the outer radius
     float band_Po[kMaxBands + 1], band_Mo[kMaxBands + 1], band_So[kMaxBands + 1];  // at the outer radius
     float etab[2 * kExpTab + 1];    // e^k rounded to float
+    // generated points in filter mode (band_of_u53, filter_values_u53): band j holds
+    // the radial variates band_u[j] <= u53 < band_u[j + 1]; y = 2^e m gives
+    // P = tabP[e] m^(1/alpha), M = tabM[e] m^(-1/alpha)
+    uint64_t band_u[kMaxBands + 1];
+    float tabP[kYTab], tabM[kYTab];  // 2^(e/alpha) e^-G, 2^(-e/alpha) e^-G rounded to float
+    float cw;                        // (cosh(alpha R) - 1) 2^-53 rounded to float
+    float inv_alpha_f;               // 1 / alpha rounded to float
+    float y_one;                     // e^alpha rounded to float: y >= y_one means r >= 1 (about)
+    uint32_t alpha_one;              // alpha == 1: m^(1/alpha) = m exactly
     uint32_t B;
     uint32_t batch_budget, core_heavy, fringe_limit;  // work mapping of the range query
     uint32_t error;          // nonzero: a device-side check failed (see kErr*)
@@ -160,27 +172,76 @@ __device__ __forceinline__ U64x4 draw(uint64_t id, uint64_t seed)
     return philox4x64_10(U64x4{id, 0, 0, 0}, seed, 0);
 }
 
-// Radius for band assignment and the FP32 filter, without FP64 transcendentals:
-// y = 1 + w + sqrt(w (w + 2)) in FP32 from the FP64 w = U (cosh(alpha R) - 1)
-// (relative error <= 4 * 2^-24), ln y = e ln 2 + ln m with m in [sqrt(1/2),
-// sqrt(2)) (logf: 1 ulp, <= 3e-8 here), assembled in FP64:
-// |r_approx - r| <= (2.4e-7 + 3e-8) / alpha <= 5.4e-7 < kDeltaR for alpha > 1/2.
-// Requires alpha R <= kFilterMaxAlphaR: w (w + 2) must stay below FLT_MAX, i.e.
-// w < 1.84e19, i.e. alpha R < 45.05.
-__device__ __forceinline__ double radius_approx(uint64_t u53, double R, double cm1, double inv_alpha)
+// ---------------------------------------------------------------------------
+// Generated points in filter mode: band and filter values without FP64 (GB300's
+// FP64 pipe runs at a small fraction of its integer and FP32 pipes).
+
+// 2^e as a float, e in [-126, 127].
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// Band of a generated point from its radial variate u53: the largest j < B with
+// bu[j] <= u53, where bu[j] = ceil(F(c_j) 2^53) and F(c) = (cosh(alpha c) - 1) /
+// (cosh(alpha R) - 1) is the CDF of Eq. 1 (bu[0] = 0, bu[B] = 2^53).  A variate at
+// or above bu[j] has U >= F(c_j) (1 - 1e-15), so its FP64 radius (radius_from_u53)
+// is at least c_j - 1e-13; below bu[j + 1] it is at most c_{j+1} + 1e-13.  Integer
+// compares only: the FP64 radius is never formed.
+__device__ __forceinline__ uint32_t band_of_u53(uint64_t u53, const uint64_t *bu, uint32_t B)
 {
-    const double U = static_cast<double>(u53) * kU53;
-    const float wf = static_cast<float>(U * cm1);
-    const float y = (1.0f + wf) + sqrtf(wf * (wf + 2.0f));
-    int e;
-    float m = frexpf(y, &e);
-    if (m < 0.70710678f) {
-        m *= 2.0f;
-        e -= 1;
+    uint32_t lo = 0, hi = B;  // invariant: bu[lo] <= u53, answer in [lo, hi)
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (bu[mid] <= u53) lo = mid;
+        else hi = mid;
     }
-    const double lg = static_cast<double>(e) * 0.69314718055994530942 + static_cast<double>(logf(m));
-    const double r = lg * inv_alpha;
-    return r < R ? (r > 0.0 ? r : 0.0) : R;
+    return lo;
+}
+
+// The angle's hi/lo float pair float(phi), float(phi - float(phi)) for phi =
+// fl(u53 kPhiScale) (phi_from_u53, including its clamp below 2 pi), bit for bit,
+// with integer arithmetic: kPhiScale = kSig 2^-103 with the 53-bit significand kSig
+// of 2 pi, so phi is the 106-bit product u53 kSig rounded to 53 bits (to nearest,
+// ties to even, as the FP64 multiplication rounds); hi is that rounded to 24 bits
+// the same way, and phi - hi (exact in 30 bits) is rounded to float by the
+// integer-to-float conversion.
+__device__ __forceinline__ float2 angle_hilo_u53(uint64_t u)
+{
+    constexpr uint64_t kSig = 0x1921fb54442d18ull;
+    if (u == 0) return make_float2(0.0f, 0.0f);
+    const uint64_t plo = u * kSig, phi = __umul64hi(u, kSig);
+    const int nb = phi ? 128 - __clzll(static_cast<long long>(phi)) : 64 - __clzll(static_cast<long long>(plo));
+    int sh = nb - 53;  // 0..53: the product >> sh has 53 bits (kSig has 53, u >= 1)
+    uint64_t q = sh ? (plo >> sh) | (phi << (64 - sh)) : plo;
+    if (sh) {
+        const uint64_t rem = plo & ((uint64_t{1} << sh) - 1), half = uint64_t{1} << (sh - 1);
+        if (rem > half || (rem == half && (q & 1u))) {
+            if (++q == (uint64_t{1} << 53)) {
+                q >>= 1;
+                ++sh;
+            }
+        }
+    }
+    // phi = q 2^(sh - 103); 2 pi = kSig 2^-50
+    if (sh > 53 || (sh == 53 && q >= kSig)) {
+        q = kSig - 1;  // the largest double below 2 pi
+        sh = 53;
+    }
+    uint64_t h = q >> 29;
+    const uint64_t r = q & 0x1fffffffull;
+    if (r > 0x10000000ull || (r == 0x10000000ull && (h & 1u))) ++h;  // h <= 2^24
+    const int lo_i = static_cast<int>(static_cast<int64_t>(q) - static_cast<int64_t>(h << 29));  // |.| <= 2^28
+    return make_float2(__uint2float_rn(static_cast<uint32_t>(h)) * pow2f(sh - 74),
+                       __int2float_rn(lo_i) * pow2f(sh - 103));
+}
+
+// u53 rounded to float (to nearest, ties to even), with integer arithmetic.
+__device__ __forceinline__ float u53_to_float(uint64_t u)
+{
+    if (u < (uint64_t{1} << 24)) return __uint2float_rn(static_cast<uint32_t>(u));
+    const int s = 40 - __clzll(static_cast<long long>(u));  // bit length - 24, 1..29
+    uint64_t m = u >> s;
+    const uint64_t rem = u & ((uint64_t{1} << s) - 1), half = uint64_t{1} << (s - 1);
+    if (rem > half || (rem == half && (m & 1u))) ++m;  // m <= 2^24
+    return __uint2float_rn(static_cast<uint32_t>(m)) * pow2f(s);
 }
 
 // The sampler's FP64 angle and radius of point `id` (Alg. 1, Eq. 1).

@@ -17,35 +17,43 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, PlanArgs a)
 }
 
 // Points by id: sort key (band << 32 | angle key) and id.  In filter mode the band
-// comes from the approximate radius (bands are then bounded by c_i -+ kDeltaR);
-// otherwise from the FP64 radius, which is also stored by id for the gather.
+// comes from the radial variate compared with the band thresholds (band_of_u53, no
+// FP64); otherwise from the FP64 radius, which is also stored by id for the gather.
 __global__ void __launch_bounds__(kSampleThreads) sample_kernel(Meta *M, uint64_t n, uint64_t seed,
                                                                 uint64_t *keys, uint32_t *ids,
                                                                 double *r_by_id)
 {
     __shared__ double c[kMaxBands + 1];
+    __shared__ uint64_t bu[kMaxBands + 1];
     __shared__ unsigned int hist[kMaxBands];
     const uint32_t B = M->B;
     const bool filter = M->filter != 0;
     const double R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
-    if (threadIdx.x <= B) c[threadIdx.x] = M->c[threadIdx.x];
+    if (threadIdx.x <= B) {
+        c[threadIdx.x] = M->c[threadIdx.x];
+        bu[threadIdx.x] = M->band_u[threadIdx.x];
+    }
     if (threadIdx.x < kMaxBands) hist[threadIdx.x] = 0;
     __syncthreads();
     if (M->error) return;
-    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        const U64x4 x = draw(i, seed);
-        double r;
-        if (filter) {
-            r = radius_approx(x.x1 >> 11, R, cm1, inv_alpha);
-        } else {
-            r = radius_from_u53(x.x1 >> 11, R, cm1, inv_alpha);
-            r_by_id[i] = r;
+    // warp-uniform trip count (the histogram is counted per warp)
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t i0 = blockIdx.x * static_cast<uint64_t>(blockDim.x) + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+        const uint64_t i = i0 + (threadIdx.x & 31u);
+        uint32_t b = kMaxBands;
+        if (i < n) {
+            const U64x4 x = draw(i, seed);
+            if (filter) {
+                b = band_of_u53(x.x1 >> 11, bu, B);
+            } else {
+                const double r = radius_from_u53(x.x1 >> 11, R, cm1, inv_alpha);
+                r_by_id[i] = r;
+                b = band_of(r, c, B);
+            }
+            keys[i] = (static_cast<uint64_t>(b) << 32) | static_cast<uint32_t>(x.x0 >> 32);
+            ids[i] = static_cast<uint32_t>(i);
         }
-        const uint32_t b = band_of(r, c, B);
-        keys[i] = (static_cast<uint64_t>(b) << 32) | static_cast<uint32_t>(x.x0 >> 32);
-        ids[i] = static_cast<uint32_t>(i);
-        atomicAdd(&hist[b], 1u);
+        hist_add_warp(hist, b);
     }
     __syncthreads();
     if (threadIdx.x < B && hist[threadIdx.x]) atomicAdd(&M->band_count[threadIdx.x], hist[threadIdx.x]);
@@ -89,25 +97,23 @@ __global__ void __launch_bounds__(256) gather_filter_kernel(const Meta *M, uint6
                                                             SortedPoints P)
 {
     __shared__ float etab[2 * kExpTab + 1];
+    __shared__ YTab Y;
     for (int j = threadIdx.x; j <= 2 * kExpTab; j += blockDim.x) etab[j] = M->etab[j];
+    load_ytab(Y, M);
     __syncthreads();
     if (M->error || !M->filter) return;
-    const double G = M->G, R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
+    const double G = M->G;
     for (uint64_t p = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; p < n;
          p += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
         const uint32_t id = sids[p];
-        double ph, r;
-        if (phi_src) {
-            ph = phi_src[id];
-            r = r_src[id];
-        } else {
-            const U64x4 x = draw(id, seed);
-            ph = phi_from_u53(x.x0 >> 11);
-            r = radius_approx(x.x1 >> 11, R, cm1, inv_alpha);
-        }
         float2 a;
         float4 q;
-        filter_values(ph, r, G, etab, &a, &q);
+        if (phi_src) {  // caller's points: from the FP64 coordinates
+            filter_values(phi_src[id], r_src[id], G, etab, &a, &q);
+        } else {        // generated points: from the variates, without FP64
+            const U64x4 x = draw(id, seed);
+            filter_values_u53(x.x0 >> 11, x.x1 >> 11, Y, &a, &q);
+        }
         P.akey[p] = static_cast<uint32_t>(keys[p]);
         P.ang[p] = a;
         P.pms[p] = q;

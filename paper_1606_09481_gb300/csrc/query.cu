@@ -1460,7 +1460,7 @@ union PersistSmem {
         stg::TileSmem sm;
         uint32_t sval[stg::kTile];
     } down;
-    float etab[2 * kExpTab + 1];
+    stg::YTab ytab;
     struct {
         BandShared S[kWarps];
         BatchSmem<true> W[kWarps];
@@ -1525,7 +1525,7 @@ __global__ void __launch_bounds__(kThreads, kPersistMinBlocks) batch_persistent_
     }
     // gather (a tile's graph is in filter or in FP64 mode: one of the two writes)
     for (uint32_t vb = blockIdx.x; vb < tiles; vb += nblocks) {
-        stg::gather_filter_tile(b.metas, bt, kin, vin, b.P, vb, U.etab);
+        stg::gather_filter_tile(b.metas, bt, kin, vin, b.P, vb, U.ytab);
         stg::gather_fp64_tile(b.metas, bt, kin, vin, b.r_by_pos, b.P, vb);
     }
     if (!sync()) return;

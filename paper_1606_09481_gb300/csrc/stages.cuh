@@ -169,9 +169,10 @@ __device__ void plan_block(Meta *M, const PlanArgs &a, int depth, PlanSmem &PS)
         M->c[B] = R;
     }
     __syncthreads();
-    // FP32 window constants, one band per thread: the filter's radii carry an error
-    // up to kDeltaR, so band i is bounded by c_i - kDeltaR (inner) and c_{i+1} +
-    // kDeltaR (outer)
+    // FP32 window constants, one band per thread: band i is bounded by c_i - kDeltaR
+    // (inner) and c_{i+1} + kDeltaR (outer), a slack well above how far a member's
+    // FP64 radius can be from its band (1e-13: band_of_u53; caller points are
+    // assigned by their FP64 radius)
     const double sq = ::exp(-G);
     for (uint32_t j = t; j <= B; j += blockDim.x) {
         M->cosh_c[j] = ::cosh(M->c[j]);
@@ -186,8 +187,31 @@ __device__ void plan_block(Meta *M, const PlanArgs &a, int depth, PlanSmem &PS)
         M->band_Mo[j] = static_cast<float>(::exp(-co) * sq);
         M->band_So[j] = static_cast<float>(::sinh(co) * sq * 1.4142135623730951);
     }
+    // generated points in filter mode (band_of_u53, filter_values_u53)
+    const double cm1 = M->cm1;
+    for (uint32_t j = t; j <= B; j += blockDim.x) {
+        uint64_t bu = 0;
+        if (j == B) {
+            bu = uint64_t{1} << 53;
+        } else if (j > 0) {
+            const double sh = ::sinh(0.5 * alpha * M->c[j]);
+            const double F = 2.0 * sh * sh / cm1;  // (cosh(alpha c_j) - 1) / (cosh(alpha R) - 1)
+            const double T = ceil(F * 9007199254740992.0);
+            bu = T <= 0.0 ? 0 : (T >= 9007199254740992.0 ? uint64_t{1} << 53 : static_cast<uint64_t>(T));
+        }
+        M->band_u[j] = bu;
+    }
+    for (int e = t; e < kYTab; e += blockDim.x) {
+        const double ea = static_cast<double>(e) * 0.69314718055994530942 / alpha;  // ln(2^(e/alpha))
+        M->tabP[e] = static_cast<float>(fmin(::exp(ea - G), 3.0e38));
+        M->tabM[e] = static_cast<float>(::exp(-ea - G));
+    }
     if (t < kMaxBands) M->band_count[t] = 0;
     if (t != 0) return;
+    M->cw = static_cast<float>(cm1 * 0x1.0p-53);
+    M->inv_alpha_f = static_cast<float>(1.0 / alpha);
+    M->y_one = static_cast<float>(::exp(alpha));
+    M->alpha_one = alpha == 1.0 ? 1u : 0u;
     M->m = 0;
     M->candidates = 0;
     M->near_threshold = 0;
@@ -233,8 +257,19 @@ constexpr int kSampleThreads = 256;
 
 struct SampleSmem {
     double c[kMaxBands + 1];
+    uint64_t bu[kMaxBands + 1];
     unsigned int hist[kMaxBands];
 };
+
+// Adds the warp's points to the band histogram: one shared atomic per distinct
+// band among the lanes (b = kMaxBands for a lane without a point).  All lanes call it.
+__device__ __forceinline__ void hist_add_warp(unsigned int *hist, uint32_t b)
+{
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const unsigned lane = threadIdx.x & 31u;
+    if (b < static_cast<uint32_t>(kMaxBands) && (peers & ((1u << lane) - 1u)) == 0)
+        atomicAdd(&hist[b], static_cast<unsigned int>(__popc(peers)));
+}
 
 // Batch, tile t (one CTA): position p of graph g holds vertex p - pt_off[g]; the
 // FP64 radius (FP64 mode) is stored by position.
@@ -242,6 +277,7 @@ __device__ void sample_tile(Meta *metas, const BatchTables &bt, uint64_t *keys, 
                             uint32_t t, SampleSmem &SS)
 {
     double *c = SS.c;
+    uint64_t *bu = SS.bu;
     unsigned int *hist = SS.hist;
     __syncthreads();  // the CTA's previous item is done with the shared arrays
     const uint4 T = bt.tiles[t];
@@ -250,25 +286,32 @@ __device__ void sample_tile(Meta *metas, const BatchTables &bt, uint64_t *keys, 
     const bool filter = M->filter != 0;
     const double R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
     const uint64_t seed = M->seed;
-    if (threadIdx.x <= B) c[threadIdx.x] = M->c[threadIdx.x];
+    if (threadIdx.x <= B) {
+        c[threadIdx.x] = M->c[threadIdx.x];
+        bu[threadIdx.x] = M->band_u[threadIdx.x];
+    }
     if (threadIdx.x < kMaxBands) hist[threadIdx.x] = 0;
     __syncthreads();
     if (M->error) return;
     const uint32_t first_id = T.y - bt.pt_off[T.x];
-    for (uint32_t j = threadIdx.x; j < T.z; j += blockDim.x) {
-        const uint32_t id = first_id + j, pos = T.y + j;
-        const U64x4 x = draw(id, seed);
-        double r;
-        if (filter) {
-            r = radius_approx(x.x1 >> 11, R, cm1, inv_alpha);
-        } else {
-            r = radius_from_u53(x.x1 >> 11, R, cm1, inv_alpha);
-            r_by_pos[pos] = r;
+    // warp-uniform trip count (the histogram is counted per warp)
+    for (uint32_t j0 = threadIdx.x & ~31u; j0 < T.z; j0 += blockDim.x) {
+        const uint32_t j = j0 + (threadIdx.x & 31u);
+        uint32_t b = kMaxBands;
+        if (j < T.z) {
+            const uint32_t id = first_id + j, pos = T.y + j;
+            const U64x4 x = draw(id, seed);
+            if (filter) {
+                b = band_of_u53(x.x1 >> 11, bu, B);
+            } else {
+                const double r = radius_from_u53(x.x1 >> 11, R, cm1, inv_alpha);
+                r_by_pos[pos] = r;
+                b = band_of(r, c, B);
+            }
+            keys[pos] = (static_cast<uint64_t>(b) << 32) | static_cast<uint32_t>(x.x0 >> 32);
+            ids[pos] = id;
         }
-        const uint32_t b = band_of(r, c, B);
-        keys[pos] = (static_cast<uint64_t>(b) << 32) | static_cast<uint32_t>(x.x0 >> 32);
-        ids[pos] = id;
-        atomicAdd(&hist[b], 1u);
+        hist_add_warp(hist, b);
     }
     __syncthreads();
     if (threadIdx.x < B && hist[threadIdx.x]) atomicAdd(&M->band_count[threadIdx.x], hist[threadIdx.x]);
@@ -327,27 +370,104 @@ __device__ __forceinline__ void filter_values(double ph, double r, double G, con
     *pms = make_float4(P, Mv, S, gam);
 }
 
+// Per-graph constants of filter_values_u53, staged in shared memory.
+struct YTab {
+    float P[kYTab], M[kYTab];
+    float cw, ia, y_one;
+    uint32_t alpha_one;
+    double G, inv_alpha;
+};
+
+// All threads call it; the caller synchronises before the first use.
+__device__ __forceinline__ void load_ytab(YTab &Y, const Meta *M)
+{
+    for (int j = threadIdx.x; j < kYTab; j += blockDim.x) {
+        Y.P[j] = M->tabP[j];
+        Y.M[j] = M->tabM[j];
+    }
+    if (threadIdx.x == 0) {
+        Y.cw = M->cw;
+        Y.ia = M->inv_alpha_f;
+        Y.y_one = M->y_one;
+        Y.alpha_one = M->alpha_one;
+        Y.G = M->G;
+        Y.inv_alpha = M->inv_alpha;
+    }
+}
+
+// Filter-mode values of a generated point from its variates (ua: angle, ur:
+// radius), in FP32 and integer arithmetic (the rare points with r < 1 aside):
+//   angle  angle_hilo_u53: the pair filter_values forms from the FP64 angle;
+//   y      w = U (cosh(alpha R) - 1) as fl(fl(U) cw) (relative error <= 3 u,
+//          u = 2^-24), y = (1 + w) + sqrt(w (w + 2)) in FP32: within 6 u of the
+//          exact y = e^{alpha r} (dy/y = dw / sqrt(w^2 + 2 w) <= dw/w, and three
+//          roundings of positive terms);
+//   P, M   y = 2^e m with m in [sqrt(1/2), sqrt(2)): e^{r - G} = y^{1/alpha} e^{-G}
+//          = tabP[e] m^{1/alpha}, e^{-r-G} = tabM[e] m^{-1/alpha}; m^{+-1/alpha} is
+//          m and 1/m for alpha = 1, else exp2f(+-log2f(m) / alpha) (log2f within
+//          1 ulp, exp2f within 2 ulp: <= 3.7e-7 relative); with the rounding of the
+//          table entry and of the product the relative error is <= 6 u / alpha +
+//          3.7e-7 + 2 u <= 1.2e-6 < kEpsPM for alpha > 1/2;
+//   S      (P - M) / sqrt 2 for r >= 1 (y >= e^alpha), as filter_values; below,
+//          from the radius ln(y) / alpha in FP64 (absolute error <= 6 u / alpha).
+__device__ __forceinline__ void filter_values_u53(uint64_t ua, uint64_t ur, const YTab &Y, float2 *ang,
+                                                  float4 *pms)
+{
+    *ang = angle_hilo_u53(ua);
+    const float wf = u53_to_float(ur) * Y.cw;
+    const float y = (1.0f + wf) + sqrtf(wf * (wf + 2.0f));
+    const int bits = __float_as_int(y);  // y >= 1: normal
+    int e = (bits >> 23) - 126;
+    float m = __int_as_float((bits & 0x007fffff) | 0x3f000000);  // y = 2^e m, m in [1/2, 1)
+    if (m < 0.70710678f) {
+        m *= 2.0f;
+        e -= 1;
+    }
+    e = e < 0 ? 0 : (e >= kYTab ? kYTab - 1 : e);
+    float mp, mm;
+    if (Y.alpha_one) {
+        mp = m;
+        mm = 1.0f / m;
+    } else {
+        const float t = log2f(m) * Y.ia;
+        mp = exp2f(t);
+        mm = exp2f(-t);
+    }
+    const float P = Y.P[e] * mp;
+    const float Mv = Y.M[e] * mm;
+    float S, gam;
+    if (y >= Y.y_one) {
+        S = (P - Mv) * 0.70710678118654752f;
+        gam = kEpsPM * ((P + Mv) / (P - Mv)) + 2.0f * kEps32;
+    } else if (y > 1.0f) {
+        const double r = ::log(static_cast<double>(y)) * Y.inv_alpha;
+        S = static_cast<float>(::sinh(r) * ::exp(-Y.G) * 1.4142135623730951);
+        gam = kEpsPM * static_cast<float>(::cosh(r) / ::sinh(r)) + 2.0f * kEps32;
+    } else {
+        S = 0.0f;
+        gam = 0.0f;
+    }
+    *pms = make_float4(P, Mv, S, gam);
+}
+
 // Batch gathers, tile t (one CTA); ids are local, the FP64 radius is by position.
 __device__ void gather_filter_tile(const Meta *metas, const BatchTables &bt, const uint64_t *keys,
-                                   const uint32_t *sids, const SortedPoints &P, uint32_t t, float *etab)
+                                   const uint32_t *sids, const SortedPoints &P, uint32_t t, YTab &Y)
 {
-    __syncthreads();  // the CTA's previous item is done with etab
+    __syncthreads();  // the CTA's previous item is done with Y
     const uint4 T = bt.tiles[t];
     const Meta *M = metas + T.x;
-    for (int j = threadIdx.x; j <= 2 * kExpTab; j += blockDim.x) etab[j] = M->etab[j];
+    load_ytab(Y, M);
     __syncthreads();
     if (M->error || !M->filter) return;
-    const double G = M->G, R = M->R, cm1 = M->cm1, inv_alpha = M->inv_alpha;
     const uint64_t seed = M->seed;
     for (uint32_t j = threadIdx.x; j < T.z; j += blockDim.x) {
         const uint32_t p = T.y + j;
         const uint32_t id = sids[p];
         const U64x4 x = draw(id, seed);
-        const double ph = phi_from_u53(x.x0 >> 11);
-        const double r = radius_approx(x.x1 >> 11, R, cm1, inv_alpha);
         float2 a;
         float4 q;
-        filter_values(ph, r, G, etab, &a, &q);
+        filter_values_u53(x.x0 >> 11, x.x1 >> 11, Y, &a, &q);
         P.akey[p] = static_cast<uint32_t>(keys[p]);
         P.ang[p] = a;
         P.pms[p] = q;

@@ -49,8 +49,17 @@ def fma(a, b, c):
     return (np.asarray(a, f64) * np.asarray(b, f64) + np.asarray(c, f64)).astype(f32)
 
 
-def filter_values(ph, r, G):
-    """Angle hi/lo and (P, M, S, gamma) of points with FP64 angle ph and radius r."""
+# Largest relative error of the stored P and M of a generated point
+# (filter_values_u53: y from the variate in FP32, then the exponent tables),
+# established by test_generated_filter_values_within_the_bound below; the
+# decision and window checks perturb P and M by it.
+EPS_PM_U53 = 1.2e-6
+
+
+def filter_values(ph, r, G, eP=0.0, eM=0.0, er=0.0):
+    """Angle hi/lo and (P, M, S, gamma) of points with FP64 angle ph and radius r;
+    P and M multiplied by (1 + eP), (1 + eM) and the radius of the small-r
+    branch shifted by er (the stored values' errors)."""
     K = C["kExpTab"]
     etab = np.exp(np.arange(-K, K + 1, dtype=f64)).astype(f32)
     hi = ph.astype(f32)
@@ -61,7 +70,9 @@ def filter_values(ph, r, G):
         f = (x - kd).astype(f32)
         return (etab[kd.astype(np.int64) + K] * np.exp(f)).astype(f32)
 
-    P, M = exp_split(r - G), exp_split(-r - G)
+    P = (exp_split(r - G) * (1.0 + np.asarray(eP, f64))).astype(f32)
+    M = (exp_split(-r - G) * (1.0 + np.asarray(eM, f64))).astype(f32)
+    r = np.clip(r + er, 0.0, None)
     big = r >= 1.0
     with np.errstate(divide="ignore", invalid="ignore"):
         S_big = ((P - M) * f32(0.70710678118654752)).astype(f32)
@@ -129,11 +140,14 @@ def test_filter_decisions_are_sound(O, R):
     n = 20000
     phv, rv, phw, rw, delta = _pairs(rng, R, n)
     G = 0.5 * math.log(2 * math.cosh(R))
-    # the sampler's FP32-assisted radius is within kDeltaR / 2 of the FP64 one
-    eps = C["kDeltaR"] * 0.54
-    rva = np.clip(rv + rng.choice([-eps, eps, 0.0], n), 0, R)
-    rwa = np.clip(rw + rng.choice([-eps, eps, 0.0], n), 0, R)
-    dec = filter_decide(filter_values(phv, rva, G), filter_values(phw, rwa, G))
+    # stored P and M within EPS_PM_U53 (relative) of the exact ones, the small-r
+    # branch's radius within 6 u / alpha (alpha > 1/2)
+    e, er = EPS_PM_U53, 12 * 2.0 ** -24
+
+    def err():
+        return rng.choice([-e, e, 0.0], n), rng.choice([-e, e, 0.0], n), rng.choice([-er, er, 0.0], n)
+
+    dec = filter_decide(filter_values(phv, rv, G, *err()), filter_values(phw, rw, G, *err()))
     truth = np.array([O.edge(phv[i], rv[i], phw[i], rw[i], R) for i in range(n)], dtype=np.int64)
     decided = dec != 2
     wrong = np.flatnonzero(decided & (dec != truth))
@@ -295,7 +309,10 @@ def test_windows_contain_every_edge_and_cores_only_edges(O, n, k, alpha):
             d = np.abs(kv - kw)
             dists.append(np.minimum(d, 2**32 - d))
         kd, kd_core = np.maximum(*dists), np.minimum(*dists)
-        v = filter_values(phv, rv_a, G)
+        # the owner's stored values: P and M within EPS_PM_U53 of those of its radius
+        # rv (a third low, a third high, a third exact)
+        ev = rng.choice([-EPS_PM_U53, EPS_PM_U53, 0.0], (2, count))
+        v = filter_values(phv, rv, G, ev[0], ev[1], rng.choice([-12, 12, 0], count) * 2.0 ** -24)
         for band in np.unique(i):
             sel = np.flatnonzero(i == band)
             Bc = band_constants(R, c, band, G)
@@ -339,46 +356,212 @@ def test_window_checks_detect_planted_errors(O, monkeypatch):
 
 
 # ---------------------------------------------------------------------------
-# The sampler's FP32-assisted radius (band assignment and filter values): within
-# kDeltaR of the FP64 radius for every alpha > 1/2 and alpha R up to the filter's
-# limit, with logf taken 2 ulp off in either direction.
+# Generated points in filter mode: the band from the radial variate and the
+# filter values from the variates, without FP64 (band_of_u53, angle_hilo_u53,
+# filter_values_u53), restated operation by operation.
 
-def radius_approx(u53, R, alpha, s):
-    cm1 = math.cosh(alpha * R) - 1.0
-    U = u53.astype(f64) * 2.0 ** -53
-    wf = (U * cm1).astype(f32)
-    y = ((f32(1.0) + wf).astype(f32) + np.sqrt((wf * (wf + f32(2.0)).astype(f32)).astype(f32))).astype(f32)
+K_SIG = 0x1921FB54442D18  # significand of 2 pi: kPhiScale = K_SIG 2^-103
+
+
+def angle_hilo_u53(u):
+    """The device's integer construction of the angle's hi/lo floats."""
+    if u == 0:
+        return 0.0, 0.0
+    prod = u * K_SIG
+    sh = prod.bit_length() - 53
+    q, rem = prod >> sh, prod & ((1 << sh) - 1)
+    if sh and (rem > (1 << (sh - 1)) or (rem == (1 << (sh - 1)) and q & 1)):
+        q += 1
+        if q == 1 << 53:
+            q >>= 1
+            sh += 1
+    if sh > 53 or (sh == 53 and q >= K_SIG):
+        q, sh = K_SIG - 1, 53
+    h, r = q >> 29, q & ((1 << 29) - 1)
+    if r > (1 << 28) or (r == (1 << 28) and h & 1):
+        h += 1
+    lo_i = q - (h << 29)
+    hi = float(np.float32(h)) * 2.0 ** (sh - 74)
+    lo = float(np.float32(lo_i)) * 2.0 ** (sh - 103)  # int -> float rounds to nearest even
+    return hi, lo
+
+
+def test_generated_angle_pair_is_the_fp64_pair():
+    """The integer construction gives bit for bit the pair float(phi),
+    float(phi - float(phi)) of phi = fl(u53 * 2pi 2^-53) (clamped below 2 pi):
+    small variates (many rounding ties), random ones, and the extremes."""
+    rng = np.random.default_rng(53)
+    us = np.concatenate([np.arange(0, 4096), rng.integers(0, 2**53, 60000, dtype=np.int64),
+                         (2.0 ** rng.uniform(0, 53, 20000)).astype(np.int64),
+                         np.array([2**52, 2**52 + 1, 2**53 - 2, 2**53 - 1, 2**29 + 2**28], dtype=np.int64)])
+    two_pi = float.fromhex("0x1.921fb54442d18p+2")
+    ph = us.astype(f64) * float.fromhex("0x1.921fb54442d18p-51")
+    ph = np.where(ph < two_pi, ph, np.nextafter(two_pi, 0.0))
+    hi = ph.astype(f32)
+    lo = (ph - hi.astype(f64)).astype(f32)
+    got = np.array([angle_hilo_u53(int(u)) for u in us])
+    assert np.array_equal(got[:, 0].astype(f32), hi) and np.array_equal(got[:, 1].astype(f32), lo)
+    # the restatement is exact in float64 (powers of two times <= 29-bit integers)
+    assert np.array_equal(got[:, 0], hi.astype(f64)) and np.array_equal(got[:, 1], lo.astype(f64))
+
+
+def _cm1(O, alpha, R):
+    return float(O.dm("cosh", np.array([alpha * R]))[0]) - 1.0
+
+
+def filter_values_u53(O, ur, alpha, R, s_log=0, s_exp=0):
+    """P, M, S, gamma of generated points from their radial variates, as the
+    device computes them; log2f and exp2f moved by their documented largest
+    errors (1 and 2 ulp) in the direction s_log, s_exp."""
+    G = 0.5 * math.log(2.0 * float(O.dm("cosh", np.array([R]))[0]))
+    cm1 = _cm1(O, alpha, R)
+    cw = f32(cm1 * 2.0 ** -53)
+    uf = ur.astype(f64).astype(f32)  # exact in float64, one rounding to float32
+    wf = (uf * cw).astype(f32)
+    y = ((f32(1) + wf).astype(f32) + np.sqrt((wf * (wf + f32(2)).astype(f32)).astype(f32))).astype(f32)
     m, e = np.frexp(y)
     low = m < f32(0.70710678)
-    m = np.where(low, (m * f32(2.0)).astype(f32), m).astype(f32)
-    e = np.where(low, e - 1, e)
-    lg = e.astype(f64) * 0.69314718055994530942 + bump(np.log(m).astype(f32), 2 * s).astype(f64)
-    r = lg * (1.0 / alpha)
-    return np.where(r < R, np.maximum(r, 0.0), R)
+    m = np.where(low, (m * f32(2)).astype(f32), m).astype(f32)
+    e = np.clip(np.where(low, e - 1, e), 0, 65)
+    ea = e * 0.69314718055994530942 / alpha
+    tabP = np.minimum(np.exp(ea - G), 3.0e38).astype(f32)
+    tabM = np.exp(-ea - G).astype(f32)
+    if alpha == 1.0:
+        mp, mm = m, (f32(1) / m).astype(f32)
+    else:
+        ia = f32(1.0 / alpha)
+        t = (bump(np.log2(m).astype(f32), s_log) * ia).astype(f32)
+        mp = bump(np.exp2(t).astype(f32), 2 * s_exp)
+        mm = bump(np.exp2(-t).astype(f32), 2 * s_exp)
+    P = (tabP * mp).astype(f32)
+    M = (tabM * mm).astype(f32)
+    y_one = f32(math.exp(alpha))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        S_big = ((P - M) * f32(0.70710678118654752)).astype(f32)
+        g_big = (C["kEpsPM"] * ((P + M) / (P - M)) + f32(2) * C["kEps32"]).astype(f32)
+        r = np.log(y.astype(f64)) * (1.0 / alpha)
+        S_small = (np.sinh(r) * math.exp(-G) * 1.4142135623730951).astype(f32)
+        g_small = (C["kEpsPM"] * (np.cosh(r) / np.sinh(r)).astype(f32) + f32(2) * C["kEps32"]).astype(f32)
+    S = np.where(y >= y_one, S_big, np.where(y > f32(1), S_small, f32(0))).astype(f32)
+    gam = np.where(y >= y_one, g_big, np.where(y > f32(1), g_small, f32(0))).astype(f32)
+    return P, M, S, gam, y, G
+
+
+def _variates(rng):
+    return np.concatenate([rng.integers(0, 2**53, 1500, dtype=np.int64),
+                           (2.0 ** rng.uniform(0, 53, 700)).astype(np.int64),
+                           np.array([0, 1, 2, 3, 2**20, 2**40, 2**52, 2**53 - 2, 2**53 - 1], dtype=np.int64)])
 
 
 @pytest.mark.parametrize("alpha,R", [(0.51, 30.0), (0.55, 25.0), (0.75, 25.564), (1.0, 23.5089), (1.5, 16.0),
                                      (3.0, 14.66), (1.375, 32.0), (1.0, 31.9), (0.51, 3.0), (1.0, 2.0)])
-def test_sampler_radius_within_kDeltaR(alpha, R):
+def test_generated_filter_values_within_the_bound(O, alpha, R):
+    """P = e^{r - G} and M = e^{-r - G} of generated points, formed from y in FP32
+    and the exponent tables, stay within EPS_PM_U53 < kEpsPM of the exact values
+    of the point's radius (inverse CDF of Eq. 1 in 120-bit arithmetic), and S
+    within its stored bound gamma, for every alpha > 1/2 and alpha R up to the
+    filter's limit, with log2f / exp2f at either end of their error."""
     mpmath = pytest.importorskip("mpmath")
-    mpmath.mp.prec = 200
+    mpmath.mp.prec = 120
+    assert EPS_PM_U53 < float(C["kEpsPM"])
     rng = np.random.default_rng(int(alpha * 100 + R))
-    u53 = np.concatenate([rng.integers(0, 2**53, 3000, dtype=np.int64),
-                          (2.0 ** rng.uniform(0, 53, 1000)).astype(np.int64),
-                          np.array([0, 1, 2, 3, 2**20, 2**40, 2**52, 2**53 - 2, 2**53 - 1], dtype=np.int64)])
-    cm1 = mpmath.cosh(mpmath.mpf(alpha) * R) - 1
-    exact = np.array([float(mpmath.acosh(1 + mpmath.mpf(int(u)) / 2**53 * cm1) / alpha) for u in u53])
-    exact = np.minimum(exact, R)
-    for s in (-1, 0, 1):
-        err = np.abs(radius_approx(u53, R, alpha, s) - exact)
-        assert err.max() <= 5.4e-7, (s, err.max(), u53[err.argmax()])
-    assert 5.4e-7 < C["kDeltaR"]
+    ur = _variates(rng)
+    cm1 = mpmath.mpf(_cm1(O, alpha, R))
+    Gm = None
+    exact = []
+    for u in ur:
+        r = mpmath.acosh(1 + mpmath.mpf(int(u)) / 2**53 * cm1) / alpha
+        exact.append(min(r, mpmath.mpf(R)))
+    worst = 0.0
+    for s_log in (-1, 0, 1):
+        for s_exp in (-1, 0, 1):
+            P, M, S, gam, y, G = filter_values_u53(O, ur, alpha, R, s_log, s_exp)
+            if Gm is None:
+                Gm = mpmath.mpf(G)
+                Pe = np.array([float(mpmath.exp(r - Gm)) for r in exact])
+                Me = np.array([float(mpmath.exp(-r - Gm)) for r in exact])
+                Se = np.array([float(mpmath.sinh(r) * mpmath.exp(-Gm) * mpmath.sqrt(2)) for r in exact])
+            eP = np.abs(P.astype(f64) / Pe - 1)
+            eM = np.abs(M.astype(f64) / Me - 1)
+            worst = max(worst, eP.max(), eM.max())
+            assert eP.max() <= EPS_PM_U53 and eM.max() <= EPS_PM_U53, (s_log, s_exp, eP.max(), eM.max())
+            # S within gamma (relative) where y > 1; where y rounds to 1 the point is
+            # stored at r = 0 (S = 0, gamma = 0) and its true radius is below
+            # 12 u / alpha: an absolute error of S that the relative term of the
+            # filter's bound covers (X >= (P_v + M_v) e^{-G} ~ 2 S_v e^{-G}/sqrt 2)
+            pos = y > f32(1)
+            eS = np.abs(S.astype(f64)[pos] / Se[pos] - 1)
+            assert np.all(eS <= gam.astype(f64)[pos]), (s_log, s_exp, (eS - gam[pos]).max())
+            r0 = np.array([float(r) for r in exact])[~pos]
+            assert np.all(S[~pos] == 0) and np.all(r0 <= 12 * 2.0 ** -24 / alpha)
+    assert worst > 0.02 * EPS_PM_U53  # the comparison is not vacuous
 
 
-def test_filter_range_keeps_the_sampler_radius_finite():
+def test_generated_filter_values_bound_is_tight_enough_to_catch_a_dropped_term(O):
+    """A planted mistake in the restatement (the table without the e^-G factor's
+    rounding direction, here y used without its sqrt term) breaks the bound."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 120
+    alpha, R = 1.0, 23.5089
+    ur = _variates(np.random.default_rng(7))
+    P, M, S, gam, y, G = filter_values_u53(O, ur, alpha, R)
+    cm1 = mpmath.mpf(_cm1(O, alpha, R))
+    # y without the sqrt term: 1 + w, about half of y for large w
+    wf = (ur.astype(f64).astype(f32) * f32(float(cm1) * 2.0 ** -53)).astype(f32)
+    bad_y = (f32(1) + wf).astype(f32)
+    bad_P = (bad_y.astype(f64) * math.exp(-G))
+    Pe = np.array([float(mpmath.exp(mpmath.acosh(1 + mpmath.mpf(int(u)) / 2**53 * cm1) / alpha - mpmath.mpf(G)))
+                   for u in ur])
+    assert np.abs(bad_P / Pe - 1).max() > EPS_PM_U53
+    assert np.abs(P.astype(f64) / Pe - 1).max() <= EPS_PM_U53
+
+
+def band_thresholds(c, alpha, cm1):
+    """The plan's band thresholds on the radial variate: ceil(F(c_j) 2^53)."""
+    B = len(c) - 1
+    bu = np.zeros(B + 1, dtype=np.int64)
+    for j in range(1, B):
+        sh = math.sinh(0.5 * alpha * c[j])
+        T = math.ceil(2.0 * sh * sh / cm1 * 2.0 ** 53)
+        bu[j] = min(max(T, 0), 2**53)
+    bu[B] = 2**53
+    return bu
+
+
+@pytest.mark.parametrize("n,k,alpha", [(10**7, 200, 1.0), (10**6, 16, 0.75), (5000, 60, 1.5), (10**5, 8, 0.55)])
+def test_band_thresholds_bound_the_radius(O, n, k, alpha):
+    """A variate at or above the threshold of band j has radius >= c_j - 1e-13, one
+    below the threshold of band j + 1 has radius <= c_{j+1} + 1e-13 (radius: the
+    oracle's FP64 inverse CDF), checked at every threshold and on random variates;
+    a threshold one step too low (planted) puts a radius below its band."""
+    R = O.target_radius(n, k, alpha)
+    B = O.default_bands(n)
+    c = O.boundaries(R, B)
+    cm1 = _cm1(O, alpha, R)
+    bu = band_thresholds(c, alpha, cm1)
+    assert np.all(np.diff(bu) >= 0)
+    rng = np.random.default_rng(n % 1000 + k)
+    near = np.concatenate([bu[1:B, None] + np.arange(-3, 4)[None, :]]).ravel()
+    us = np.concatenate([near, rng.integers(0, 2**53, 5000, dtype=np.int64),
+                         (2.0 ** rng.uniform(0, 53, 2000)).astype(np.int64)])
+    us = np.clip(us, 0, 2**53 - 1)
+    r = O.radius_from_u53(us, alpha, R)
+    band = np.searchsorted(bu, us, side="right") - 1
+    assert np.all(band >= 0) and np.all(band < B)
+    assert np.all(r >= c[band] - 1e-13) and np.all(r <= c[band + 1] + 1e-13)
+    # the thresholds are tight: one below band j's threshold lies below c_j
+    below = O.radius_from_u53(np.maximum(bu[1:B] - 1, 0), alpha, R)
+    assert np.all(below <= c[1:B] + 1e-13)
+    low = bu.copy()
+    low[1:B] = np.maximum(low[1:B] - max(1, int(2**53 * 1e-9)), 0)
+    band = np.searchsorted(low, us, side="right") - 1
+    assert np.any(r < c[band] - 1e-13)
+
+
+def test_filter_range_keeps_y_finite():
     """The filter is used only for alpha R <= kFilterMaxAlphaR; there the FP32
-    w (w + 2) of the approximate radius must not overflow (it would put every
-    point at R), and just above the limit it would."""
+    w (w + 2) of y must not overflow (it would make every y infinite), and just
+    above the limit it would."""
     src = open(os.path.join(CSRC, "common.cuh")).read()
     lim = float(re.search(r"constexpr double kFilterMaxAlphaR = ([0-9.]+);", src).group(1))
     for aR, finite in ((lim, True), (45.2, False)):
@@ -386,10 +569,9 @@ def test_filter_range_keeps_the_sampler_radius_finite():
         with np.errstate(over="ignore"):
             prod = (wf * (wf + f32(2.0)).astype(f32)).astype(f32)
         assert np.isfinite(prod) == finite, aR
-    # at the limit the approximate radius of the largest variate is still right
-    alpha, R = 1.375, lim / 1.375
-    r = radius_approx(np.array([2**53 - 1], dtype=np.int64), R, alpha, 0)
-    assert abs(r[0] - R) < 5.4e-7
+    # and y's exponent stays inside the tables: y < 2^65
+    y = f32(2) * f32(math.cosh(lim)) + f32(2)
+    assert np.frexp(y)[1] <= 65
 
 
 def window_fp64(rv, c, i, R):
