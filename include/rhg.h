@@ -413,6 +413,25 @@ int rhg_update_edges(const double *d_phi, const double *d_r, uint64_t n, double 
                      uint32_t *d_new_pairs, uint64_t capacity_edges, void *stream, rhg_result *result);
 
 /*
+ * rhg_sort_keys -- the angular sort of Alg. 1 (points by band, then by angle key
+ * within the band) as the generator runs it on its own points, on caller keys:
+ * d_keys[i] = (band << 32) | angle key of point i, band < num_bands; band j is
+ * cut into 2^bucket_bits[j] buckets (bucket_bits[j] <= 24, a host array) by the
+ * top bits of the angle key.  Writes d_sorted_keys (n uint64) and d_sorted_ids (n
+ * uint32: the i of each key), ascending by (key, i).  Every key distribution is
+ * sorted; a bucket of more than 2048 keys, or more than 32 keys of one bucket
+ * sharing the next 8 angle-key bits, takes a slower path (the generator sizes its
+ * buckets from the band's expected count: 512 to 1024 uniform angles each).
+ * Workspace: rhg_sort_keys_workspace_bytes, 256-byte aligned.  Errors:
+ * INVALID_ARG (arguments; a band >= num_bands in d_keys, found on the device),
+ * OOM (workspace too small), CUDA.  Synchronises the stream.
+ */
+int rhg_sort_keys_workspace_bytes(uint64_t n, uint32_t num_bands, const uint32_t *bucket_bits, size_t *bytes);
+int rhg_sort_keys(const uint64_t *d_keys, uint64_t n, uint32_t num_bands, const uint32_t *bucket_bits,
+                  void *d_workspace, size_t workspace_bytes, uint64_t *d_sorted_keys, uint32_t *d_sorted_ids,
+                  void *stream);
+
+/*
  * rhg_dm_eval -- the library's deterministic FP64 functions on a device array,
  * for verification against an independent implementation: fn = 0 exp, 1 log,
  * 2 cos, 3 cosh, 4 sinh, 5 asinh (y >= 0; dynamic model).  d_out[i] = f(d_in[i]),

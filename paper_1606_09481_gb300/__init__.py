@@ -129,6 +129,8 @@ def _load_locked() -> ctypes.CDLL:
     L.rhg_edges_from_points.argtypes = [_p, _p, _c_u64, _c_dbl, _c_u32, _c_dbl, _c_u32, _p, _c_size, _p,
                                         _c_u64, _p, ctypes.POINTER(Result)]
     L.rhg_dm_eval.argtypes = [ctypes.c_int, _p, _p, _c_u64, _p]
+    L.rhg_sort_keys_workspace_bytes.argtypes = [_c_u64, ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_size_t)]
+    L.rhg_sort_keys.argtypes = [_p, _c_u64, ctypes.c_uint32, _p, _p, ctypes.c_size_t, _p, _p, _p]
     L.rhg_set_stage_events.argtypes = [_p, _c_u32]
     L.rhg_launch_count.restype = _c_u64
     L.rhg_launch_count.argtypes = []
@@ -551,6 +553,28 @@ def update_edges(phi, r, R, moved_ids, old_pairs, num_bands=0, band_ratio=0.0, f
         cap = int(res.m)
     _check(rc, "rhg_update_edges", res)
     return out[: 2 * res.m].view(-1, 2), res
+
+
+def sort_keys(keys, num_bands: int, bucket_bits):
+    """rhg_sort_keys: keys (int64 CUDA tensor of (band << 32) | angle key) sorted
+    by (key, index) through the generator's bucket sort; bucket_bits[j] = the
+    top angle-key bits that cut band j into buckets.  Returns (sorted keys,
+    indices) as int64 / int32 CUDA tensors."""
+    torch = _torch()
+    keys = keys.contiguous()
+    n = keys.numel()
+    bits = (ctypes.c_uint32 * len(bucket_bits))(*[int(b) for b in bucket_bits])
+    nbytes = ctypes.c_size_t(0)
+    _check(load().rhg_sort_keys_workspace_bytes(n, num_bands, bits, ctypes.byref(nbytes)),
+           "rhg_sort_keys_workspace_bytes")
+    ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=keys.device)
+    base = ws.data_ptr()
+    ptr = (base + 255) // 256 * 256
+    out_k = torch.empty(n, dtype=torch.int64, device=keys.device)
+    out_i = torch.empty(n, dtype=torch.int32, device=keys.device)
+    _check(load().rhg_sort_keys(keys.data_ptr(), n, num_bands, bits, ptr, nbytes.value, out_k.data_ptr(),
+                                out_i.data_ptr(), _stream()), "rhg_sort_keys")
+    return out_k, out_i
 
 
 def dm_eval(fn: str, x):

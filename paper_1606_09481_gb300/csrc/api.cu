@@ -54,7 +54,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 // Byte offsets of every buffer inside the caller's workspace.
 struct Layout {
     size_t meta, keys0, keys1, ids0, ids1, r_by_id, akey, id, ang, pms, phi, r, ch, sh, heavy, recheck, bidx,
-        sort_tmp, csr0, csr1, total;
+        bcount, bstart, sort_tmp, csr0, csr1, total;
     uint32_t heavy_cap, recheck_cap;
 };
 
@@ -170,6 +170,8 @@ Layout make_layout(uint64_t n, uint64_t csr_entries, uint64_t chunk_extra = 0)
     L.heavy = take(static_cast<size_t>(L.heavy_cap) * 16);
     L.recheck = take(static_cast<size_t>(L.recheck_cap) * 8);
     L.bidx = take(static_cast<size_t>(index_entries(n)) * 4);
+    L.bcount = take(static_cast<size_t>(bucket_entries(n)) * 4);
+    L.bstart = take(static_cast<size_t>(bucket_entries(n) + 1) * 4);
     const size_t sort_points = radix_temp_bytes(n);
     const size_t sort_csr = csr_entries ? radix_temp_bytes(csr_entries) : 0;
     L.sort_tmp = take(sort_points > sort_csr ? sort_points : sort_csr);
@@ -307,16 +309,50 @@ Status enqueue_points(const Pipeline &pl, const PlanArgs &pa, const double *phi_
 {
     Status st;
     Meta *M = pl.meta();
+    uint64_t *k0 = at<uint64_t>(pl.ws, pl.L.keys0), *k1 = at<uint64_t>(pl.ws, pl.L.keys1);
+    uint32_t *i0 = at<uint32_t>(pl.ws, pl.L.ids0), *i1 = at<uint32_t>(pl.ws, pl.L.ids1);
+    double *rid = at<double>(pl.ws, pl.L.r_by_id);
+    if (!phi_in) {
+        // generated points (uniform angles): bucket sort with the gather fused in
+        BucketArgs ba{};
+        ba.M = M;
+        ba.n = pl.n;
+        ba.seed = pa.seed;
+        ba.counts = at<uint32_t>(pl.ws, pl.L.bcount);
+        ba.start = at<uint32_t>(pl.ws, pl.L.bstart);
+        ba.comp = k1;
+        ba.scratch = k0;
+        ba.r_by_id = rid;
+        ba.P = pl.sorted(k1);
+        PlanArgs pb = pa;
+        pb.bucket_counts = ba.counts;
+        mark(RHG_STAGE_PLAN, false, stream);
+        st = launch_plan(M, pb, stream);
+        if (st.code) return st;
+        mark(RHG_STAGE_PLAN, true, stream);
+        mark(RHG_STAGE_SAMPLE, false, stream);
+        st = launch_sample(M, pl.n, pa.seed, k0, nullptr, rid, ba.counts, stream);
+        if (st.code) return st;
+        mark(RHG_STAGE_SAMPLE, true, stream);
+        mark(RHG_STAGE_SORT, false, stream);
+        st = launch_bucket_scan(ba, stream);
+        if (st.code) return st;
+        st = launch_bucket_scatter(ba, k0, stream);
+        if (st.code) return st;
+        mark(RHG_STAGE_SORT, true, stream);
+        mark(RHG_STAGE_GATHER, false, stream);
+        st = launch_bucket_sort(ba, true, stream);
+        if (st.code) return st;
+        mark(RHG_STAGE_GATHER, true, stream);
+        *P_out = ba.P;
+        return st;
+    }
     mark(RHG_STAGE_PLAN, false, stream);
     st = launch_plan(M, pa, stream);
     if (st.code) return st;
     mark(RHG_STAGE_PLAN, true, stream);
-    uint64_t *k0 = at<uint64_t>(pl.ws, pl.L.keys0), *k1 = at<uint64_t>(pl.ws, pl.L.keys1);
-    uint32_t *i0 = at<uint32_t>(pl.ws, pl.L.ids0), *i1 = at<uint32_t>(pl.ws, pl.L.ids1);
-    double *rid = at<double>(pl.ws, pl.L.r_by_id);
     mark(RHG_STAGE_SAMPLE, false, stream);
-    if (phi_in) st = launch_load_points(M, pl.n, phi_in, r_in, k0, i0, stream);
-    else st = launch_sample(M, pl.n, pa.seed, k0, i0, rid, stream);
+    st = launch_load_points(M, pl.n, phi_in, r_in, k0, i0, stream);
     if (st.code) return st;
     mark(RHG_STAGE_SAMPLE, true, stream);
     mark(RHG_STAGE_SORT, false, stream);
@@ -811,6 +847,47 @@ bool plan_layout(const rhg_batch_plan *plan, BatchLayout &L)
 
 using namespace rhg;
 
+// rhg_sort_keys on validated arguments: the bucket tables go to the workspace's
+// Meta block, then count, scan, scatter and the per-bucket sort; *err = the
+// device's error word.
+Status sort_keys(const uint64_t *d_keys, uint64_t n, uint32_t num_bands, const uint32_t *bucket_bits, void *d_ws,
+                 uint64_t *d_sorted_keys, uint32_t *d_sorted_ids, cudaStream_t s, uint32_t *err)
+{
+    Status st;
+    Meta h{};
+    h.B = num_bands;
+    uint32_t off = 0;
+    for (uint32_t j = 0; j < num_bands; ++j) {
+        h.bk_off[j] = off;
+        h.bk_bits[j] = bucket_bits[j];
+        off += 1u << bucket_bits[j];
+    }
+    h.bk_off[num_bands] = off;
+    h.nbuckets = off;
+    char *w = static_cast<char *>(d_ws);
+    const size_t o_counts = align_up(sizeof(Meta)), o_start = o_counts + align_up(uint64_t{off} * 4),
+                 o_comp = o_start + align_up((uint64_t{off} + 1) * 4), o_scratch = o_comp + align_up(n * 8);
+    BucketArgs ba{};
+    ba.M = reinterpret_cast<Meta *>(w);
+    ba.n = n;
+    ba.counts = reinterpret_cast<uint32_t *>(w + o_counts);
+    ba.start = reinterpret_cast<uint32_t *>(w + o_start);
+    ba.comp = reinterpret_cast<uint64_t *>(w + o_comp);
+    ba.scratch = reinterpret_cast<uint64_t *>(w + o_scratch);
+    ba.out_keys = d_sorted_keys;
+    ba.out_ids = d_sorted_ids;
+    RHG_CUDA_TRY(cudaMemcpyAsync(ba.M, &h, sizeof(Meta), cudaMemcpyHostToDevice, s));
+    RHG_CUDA_TRY(cudaMemsetAsync(ba.counts, 0, uint64_t{off} * 4, s));
+    st = launch_bucket_count(ba, d_keys, s);
+    if (!st.code) st = launch_bucket_scan(ba, s);
+    if (!st.code) st = launch_bucket_scatter(ba, d_keys, s);
+    if (!st.code) st = launch_bucket_sort(ba, false, s);
+    if (st.code) return st;
+    RHG_CUDA_TRY(cudaMemcpyAsync(err, &ba.M->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    RHG_CUDA_TRY(cudaStreamSynchronize(s));
+    return st;
+}
+
 extern "C" {
 
 const char *rhg_status_str(int status)
@@ -1258,6 +1335,39 @@ int rhg_update_edges(const double *d_phi, const double *d_r, uint64_t n, double 
     if (h.work_counter != moved_count) return RHG_ERR_INVALID_ARG;  // an id repeated or out of range
     if (h.m > capacity_edges) return RHG_ERR_OVERFLOW;
     return RHG_OK;
+}
+
+int rhg_sort_keys_workspace_bytes(uint64_t n, uint32_t num_bands, const uint32_t *bucket_bits, size_t *bytes)
+{
+    if (!bytes || !bucket_bits || num_bands < 1 || num_bands > static_cast<uint32_t>(kMaxBands) ||
+        n > 0xFFFFFFFFull)
+        return RHG_ERR_INVALID_ARG;
+    uint64_t nb = 0;
+    for (uint32_t j = 0; j < num_bands; ++j) {
+        if (bucket_bits[j] > 24) return RHG_ERR_INVALID_ARG;
+        nb += uint64_t{1} << bucket_bits[j];
+    }
+    if (nb > 0xFFFFFFFEull) return RHG_ERR_INVALID_ARG;
+    *bytes = align_up(sizeof(Meta)) + align_up(nb * 4) + align_up((nb + 1) * 4) + 2 * align_up(n * 8);
+    return RHG_OK;
+}
+
+int rhg_sort_keys(const uint64_t *d_keys, uint64_t n, uint32_t num_bands, const uint32_t *bucket_bits,
+                  void *d_workspace, size_t workspace_bytes, uint64_t *d_sorted_keys, uint32_t *d_sorted_ids,
+                  void *stream)
+{
+    size_t need = 0;
+    int rc = rhg_sort_keys_workspace_bytes(n, num_bands, bucket_bits, &need);
+    if (rc) return rc;
+    if (n && (!d_keys || !d_sorted_keys || !d_sorted_ids || !d_workspace)) return RHG_ERR_INVALID_ARG;
+    if (!n) return RHG_OK;
+    if (reinterpret_cast<uintptr_t>(d_workspace) & 255) return RHG_ERR_INVALID_ARG;
+    if (workspace_bytes < need) return RHG_ERR_OOM;
+    uint32_t err = 0;
+    const Status st = sort_keys(d_keys, n, num_bands, bucket_bits, d_workspace, d_sorted_keys, d_sorted_ids,
+                                static_cast<cudaStream_t>(stream), &err);
+    if (st.code) return st.code;
+    return err ? RHG_ERR_INVALID_ARG : RHG_OK;
 }
 
 int rhg_dm_eval(int fn, const double *d_in, double *d_out, uint64_t count, void *stream)

@@ -20,6 +20,13 @@ __host__ __device__ constexpr uint64_t index_entries(uint64_t n) { return n / kB
 constexpr int kExpTab = 64;  // e^k table for k = -64..64 (FP32 filter values)
 constexpr int kYTab = 66;    // 2^(+-e/alpha) e^-G tables for the exponents e = 0..65 of y (filter_values_u53)
 constexpr uint32_t kClaimCounters = 16;  // work-claim counters of the range query (Meta::claim)
+// bucket sort of generated points (angular sort within each band): band j is cut
+// into 2^bits_j buckets by the top bits of the angle key, about kBucketTarget to
+// 2 kBucketTarget expected points each; buckets of up to kBucketCap points are
+// sorted in shared memory.  bucket_entries(n) bounds the buckets of all bands.
+constexpr uint32_t kBucketTarget = 512;
+constexpr uint32_t kBucketCap = 2048;
+__host__ __device__ constexpr uint64_t bucket_entries(uint64_t n) { return n / kBucketTarget + kMaxBands + 1; }
 constexpr int kMaxStageMarks = 32;       // stage timestamps of the persistent batch launch
 
 // ---------------------------------------------------------------------------
@@ -72,6 +79,11 @@ struct Meta {
     float inv_alpha_f;               // 1 / alpha rounded to float
     float y_one;                     // e^alpha rounded to float: y >= y_one means r >= 1 (about)
     uint32_t alpha_one;              // alpha == 1: m^(1/alpha) = m exactly
+    // buckets of the sort (generated points): band j holds the buckets
+    // bk_off[j] .. bk_off[j+1]-1, bucket = bk_off[j] + (angle key >> (32 - bk_bits[j]))
+    uint32_t bk_off[kMaxBands + 1];
+    uint32_t bk_bits[kMaxBands];
+    uint32_t nbuckets;
     uint32_t B;
     uint32_t batch_budget, core_heavy, fringe_limit;  // work mapping of the range query
     uint32_t error;          // nonzero: a device-side check failed (see kErr*)
@@ -194,6 +206,13 @@ __device__ __forceinline__ uint32_t band_of_u53(uint64_t u53, const uint64_t *bu
         else hi = mid;
     }
     return lo;
+}
+
+// Sort bucket of key = (band << 32) | angle key (band < B; see Meta::bk_off).
+__device__ __forceinline__ uint32_t bucket_of(uint64_t key, const uint32_t *off, const uint32_t *bits)
+{
+    const uint32_t b = static_cast<uint32_t>(key >> 32), nb = bits[b];
+    return off[b] + (nb ? static_cast<uint32_t>(key) >> (32 - nb) : 0u);
 }
 
 // The angle's hi/lo float pair float(phi), float(phi - float(phi)) for phi =

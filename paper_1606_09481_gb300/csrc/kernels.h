@@ -15,6 +15,7 @@ struct PlanArgs {
     uint32_t allow_filter;  // FP32 filter permitted (the plan still requires R, alpha R in range)
     uint32_t verify;        // check every filter decision against the FP64 predicate
     uint32_t batch_budget, core_heavy, fringe_limit;  // work mapping of the range query (resolved, nonzero)
+    uint32_t *bucket_counts;  // bucket_entries(n) counters the plan clears (bucket sort), or NULL
 };
 
 // Sorted, structure-of-arrays view of the points: position p is the p-th point in
@@ -72,8 +73,9 @@ struct QueryArgs {
 
 // ---- points.cu ----
 Status launch_plan(Meta *d_meta, const PlanArgs &a, cudaStream_t stream);
+// bucket_counts (optional): the sort buckets' point counts (bucket sort).
 Status launch_sample(Meta *d_meta, uint64_t n, uint64_t seed, uint64_t *keys, uint32_t *ids,
-                     double *r_by_id, cudaStream_t stream);
+                     double *r_by_id, uint32_t *bucket_counts, cudaStream_t stream);
 Status launch_load_points(Meta *d_meta, uint64_t n, const double *phi, const double *r,
                           uint64_t *keys, uint32_t *ids, cudaStream_t stream);
 Status launch_band_offsets(Meta *d_meta, cudaStream_t stream);
@@ -87,6 +89,37 @@ Status launch_dm_eval(int fn, const double *in, double *out, uint64_t count, cud
 Status launch_points_by_id(const Meta *d_meta, uint64_t n, uint64_t seed, double *phi, double *r,
                            cudaStream_t stream);
 
+
+// ---- bucket.cu ----
+// Bucket sort of the keys (band << 32 | angle key) of points 0..n-1 by (key, id)
+// (Alg. 1, angular sort within each band), for generated points, whose angles are
+// uniform within a band: counts per bucket (the sampler's, or
+// launch_bucket_count), an exclusive scan into bucket starts (with the band
+// offsets of band_offsets_one), a scatter of (angle key << 32 | id) into the
+// buckets, then one CTA per bucket sorts it in shared memory (a counting pass on
+// the next 8 key bits, then each sub-bucket by one thread; buckets beyond
+// kBucketCap or with a sub-bucket beyond kSubMax take an LSD radix sort of the
+// bucket in global memory) and hands every position on: gather mode writes the
+// sorted key back into comp and the filter (or FP64) values of the point
+// (SortedPoints), keys mode writes the sorted keys and ids.
+struct BucketArgs {
+    Meta *M;
+    uint64_t n;
+    uint64_t seed;
+    uint32_t *counts;        // bucket_entries(n): counts, then cursors
+    uint32_t *start;         // bucket_entries(n) + 1: bucket starts
+    uint64_t *comp;          // n: (angle key << 32 | id) by bucket; gather mode: the sorted keys after
+    uint64_t *scratch;       // n: scratch of the global-memory path
+    const double *r_by_id;   // FP64 mode: the sampled FP64 radii by id
+    SortedPoints P;          // gather mode output
+    uint64_t *out_keys;      // keys mode output
+    uint32_t *out_ids;
+};
+Status launch_bucket_count(const BucketArgs &a, const uint64_t *keys, cudaStream_t stream);
+// band offsets + bucket starts (one CTA)
+Status launch_bucket_scan(const BucketArgs &a, cudaStream_t stream);
+Status launch_bucket_scatter(const BucketArgs &a, const uint64_t *keys, cudaStream_t stream);
+Status launch_bucket_sort(const BucketArgs &a, bool gather, cudaStream_t stream);
 
 // ---- sort.cu ----
 // LSD radix sort of 64-bit keys (optionally with uint32 values) over the 8-bit

@@ -19,12 +19,14 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Meta *M, PlanArgs a)
 // Points by id: sort key (band << 32 | angle key) and id.  In filter mode the band
 // comes from the radial variate compared with the band thresholds (band_of_u53, no
 // FP64); otherwise from the FP64 radius, which is also stored by id for the gather.
+// With bucket_counts, every point also counts in its sort bucket (bucket sort).
 __global__ void __launch_bounds__(kSampleThreads) sample_kernel(Meta *M, uint64_t n, uint64_t seed,
                                                                 uint64_t *keys, uint32_t *ids,
-                                                                double *r_by_id)
+                                                                double *r_by_id, uint32_t *bucket_counts)
 {
     __shared__ double c[kMaxBands + 1];
     __shared__ uint64_t bu[kMaxBands + 1];
+    __shared__ uint32_t bk_off[kMaxBands + 1], bk_bits[kMaxBands];
     __shared__ unsigned int hist[kMaxBands];
     const uint32_t B = M->B;
     const bool filter = M->filter != 0;
@@ -32,6 +34,8 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(Meta *M, uint64_
     if (threadIdx.x <= B) {
         c[threadIdx.x] = M->c[threadIdx.x];
         bu[threadIdx.x] = M->band_u[threadIdx.x];
+        bk_off[threadIdx.x] = M->bk_off[threadIdx.x];
+        if (threadIdx.x < B) bk_bits[threadIdx.x] = M->bk_bits[threadIdx.x];
     }
     if (threadIdx.x < kMaxBands) hist[threadIdx.x] = 0;
     __syncthreads();
@@ -40,9 +44,10 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(Meta *M, uint64_
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     for (uint64_t i0 = blockIdx.x * static_cast<uint64_t>(blockDim.x) + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
         const uint64_t i = i0 + (threadIdx.x & 31u);
-        uint32_t b = kMaxBands;
+        uint32_t b = kMaxBands, akey = 0;
         if (i < n) {
             const U64x4 x = draw(i, seed);
+            akey = static_cast<uint32_t>(x.x0 >> 32);
             if (filter) {
                 b = band_of_u53(x.x1 >> 11, bu, B);
             } else {
@@ -50,10 +55,17 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(Meta *M, uint64_
                 r_by_id[i] = r;
                 b = band_of(r, c, B);
             }
-            keys[i] = (static_cast<uint64_t>(b) << 32) | static_cast<uint32_t>(x.x0 >> 32);
-            ids[i] = static_cast<uint32_t>(i);
+            keys[i] = (static_cast<uint64_t>(b) << 32) | akey;
+            if (ids) ids[i] = static_cast<uint32_t>(i);
         }
         hist_add_warp(hist, b);
+        if (bucket_counts) {  // one global atomic per distinct bucket among the lanes
+            const uint32_t bk = b < B ? bucket_of((static_cast<uint64_t>(b) << 32) | akey, bk_off, bk_bits)
+                                      : 0xffffffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, bk);
+            if (bk != 0xffffffffu && (peers & ((1u << (threadIdx.x & 31u)) - 1u)) == 0)
+                atomicAdd(&bucket_counts[bk], static_cast<uint32_t>(__popc(peers)));
+        }
     }
     __syncthreads();
     if (threadIdx.x < B && hist[threadIdx.x]) atomicAdd(&M->band_count[threadIdx.x], hist[threadIdx.x]);
@@ -188,11 +200,11 @@ Status launch_plan(Meta *d_meta, const PlanArgs &a, cudaStream_t stream)
 }
 
 Status launch_sample(Meta *d_meta, uint64_t n, uint64_t seed, uint64_t *keys, uint32_t *ids,
-                     double *r_by_id, cudaStream_t stream)
+                     double *r_by_id, uint32_t *bucket_counts, cudaStream_t stream)
 {
     Status st;
     sample_kernel<<<grid_for(n, kSampleThreads, 8), kSampleThreads, 0, stream>>>(d_meta, n, seed, keys,
-                                                                                ids, r_by_id);
+                                                                                ids, r_by_id, bucket_counts);
     RHG_LAUNCH_CHECK();
     return st;
 }

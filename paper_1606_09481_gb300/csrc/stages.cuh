@@ -207,6 +207,25 @@ __device__ void plan_block(Meta *M, const PlanArgs &a, int depth, PlanSmem &PS)
         M->tabM[e] = static_cast<float>(::exp(-ea - G));
     }
     if (t < kMaxBands) M->band_count[t] = 0;
+    __syncthreads();  // band_u complete
+    // sort buckets: 2^b per band with kBucketTarget <= E / 2^b < 2 kBucketTarget for
+    // the band's expected count E = n (F(c_{j+1}) - F(c_j)) (b = 0 below)
+    if (t == 0) {
+        uint32_t off = 0;
+        for (uint32_t j = 0; j < B; ++j) {
+            const double E = nd * static_cast<double>(M->band_u[j + 1] - M->band_u[j]) * 0x1.0p-53;
+            uint32_t b = 0;
+            while (b < 24 && static_cast<double>(kBucketTarget) * static_cast<double>(2u << b) <= E) ++b;
+            M->bk_off[j] = off;
+            M->bk_bits[j] = b;
+            off += 1u << b;
+        }
+        M->bk_off[B] = off;
+        M->nbuckets = off;
+    }
+    __syncthreads();
+    if (a.bucket_counts)
+        for (uint32_t j = t; j < M->nbuckets; j += blockDim.x) a.bucket_counts[j] = 0;
     if (t != 0) return;
     M->cw = static_cast<float>(cm1 * 0x1.0p-53);
     M->inv_alpha_f = static_cast<float>(1.0 / alpha);
@@ -641,15 +660,31 @@ __device__ void seg_scan_graph(const BatchTables &bt, uint32_t *counts, uint32_t
     __syncthreads();  // the CTA's previous item is done with warp_sum
     const uint32_t d = threadIdx.x;
     const uint32_t t0 = bt.tile_first[g], t1 = bt.tile_first[g + 1];
+    constexpr uint32_t kAhead = 8;  // tiles whose counts are loaded together (latency, not bandwidth)
     uint32_t run = 0;
-    for (uint32_t t = t0; t < t1; ++t) {
-        uint32_t &c = counts[static_cast<uint64_t>(t) * kRadix + d];
-        const uint32_t v = c;
-        c = run;
-        run += v;
+    for (uint32_t t = t0; t < t1; t += kAhead) {
+        uint32_t v[kAhead];
+#pragma unroll
+        for (uint32_t u = 0; u < kAhead; ++u) v[u] = t + u < t1 ? counts[static_cast<uint64_t>(t + u) * kRadix + d] : 0u;
+#pragma unroll
+        for (uint32_t u = 0; u < kAhead; ++u) {
+            const uint32_t c = v[u];
+            v[u] = run;
+            run += c;
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < kAhead; ++u)
+            if (t + u < t1) counts[static_cast<uint64_t>(t + u) * kRadix + d] = v[u];
     }
     const uint32_t base = bt.pt_off[g] + block_exclusive(run, warp_sum);
-    for (uint32_t t = t0; t < t1; ++t) counts[static_cast<uint64_t>(t) * kRadix + d] += base;
+    for (uint32_t t = t0; t < t1; t += kAhead) {
+        uint32_t v[kAhead];
+#pragma unroll
+        for (uint32_t u = 0; u < kAhead; ++u) v[u] = t + u < t1 ? counts[static_cast<uint64_t>(t + u) * kRadix + d] : 0u;
+#pragma unroll
+        for (uint32_t u = 0; u < kAhead; ++u)
+            if (t + u < t1) counts[static_cast<uint64_t>(t + u) * kRadix + d] = v[u] + base;
+    }
 }
 
 template <bool kValues>
