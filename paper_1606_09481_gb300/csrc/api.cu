@@ -15,6 +15,17 @@
 
 #include "kernels.h"
 
+// A CUDA call in an entry point that reports through rhg_result: on failure the
+// error goes to res->cuda_error and the entry returns RHG_ERR_CUDA.
+#define RHG_RESULT_TRY(expr, res)          \
+    do {                                   \
+        const cudaError_t _e = (expr);     \
+        if (_e != cudaSuccess) {           \
+            (res)->cuda_error = _e;        \
+            return RHG_ERR_CUDA;           \
+        }                                  \
+    } while (0)
+
 namespace rhg {
 
 static std::atomic<unsigned long long> g_launches{0};
@@ -832,6 +843,75 @@ int static_scratch(void **ptr, cudaError_t *err)
     return RHG_OK;
 }
 
+// Resources of rhg_generate_pairs_host's overlapped copy, made once per CUDA
+// context and kept: a copy stream, one event per query phase, and host words
+// (registered, mapped) the phase ends write their edge counts into.  The mutex
+// serialises the calls that use them.
+struct HostCopy {
+    std::mutex mu;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev[kMaxPhases] = {};
+    uint64_t *h_m = nullptr;  // this context's kMaxPhases words
+    uint64_t *d_m = nullptr;  // their device address
+};
+alignas(4096) uint64_t g_phase_words[kMaxContexts][kMaxPhases];
+bool g_phase_words_registered = false;
+std::mutex g_copy_mu;
+unsigned long long g_copy_ctx[kMaxContexts] = {};
+HostCopy g_copy[kMaxContexts];
+
+int host_copy_resources(HostCopy **out, cudaError_t *err)
+{
+    std::lock_guard<std::mutex> lock(g_copy_mu);
+    unsigned long long id = 0;
+    int rc;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);  // current_context_id's function pointers
+        rc = current_context_id(&id, err);
+    }
+    if (rc) return rc;
+    if (!id) {  // no context yet: make the device's primary context current
+        *err = cudaFree(nullptr);
+        if (*err != cudaSuccess) return RHG_ERR_CUDA;
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        rc = current_context_id(&id, err);
+        if (rc) return rc;
+        if (!id) {
+            *err = cudaErrorDeviceUninitialized;
+            return RHG_ERR_CUDA;
+        }
+    }
+    int slot = -1;
+    for (int j = 0; j < kMaxContexts; ++j)
+        if (g_copy_ctx[j] == id) {
+            *out = &g_copy[j];
+            return RHG_OK;
+        } else if (slot < 0 && g_copy_ctx[j] == 0) {
+            slot = j;
+        }
+    if (slot < 0) {  // every slot taken: no overlapped copy for this context
+        *out = nullptr;
+        return RHG_OK;
+    }
+    if (!g_phase_words_registered) {
+        *err = cudaHostRegister(g_phase_words, sizeof(g_phase_words), cudaHostRegisterPortable | cudaHostRegisterMapped);
+        if (*err != cudaSuccess) return RHG_ERR_CUDA;
+        g_phase_words_registered = true;
+    }
+    HostCopy &h = g_copy[slot];
+    *err = cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking);
+    for (int p = 0; p < kMaxPhases && *err == cudaSuccess; ++p)
+        *err = cudaEventCreateWithFlags(&h.ev[p], cudaEventDisableTiming);
+    void *dm = nullptr;
+    if (*err == cudaSuccess) *err = cudaHostGetDevicePointer(&dm, g_phase_words[slot], 0);
+    if (*err != cudaSuccess) return RHG_ERR_CUDA;
+    h.h_m = g_phase_words[slot];
+    h.d_m = static_cast<uint64_t *>(dm);
+    g_copy_ctx[slot] = id;
+    *out = &h;
+    return RHG_OK;
+}
+
 // The layout a plan describes; false if the plan is not one rhg_batch_prepare made.
 bool plan_layout(const rhg_batch_plan *plan, BatchLayout &L)
 {
@@ -886,6 +966,95 @@ Status sort_keys(const uint64_t *d_keys, uint64_t n, uint32_t num_bands, const u
     RHG_CUDA_TRY(cudaMemcpyAsync(err, &ba.M->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     RHG_CUDA_TRY(cudaStreamSynchronize(s));
     return st;
+}
+
+// Query phases for the overlapped host copy: one per ~2^23 expected edges (64 MB
+// of pairs), at most 8.
+uint32_t copy_phases(const rhg_params &p)
+{
+    const double m = static_cast<double>(p.n) * p.k * 0.5;
+    const double ph = std::floor(m / 8388608.0);
+    return ph < 1.0 ? 1u : (ph > 8.0 ? 8u : static_cast<uint32_t>(ph));
+}
+
+// rhg_generate_pairs_host into pinned memory: the point pipeline, then the range
+// query in phases; after phase p the host copies the edges the phase added on the
+// copy stream (the copy engines run beside the next phases).  A recheck list that
+// overflows (rerun in FP64 mode) falls back to generate-then-copy.
+int generate_host_overlapped(const rhg_params *p, void *d_ws, size_t ws_bytes, uint32_t *d_pairs, uint64_t capacity,
+                             uint32_t *h_pairs, uint64_t h_capacity, HostCopy &hc, cudaStream_t stream,
+                             rhg_result *res)
+{
+    std::memset(res, 0, sizeof(*res));
+    uint32_t B;
+    double ratio;
+    int rc = check_params(p, &B, &ratio);
+    if (rc) return rc;
+    if (!d_ws) return RHG_ERR_INVALID_ARG;
+    if (capacity && (!d_pairs || (reinterpret_cast<uintptr_t>(d_pairs) & 7))) return RHG_ERR_INVALID_ARG;
+    const Layout L = make_layout(p->n, 0, chunk_extra(*p));
+    if (ws_bytes < L.total) return RHG_ERR_OOM;
+    if (reinterpret_cast<uintptr_t>(d_ws) & 255) return RHG_ERR_INVALID_ARG;
+    Pipeline pl{d_ws, L, p->n};
+    const PlanArgs pa = with_mapping(PlanArgs{p->n, p->k, p->alpha, p->seed, B, ratio, p->R_override,
+                                              (p->flags & RHG_FLAG_FP64_ONLY) ? 0u : 1u,
+                                              (p->flags & RHG_FLAG_VERIFY) ? 1u : 0u},
+                                     *p);
+    std::lock_guard<std::mutex> lock(hc.mu);
+    SortedPoints P;
+    Status st = enqueue_points(pl, pa, nullptr, nullptr, &P, stream);
+    if (st.code) return finish(st, res);
+    QueryArgs q{};
+    q.M = pl.meta();
+    q.P = P;
+    q.pairs = d_pairs;
+    q.capacity = capacity;
+    q.heavy = at<uint4>(pl.ws, pl.L.heavy);
+    q.heavy_cap = pl.L.heavy_cap;
+    q.recheck = at<uint2>(pl.ws, pl.L.recheck);
+    q.recheck_cap = pl.L.recheck_cap;
+    q.heavy_min = kHeavyMin;
+    q.bidx = at<uint32_t>(pl.ws, pl.L.bidx);
+    q.verify = pa.verify != 0;
+    const uint32_t phases = copy_phases(*p);
+    for (uint32_t i = 0; i < phases; ++i) hc.h_m[i] = ~uint64_t{0};
+    mark(RHG_STAGE_QUERY, false, stream);
+    st = launch_query_phased(q, phases, hc.d_m, hc.ev, stream);
+    if (st.code) return finish(st, res);
+    mark(RHG_STAGE_QUERY, true, stream);
+    const uint64_t limit = capacity < h_capacity ? capacity : h_capacity;
+    uint64_t done = 0;
+    for (uint32_t i = 0; i < phases; ++i) {
+        RHG_RESULT_TRY(cudaEventSynchronize(hc.ev[i]), res);
+        uint64_t m = *reinterpret_cast<volatile uint64_t *>(hc.h_m + i);
+        if (m > limit) m = limit;
+        if (m > done) {
+            RHG_RESULT_TRY(cudaMemcpyAsync(h_pairs + 2 * done, d_pairs + 2 * done, (m - done) * 8,
+                                           cudaMemcpyDeviceToHost, hc.copy),
+                           res);
+            done = m;
+        }
+    }
+    Meta h;
+    st = read_meta(pl.meta(), &h, stream);
+    if (st.code) return finish(st, res);
+    RHG_RESULT_TRY(cudaStreamSynchronize(hc.copy), res);
+    if (h.error == kErrListFull && h.filter) {  // the FP64 rerun, then one copy
+        PlanArgs p64 = pa;
+        p64.allow_filter = 0;
+        st = run_pipeline(pl, p64, nullptr, nullptr, Output::Pairs, d_pairs, capacity, &h, stream);
+        if (st.code) return finish(st, res);
+        fill_result(res, h);
+        if (h.error) return error_from_meta(h.error);
+        if (h.m > capacity || h.m > h_capacity) return RHG_ERR_OVERFLOW;
+        if (h.m) RHG_RESULT_TRY(cudaMemcpyAsync(h_pairs, d_pairs, h.m * 8, cudaMemcpyDeviceToHost, stream), res);
+        RHG_RESULT_TRY(cudaStreamSynchronize(stream), res);
+        return RHG_OK;
+    }
+    fill_result(res, h);
+    if (h.error) return error_from_meta(h.error);
+    if (h.m > capacity || h.m > h_capacity) return RHG_ERR_OVERFLOW;
+    return RHG_OK;
 }
 
 extern "C" {
@@ -1012,10 +1181,28 @@ int rhg_generate_pairs_host(const rhg_params *p, void *d_workspace, size_t works
     if (!h_pairs && h_capacity_edges) return RHG_ERR_INVALID_ARG;
     rhg_result local{};
     rhg_result *res = result ? result : &local;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // pinned host memory the copy engines reach directly: the copy of each query
+    // phase's edges overlaps the later phases
+    cudaPointerAttributes attr{};
+    const bool pinned = h_pairs && cudaPointerGetAttributes(&attr, h_pairs) == cudaSuccess &&
+                        attr.type == cudaMemoryTypeHost;
+    cudaGetLastError();  // a pageable pointer may leave an error behind
+    if (pinned) {
+        HostCopy *hc = nullptr;
+        cudaError_t err = cudaSuccess;
+        int rc = host_copy_resources(&hc, &err);
+        if (rc) {
+            std::memset(res, 0, sizeof(*res));
+            res->cuda_error = err;
+            return rc;
+        }
+        if (hc) return generate_host_overlapped(p, d_workspace, workspace_bytes, d_pairs, capacity_edges, h_pairs,
+                                                h_capacity_edges, *hc, s, res);
+    }
     const int rc = rhg_generate_pairs(p, d_workspace, workspace_bytes, d_pairs, capacity_edges, stream, res);
     if (rc) return rc;
     if (res->m > h_capacity_edges) return RHG_ERR_OVERFLOW;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (res->m) {
         const cudaError_t e =
             cudaMemcpyAsync(h_pairs, d_pairs, res->m * 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);

@@ -28,6 +28,7 @@ constexpr uint32_t kBucketTarget = 512;
 constexpr uint32_t kBucketCap = 2048;
 __host__ __device__ constexpr uint64_t bucket_entries(uint64_t n) { return n / kBucketTarget + kMaxBands + 1; }
 constexpr int kMaxStageMarks = 32;       // stage timestamps of the persistent batch launch
+constexpr int kMaxPhases = 16;           // phases of a range query whose output is copied out as it goes
 
 // ---------------------------------------------------------------------------
 // FP32 filter: error model.  The filter evaluates X = L / cosh R in the
@@ -100,6 +101,8 @@ struct Meta {
     uint64_t verify_failures;
     uint32_t heavy_n, heavy_next;      // heavy-range chunk list
     uint32_t recheck_n, pad0;          // FP64 recheck list
+    uint32_t heavy_lo, recheck_lo;     // phased query: entries before these are done
+    uint64_t m_phase[kMaxPhases];      // phased query: the edge count after each phase
     uint64_t work_counter;             // dynamic model: moved vertices listed
     // work claims of the range query: counter c hands out the warp batches
     // c, c + kClaimCounters, ... (one counter per 128-byte line, so that the claims

@@ -69,6 +69,7 @@ struct QueryArgs {
     uint32_t heavy_min;     // ranges longer than this go to the heavy chunks (UINT32_MAX: never)
     uint32_t *bidx;         // bucket index of the bands, index_entries(n) entries
     bool verify;            // some graph runs in verification mode (RHG_FLAG_VERIFY)
+    uint32_t batch_lo, batch_hi;  // single graph: the warp batches [batch_lo, batch_hi) (batch_hi 0: all)
 };
 
 // ---- points.cu ----
@@ -140,6 +141,14 @@ size_t segmented_temp_bytes(uint32_t num_tiles);
 // so the pair order is unspecified; Meta::m is the exact edge count.  The kernels
 // of both modes are launched; each returns at once unless Meta::filter selects it.
 Status launch_query(const QueryArgs &a, bool csr, cudaStream_t stream);
+// The range query in phases (pairs output): the bucket index, then for each phase
+// a range of warp batches (the outermost sixteenth first, then the rest in equal
+// parts inwards), their heavy chunks and FP64 rechecks; after phase p the edges
+// [0, m) are final, m goes to
+// Meta::m_phase[p] and, when host_m is not NULL (device pointer of mapped host
+// memory), to host_m[p] as well.  events[p] (if not NULL) is recorded after phase p.
+Status launch_query_phased(QueryArgs a, uint32_t phases, uint64_t *host_m, cudaEvent_t *events,
+                           cudaStream_t stream);
 // The whole batch in one persistent, cooperative launch: plan, sampling, band
 // offsets, the segmented radix sort, gather, bucket index, both query phases and
 // the per-graph results, separated by grid barriers whose waits give up after

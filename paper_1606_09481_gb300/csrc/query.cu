@@ -738,7 +738,8 @@ __device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, B
     uint64_t obase = 0, cap = a.capacity;  // output region of the current graph
     uint32_t cur_g = 0xffffffffu;
     bool skip = false;
-    const uint32_t nbatch = kMulti ? a.bt.num_tiles * (kTilePoints / 32) : (n + 31) / 32;
+    const uint32_t nbatch = kMulti ? a.bt.num_tiles * (kTilePoints / 32)
+                                   : (a.batch_hi ? a.batch_hi - a.batch_lo : (n + 31) / 32);
     unsigned long long cand = 0;
     uint64_t near = 0;
     // batches in sorted order from kClaimCounters interleaved counters (counter c
@@ -778,7 +779,7 @@ __device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, B
             p0 = T.y + sub;
             cnt = T.z - sub < 32 ? T.z - sub : 32;
         } else {
-            p0 = batch * 32;
+            p0 = (a.batch_lo + batch) * 32;
             cnt = n - p0 < 32 ? n - p0 : 32;
         }
         const uint32_t p = p0 + lane;
@@ -993,9 +994,10 @@ __device__ __forceinline__ void heavy_body(const QueryArgs &a, WarpSmem *Wsm)
     const uint32_t count = C->heavy_n < a.heavy_cap ? C->heavy_n : a.heavy_cap;
     uint64_t near = 0;
     // chunks round robin over the warps (all chunks hold at most kChunk candidates
-    // and most hold exactly that): no claim traffic on a shared counter
+    // and most hold exactly that): no claim traffic on a shared counter; a phased
+    // query starts after the chunks of its earlier phases
     const uint32_t gwarps = gridDim.x * kWarps;
-    for (uint32_t item = blockIdx.x * kWarps + warp; item < count; item += gwarps) {
+    for (uint32_t item = C->heavy_lo + blockIdx.x * kWarps + warp; item < count; item += gwarps) {
         const uint4 h = a.heavy[item];
         const uint32_t g = h.w >> 1;
         Meta *Mg = kMulti ? a.M + g : a.M;
@@ -1044,7 +1046,7 @@ __global__ void __launch_bounds__(kThreads) recheck_kernel(QueryArgs a)
     const double coshR = M->coshR;
     uint64_t near = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; w0 < count; w0 += stride) {
+    for (uint32_t w0 = M->recheck_lo + ((blockIdx.x * blockDim.x + threadIdx.x) & ~31u); w0 < count; w0 += stride) {
         const uint32_t idx = w0 + lane;
         bool edge = false;
         uint32_t idv = 0, idw = 0;
@@ -1117,6 +1119,22 @@ __device__ __forceinline__ void reset_phase(Meta *C)
     }
 }
 
+
+// End of phase p of a phased query: its edges are final, the next phase starts its
+// claims, chunks and rechecks after the ones done.
+__global__ void phase_end_kernel(Meta *M, uint32_t p, uint32_t heavy_cap, uint32_t recheck_cap, uint64_t *host_m)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint64_t m = M->m;
+    M->m_phase[p] = m;
+    for (uint32_t c = 0; c < kClaimCounters; ++c) M->claim[c * 32] = 0;
+    M->heavy_lo = M->heavy_n < heavy_cap ? M->heavy_n : heavy_cap;
+    M->recheck_lo = M->recheck_n < recheck_cap ? M->recheck_n : recheck_cap;
+    if (host_m) {
+        *reinterpret_cast<volatile uint64_t *>(host_m + p) = m;
+        __threadfence_system();
+    }
+}
 
 // ------------------------------------------------------------------ subset query
 // Neighbours of the moved vertices (dynamic model, Sec. III-C), for the update of
@@ -1603,6 +1621,37 @@ Status launch_query(const QueryArgs &a, bool csr, cudaStream_t stream)
     st = csr ? run<true, true, false>(a, stream) : run<true, false, false>(a, stream);
     if (st.code) return st;
     return csr ? run<false, true, false>(a, stream) : run<false, false, false>(a, stream);
+}
+
+Status launch_query_phased(QueryArgs a, uint32_t phases, uint64_t *host_m, cudaEvent_t *events,
+                           cudaStream_t stream)
+{
+    Status st = launch_bucket_index(a, stream);
+    if (st.code) return st;
+    // phases run from the outermost batches inwards: the first phase, a sixteenth
+    // of the batches (rim points, few bands each), ends soon, so the copy of its
+    // edges starts early; the rest is split evenly
+    const uint64_t nb = (a.P.n + 31) / 32;
+    const uint64_t first = phases > 1 ? nb / 16 : nb, rest = nb - first;
+    for (uint32_t p = 0; p < phases; ++p) {
+        if (p == 0) {
+            a.batch_lo = static_cast<uint32_t>(rest);
+            a.batch_hi = static_cast<uint32_t>(nb);
+        } else {
+            a.batch_lo = static_cast<uint32_t>(rest * (phases - 1 - p) / (phases - 1));
+            a.batch_hi = static_cast<uint32_t>(rest * (phases - p) / (phases - 1));
+        }
+        if (a.batch_hi > a.batch_lo) {
+            st = run<true, false, false>(a, stream);
+            if (st.code) return st;
+            st = run<false, false, false>(a, stream);
+            if (st.code) return st;
+        }
+        phase_end_kernel<<<1, 32, 0, stream>>>(a.M, p, a.heavy_cap, a.recheck_cap, host_m);
+        RHG_LAUNCH_CHECK();
+        if (events) RHG_CUDA_TRY(cudaEventRecord(events[p], stream));
+    }
+    return st;
 }
 
 Status launch_bucket_index(const QueryArgs &a, cudaStream_t stream)

@@ -240,6 +240,8 @@ __device__ void plan_block(Meta *M, const PlanArgs &a, int depth, PlanSmem &PS)
     M->heavy_n = 0;
     M->heavy_next = 0;
     M->recheck_n = 0;
+    M->heavy_lo = 0;
+    M->recheck_lo = 0;
     M->work_counter = 0;
     for (uint32_t c = 0; c < kClaimCounters; ++c) M->claim[c * 32] = 0;
 }
@@ -267,6 +269,8 @@ __device__ void plan_batch_item(Meta *metas, const PlanArgs *args, uint32_t G, u
     C->heavy_n = 0;
     C->heavy_next = 0;
     C->recheck_n = 0;
+    C->heavy_lo = 0;
+    C->recheck_lo = 0;
     C->work_counter = 0;
     for (uint32_t c = 0; c < kClaimCounters; ++c) C->claim[c * 32] = 0;
 }

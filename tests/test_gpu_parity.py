@@ -80,6 +80,37 @@ def test_pairs_to_host_matches_device(O):
     assert np.array_equal(sorted_pairs(host[: 2 * res2.m].view(-1, 2)), sorted_pairs(dev))
 
 
+@pytest.mark.parametrize("flags", [0, 1])
+def test_pairs_to_host_in_phases(O, flags):
+    """A graph large enough for several query phases whose copies overlap the
+    later phases (pinned host memory): the same pairs as the device output, in
+    filter and FP64-only mode; a pageable host buffer takes the plain path and
+    gives them too; a host buffer one pair short reports OVERFLOW with the exact m."""
+    rhg = require_gpu()
+    import ctypes
+    import torch
+    n, k, alpha, seed = 10**6, 64, 0.75, 8
+    fl = rhg.FLAG_FP64_ONLY if flags else 0
+    dev, res = rhg.generate_pairs(n, k, alpha, seed, flags=fl)
+    assert res.m > 3 * 2**23  # three phases or more
+    p = rhg.make_params(n, k, alpha, seed, flags=fl)
+    wsp = rhg.allocate_pairs(p, capacity=res.m + 1000)
+    ref = sorted_pairs(dev)
+    for pin in (True, False):
+        host = torch.empty(2 * wsp.capacity, dtype=torch.int32)
+        if pin:
+            host = host.pin_memory()
+        res2 = rhg.generate_pairs_host(n, k, alpha, seed, host, wsp, flags=fl)
+        assert res2.m == res.m
+        assert np.array_equal(sorted_pairs(host[: 2 * res2.m].view(-1, 2)), ref)
+    host = torch.empty(2 * (res.m - 1), dtype=torch.int32).pin_memory()
+    r3 = rhg.Result()
+    rc = rhg.load().rhg_generate_pairs_host(ctypes.byref(p), wsp.ws.data_ptr(), wsp.ws.numel(), wsp.out.data_ptr(),
+                                            wsp.capacity, host.data_ptr(), res.m - 1, rhg._stream(),
+                                            ctypes.byref(r3))
+    assert rc == rhg.OVERFLOW and r3.m == res.m
+
+
 def test_overflow_reports_exact_count(O):
     rhg = require_gpu()
     import ctypes
