@@ -120,8 +120,9 @@ typedef struct rhg_result {
 /* Human-readable name of a status code (static string, never NULL). */
 const char *rhg_status_str(int status);
 
-/* ABI version of this header: 3 (2 added rhg_result.rounding_band, 3 the work
- * mapping fields of rhg_params). */
+/* ABI version of this header: 4 (2 added rhg_result.rounding_band, 3 the work
+ * mapping fields of rhg_params, 4 rhg_sort_keys and the batch's bucket-sort
+ * stages in rhg_batch_stage_times). */
 int rhg_version(void);
 
 /*
@@ -345,13 +346,14 @@ int rhg_batch_read_results(const rhg_batch_plan *plan, const void *d_workspace, 
  *
  * rhg_batch_stage_times -- device time of each stage of the last launch in
  * d_workspace (after the launch has completed), in ms, RHG_BATCH_STAGE_COUNT
- * values in this order: plan, sampling, band offsets, then 5 sort passes x
- * (digit counts, scan, scatter), gather, bucket index, range query (filter
- * graphs), heavy chunks (filter graphs), FP64 rechecks, phase reset, range query
- * (FP64 graphs), heavy chunks (FP64 graphs), results.  Synchronises the stream.
- * Errors: INVALID_ARG (no plan, count too small), CUDA.
+ * values in this order: plan, sampling (with the sort-bucket counts), band
+ * offsets and bucket starts, bucket scatter, bucket sort with the gather, bucket
+ * index, range query (filter graphs), heavy chunks (filter graphs), FP64
+ * rechecks, phase reset, range query (FP64 graphs), heavy chunks (FP64 graphs),
+ * results.  Synchronises the stream.  Errors: INVALID_ARG (no plan, count too
+ * small), CUDA.
  */
-#define RHG_BATCH_STAGE_COUNT 27u
+#define RHG_BATCH_STAGE_COUNT 13u
 int rhg_batch_stage_times(const rhg_batch_plan *plan, const void *d_workspace, void *stream, double *ms,
                           uint32_t count);
 

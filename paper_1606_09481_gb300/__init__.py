@@ -380,10 +380,8 @@ def batch_read_results(plan: BatchPlan, buf: BatchBuffers, stream=None):
     return rc, res, tot
 
 
-BATCH_STAGES = ("plan", "sample", "band_offsets") + tuple(
-    f"sort{p}_{part}" for p in range(5) for part in ("counts", "scan", "scatter")) + (
-    "gather", "bucket_index", "query_filter", "heavy_filter", "recheck", "phase_reset", "query_fp64", "heavy_fp64",
-    "results")
+BATCH_STAGES = ("plan", "sample", "bucket_scan", "bucket_scatter", "bucket_sort_gather", "bucket_index",
+                "query_filter", "heavy_filter", "recheck", "phase_reset", "query_fp64", "heavy_fp64", "results")
 
 
 def batch_stage_times(plan: BatchPlan, buf: BatchBuffers, stream=None) -> dict:

@@ -505,15 +505,19 @@ struct BatchHost {
     uint64_t chunk_extra = 0;  // chunk-list entries for graphs that may run in FP64 mode
     std::vector<PlanArgs> args;
     std::vector<uint4> tiles;
-    std::vector<uint32_t> tile_first, pt_off, idx_base;
+    std::vector<uint32_t> tile_first, pt_off, idx_base, bk_base;
     std::vector<uint64_t> out_off;
 };
 
 struct BatchLayout {
-    size_t metas, args, tiles, tile_first, pt_off, idx_base, out_off, tables_end, results, keys0, keys1, ids0, ids1,
-        r_by_pos, akey, id, ang, pms, phi, r, ch, sh, bidx, heavy, recheck, sort_tmp, bar, total;
+    size_t metas, args, tiles, tile_first, pt_off, idx_base, bk_base, out_off, tables_end, results, keys0, keys1,
+        r_by_pos, akey, id, ang, pms, phi, r, ch, sh, bidx, bk_counts, bk_start, bk_info, heavy, recheck, bar, total;
     uint32_t heavy_cap, recheck_cap;
 };
+
+// Sort buckets of a batch: graph g owns n_g / kBucketTarget + B_g + 1 of them, so
+// all graphs together own at most this many (from the point and graph counts alone).
+uint64_t batch_buckets(uint64_t G, uint64_t N) { return N / kBucketTarget + G * (kMaxBands + 1); }
 
 int batch_host(const rhg_params *graphs, uint32_t count, const uint64_t *pair_offsets, BatchHost &h)
 {
@@ -523,6 +527,7 @@ int batch_host(const rhg_params *graphs, uint32_t count, const uint64_t *pair_of
     h.tile_first.assign(count + 1, 0);
     h.pt_off.assign(count + 1, 0);
     h.idx_base.assign(count + 1, 0);
+    h.bk_base.assign(count + 1, 0);
     h.out_off.assign(count + 1, 0);
     h.tiles.clear();
     uint64_t pos = 0, idx = 0;
@@ -547,6 +552,9 @@ int batch_host(const rhg_params *graphs, uint32_t count, const uint64_t *pair_of
         if (pos >= 0xFFFFFFFFull || idx >= 0xFFFFFFFFull) return RHG_ERR_INVALID_ARG;  // 32-bit positions
         h.pt_off[g + 1] = static_cast<uint32_t>(pos);
         h.idx_base[g + 1] = static_cast<uint32_t>(idx);
+        // the plan's buckets: 2^b per band with 2^b <= E / kBucketTarget, so at most
+        // n / kBucketTarget + B of them, and one more start
+        h.bk_base[g + 1] = static_cast<uint32_t>(h.bk_base[g] + q.n / kBucketTarget + B + 1);
     }
     h.tile_first[count] = static_cast<uint32_t>(h.tiles.size());
     h.N = pos;
@@ -586,6 +594,8 @@ BatchLayout batch_layout(uint64_t G, uint64_t N, uint64_t num_tiles, uint64_t id
     o += (G + 1) * 4;
     L.idx_base = o;
     o += (G + 1) * 4;
+    L.bk_base = o;
+    o += (G + 1) * 4;
     o = (o + 7) & ~size_t{7};
     L.out_off = o;
     o += (G + 1) * 8;
@@ -594,8 +604,6 @@ BatchLayout batch_layout(uint64_t G, uint64_t N, uint64_t num_tiles, uint64_t id
     L.results = take(2 * G * sizeof(uint4));
     L.keys0 = take(N * 8);
     L.keys1 = take(N * 8);
-    L.ids0 = take(N * 4);
-    L.ids1 = take(N * 4);
     L.r_by_pos = take(N * 8);
     L.akey = take(N * 4);
     L.id = take(N * 4);
@@ -606,9 +614,11 @@ BatchLayout batch_layout(uint64_t G, uint64_t N, uint64_t num_tiles, uint64_t id
     L.ch = take(N * 8);
     L.sh = take(N * 8);
     L.bidx = take(idx_total * 4);
+    L.bk_counts = take(batch_buckets(G, N) * 4);
+    L.bk_start = take((batch_buckets(G, N) + 1) * 4);
+    L.bk_info = take(batch_buckets(G, N) * 4);
     L.heavy = take(static_cast<size_t>(L.heavy_cap) * 16);
     L.recheck = take(static_cast<size_t>(L.recheck_cap) * 8);
-    L.sort_tmp = take(segmented_temp_bytes(static_cast<uint32_t>(num_tiles)));
     L.bar = take(256);
     L.total = o;
     return L;
@@ -627,11 +637,15 @@ Status upload_tables(void *ws, const BatchLayout &L, const BatchHost &h, cudaStr
     auto put = [&](size_t off, const void *src, size_t bytes) {
         if (bytes) std::memcpy(buf.data() + (off - L.args), src, bytes);
     };
-    put(L.args, h.args.data(), h.args.size() * sizeof(PlanArgs));
+    // each graph's plan clears its own bucket counters
+    std::vector<PlanArgs> args = h.args;
+    for (uint32_t g = 0; g < h.G; ++g) args[g].bucket_counts = at<uint32_t>(ws, L.bk_counts) + h.bk_base[g];
+    put(L.args, args.data(), args.size() * sizeof(PlanArgs));
     put(L.tiles, h.tiles.data(), h.tiles.size() * sizeof(uint4));
     put(L.tile_first, h.tile_first.data(), h.tile_first.size() * 4);
     put(L.pt_off, h.pt_off.data(), h.pt_off.size() * 4);
     put(L.idx_base, h.idx_base.data(), h.idx_base.size() * 4);
+    put(L.bk_base, h.bk_base.data(), h.bk_base.size() * 4);
     put(L.out_off, h.out_off.data(), h.out_off.size() * 8);
     RHG_CUDA_TRY(cudaMemcpyAsync(at<char>(ws, L.args), buf.data(), buf.size(), cudaMemcpyHostToDevice, stream));
     RHG_CUDA_TRY(cudaStreamSynchronize(stream));
@@ -648,6 +662,7 @@ BatchTables batch_tables(void *ws, const BatchLayout &L, uint32_t G, uint64_t nu
     bt.pt_off = at<uint32_t>(ws, L.pt_off);
     bt.idx_base = at<uint32_t>(ws, L.idx_base);
     bt.out_off = at<uint64_t>(ws, L.out_off);
+    bt.bk_base = at<uint32_t>(ws, L.bk_base);
     return bt;
 }
 
@@ -664,13 +679,13 @@ Status enqueue_batch(void *ws, const BatchLayout &L, uint32_t G, uint64_t N, uin
     b.bt = batch_tables(ws, L, G, num_tiles);
     b.keys0 = at<uint64_t>(ws, L.keys0);
     b.keys1 = at<uint64_t>(ws, L.keys1);
-    b.ids0 = at<uint32_t>(ws, L.ids0);
-    b.ids1 = at<uint32_t>(ws, L.ids1);
     b.r_by_pos = at<double>(ws, L.r_by_pos);
-    b.sort_counts = at<uint32_t>(ws, L.sort_tmp);
+    b.bk_counts = at<uint32_t>(ws, L.bk_counts);
+    b.bk_start = at<uint32_t>(ws, L.bk_start);
+    b.bk_info = at<uint32_t>(ws, L.bk_info);
     SortedPoints &P = b.P;
     P.n = N;
-    P.key = kBatchSortPasses % 2 ? b.keys1 : b.keys0;  // where the sort passes leave the keys
+    P.key = b.keys1;  // the bucket sort writes the sorted keys back over its composites
     P.akey = at<uint32_t>(ws, L.akey);
     P.id = at<uint32_t>(ws, L.id);
     P.ang = at<float2>(ws, L.ang);
@@ -1073,7 +1088,7 @@ const char *rhg_status_str(int status)
     }
 }
 
-int rhg_version(void) { return 3; }
+int rhg_version(void) { return 4; }
 
 int rhg_set_stage_events(void *const *events, uint32_t count)
 {

@@ -24,10 +24,7 @@
 namespace rhg {
 namespace {
 
-using stg::TileSmem;
-
-constexpr int kBkThreads = 256;
-constexpr uint32_t kSubMax = 32;  // largest sub-bucket sorted by one thread
+constexpr int kBkThreads = stg::kThreads;
 
 __global__ void __launch_bounds__(kBkThreads) bucket_count_kernel(Meta *M, uint64_t n, const uint64_t *keys,
                                                                   uint32_t *counts)
@@ -107,47 +104,15 @@ __global__ void __launch_bounds__(kBkThreads) bucket_scatter_kernel(const Meta *
     }
 }
 
-// LSD radix sort of comp[s, s + cnt) by one CTA (8 passes of 8 bits through
-// scratch, tiles in order, so stable), for buckets the shared-memory path cannot
-// take.  The result is back in comp.
-__device__ void cta_sort_range(uint64_t *comp, uint64_t *scratch, uint32_t s, uint32_t cnt, TileSmem &ts,
-                               uint32_t *hist)
-{
-    for (int pass = 0; pass < 8; ++pass) {
-        const int shift = 8 * pass;
-        const uint64_t *src = (pass & 1) ? scratch : comp;
-        uint64_t *dst = (pass & 1) ? comp : scratch;
-        __syncthreads();
-        hist[threadIdx.x] = 0;
-        __syncthreads();
-        for (uint32_t k = threadIdx.x; k < cnt; k += kBkThreads) atomicAdd(&hist[(src[s + k] >> shift) & 255u], 1u);
-        __syncthreads();
-        ts.digit_base[threadIdx.x] = s + stg::block_exclusive(hist[threadIdx.x], ts.warp_sum);
-        __syncthreads();
-        for (uint32_t t = 0; t < cnt; t += stg::kTile) {
-            const uint32_t c = cnt - t < static_cast<uint32_t>(stg::kTile) ? cnt - t : stg::kTile;
-            stg::tile_pass<false>(src, dst, nullptr, nullptr, s + t, c, shift, ts, nullptr);
-        }
-    }
-    __syncthreads();
-}
-
-union SortSmem {
-    uint64_t buf[2][kBucketCap];
-    TileSmem ts;
-};
-
 // One CTA per bucket (grid-stride).  kGather: the sorted key goes back into comp
 // and the point's filter values (filter mode: FP32/integer from its variates) or
 // FP64 values go to P; else the sorted keys and ids go to out_keys / out_ids.
 template <bool kGather>
 __global__ void __launch_bounds__(kBkThreads, 4) bucket_sort_kernel(BucketArgs a)
 {
-    __shared__ SortSmem U;
-    __shared__ uint32_t hist[256], cur[256], wsum[kBkThreads / 32];
+    __shared__ stg::BucketSmem SB;
     __shared__ uint32_t off[kMaxBands + 1], bits[kMaxBands];
     __shared__ stg::YTab Y;
-    __shared__ int big;
     Meta *M = a.M;
     const uint32_t B = M->B, nb = M->nbuckets;
     if (threadIdx.x <= B) {
@@ -158,7 +123,6 @@ __global__ void __launch_bounds__(kBkThreads, 4) bucket_sort_kernel(BucketArgs a
     __syncthreads();
     if (M->error) return;
     const bool filter = M->filter != 0;
-    const uint32_t t = threadIdx.x;
     for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
         const uint32_t s = a.start[b], cnt = a.start[b + 1] - s;
         uint32_t band = 0;  // the largest j < B with off[j] <= b
@@ -166,46 +130,9 @@ __global__ void __launch_bounds__(kBkThreads, 4) bucket_sort_kernel(BucketArgs a
             if (band + step < B && off[band + step] <= b) band += step;
         const int rest = 32 - static_cast<int>(bits[band]);  // angle-key bits below the bucket's
         const int dsh = 32 + (rest > 8 ? rest - 8 : 0);     // the next 8 of them, in the composite
-        __syncthreads();  // the previous bucket is done with the shared arrays
-        bool fast = cnt <= kBucketCap;  // uniform over the CTA
-        if (fast) {
-            hist[t] = 0;
-            if (t == 0) big = 0;
-            __syncthreads();
-            for (uint32_t k = t; k < cnt; k += kBkThreads) {
-                const uint64_t v = a.comp[s + k];
-                U.buf[0][k] = v;
-                atomicAdd(&hist[static_cast<uint32_t>(v >> dsh) & 255u], 1u);
-            }
-            __syncthreads();
-            const uint32_t h = hist[t];
-            cur[t] = stg::block_exclusive(h, wsum);
-            if (h > kSubMax) big = 1;
-            __syncthreads();
-            for (uint32_t k = t; k < cnt; k += kBkThreads) {
-                const uint64_t v = U.buf[0][k];
-                U.buf[1][atomicAdd(&cur[static_cast<uint32_t>(v >> dsh) & 255u], 1u)] = v;
-            }
-            __syncthreads();
-            if (!big) {  // sub-bucket t is [cur[t] - h, cur[t]): insertion sort by (angle key, id)
-                uint64_t *x = U.buf[1];
-                const uint32_t e1 = cur[t], s1 = e1 - h;
-                for (uint32_t i = s1 + 1; i < e1; ++i) {
-                    const uint64_t v = x[i];
-                    uint32_t j = i;
-                    while (j > s1 && x[j - 1] > v) {
-                        x[j] = x[j - 1];
-                        --j;
-                    }
-                    x[j] = v;
-                }
-            }
-            __syncthreads();
-            fast = big == 0;
-        }
-        if (!fast) cta_sort_range(a.comp, a.scratch, s, cnt, U.ts, hist);
-        for (uint32_t k = t; k < cnt; k += kBkThreads) {
-            const uint64_t c = fast ? U.buf[1][k] : a.comp[s + k];
+        const uint64_t *sorted = stg::sort_bucket(a.comp, a.scratch, s, cnt, dsh, SB);
+        for (uint32_t k = threadIdx.x; k < cnt; k += kBkThreads) {
+            const uint64_t c = sorted[k];
             const uint32_t p = s + k, id = static_cast<uint32_t>(c), akey = static_cast<uint32_t>(c >> 32);
             const uint64_t key = (static_cast<uint64_t>(band) << 32) | akey;
             if (kGather) {
@@ -216,7 +143,7 @@ __global__ void __launch_bounds__(kBkThreads, 4) bucket_sort_kernel(BucketArgs a
                 if (filter) {
                     float2 ang;
                     float4 pms;
-                    stg::filter_values_u53(x.x0 >> 11, x.x1 >> 11, Y, &ang, &pms);
+                    stg::filter_values_u53(x.x0 >> 11, x.x1 >> 11, stg::yref(Y), &ang, &pms);
                     a.P.ang[p] = ang;
                     a.P.pms[p] = pms;
                 } else {

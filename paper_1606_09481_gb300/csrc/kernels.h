@@ -50,6 +50,7 @@ struct BatchTables {
     const uint32_t *pt_off;      // G + 1
     const uint32_t *idx_base;    // G + 1
     const uint64_t *out_off;     // G + 1
+    const uint32_t *bk_base;     // G + 1: the first sort bucket of each graph (bucket_entries(n) each)
 };
 
 // Everything the range query kernels read and write.
@@ -131,9 +132,6 @@ Status radix_sort(uint64_t n, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals
                   uint32_t *vals_alt, const int *shifts, int num_shifts, void *temp,
                   uint64_t **keys_out, uint32_t **vals_out, cudaStream_t stream);
 
-// Temporary storage of the segmented sort of a batch (tiles of one graph each;
-// the sort itself runs inside the persistent batch launch).
-size_t segmented_temp_bytes(uint32_t num_tiles);
 
 // ---- query.cu ----
 // Range query (Alg. 1): windows, search, candidate test, output; then the heavy
@@ -160,11 +158,13 @@ struct PersistBuffers {
     Meta *metas;                 // G + 1 blocks (control block last)
     const PlanArgs *args;        // G
     BatchTables bt;
-    uint64_t *keys0, *keys1;     // sort key double buffer
-    uint32_t *ids0, *ids1;       // id double buffer
+    uint64_t *keys0;             // sort keys by position (sampling), then the bucket sort's scratch
+    uint64_t *keys1;             // composites by bucket, then the sorted keys (P.key)
     double *r_by_pos;            // FP64 radius by position (FP64 mode)
-    uint32_t *sort_counts;       // segmented_temp_bytes(num_tiles)
-    SortedPoints P;              // gather output (P.key: the sorted keys)
+    uint32_t *bk_counts;         // bucket counts, then the scatter's cursors (bk_base[G] entries)
+    uint32_t *bk_start;          // bucket starts (bk_base[G] + 1 entries)
+    uint32_t *bk_info;           // bucket -> graph << 6 | band, or ~0 for an unused slot (bk_base[G] entries)
+    SortedPoints P;              // gather output (P.key = keys1)
     uint32_t *pairs;
     uint4 *heavy;
     uint32_t heavy_cap;
@@ -175,12 +175,11 @@ struct PersistBuffers {
     uint32_t *bar;               // grid barrier words
     uint64_t timeout_ns;
 };
-// stage marks a persistent launch records: start, plan, sampling, band offsets,
-// 5 sort passes x (counts, scan, scatter), gather, bucket index, filter-mode
+// stage marks a persistent launch records: start, plan, sampling, band offsets +
+// bucket starts, bucket scatter, bucket sort + gather, bucket index, filter-mode
 // query, its heavy chunks, rechecks, phase reset, FP64-mode query, its heavy
 // chunks, results (the last mark is CTA 0's end)
-constexpr int kBatchStages = 28;
-constexpr int kBatchSortPasses = 5;
+constexpr int kBatchStages = 14;
 Status launch_batch_persistent(const PersistBuffers &b, bool verify, cudaStream_t stream);
 // One grid barrier on its own, for the test of the timeout: `missing` CTAs more
 // than the launch has are expected, so with missing > 0 every wait runs out.

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) gather_filter_kernel(const Meta *M, uint6
             filter_values(phi_src[id], r_src[id], G, etab, &a, &q);
         } else {        // generated points: from the variates, without FP64
             const U64x4 x = draw(id, seed);
-            filter_values_u53(x.x0 >> 11, x.x1 >> 11, Y, &a, &q);
+            filter_values_u53(x.x0 >> 11, x.x1 >> 11, yref(Y), &a, &q);
         }
         P.akey[p] = static_cast<uint32_t>(keys[p]);
         P.ang[p] = a;

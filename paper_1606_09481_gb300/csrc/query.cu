@@ -1472,13 +1472,14 @@ __device__ bool grid_sync(uint32_t *bar, uint32_t expected, uint64_t timeout_ns,
 union PersistSmem {
     stg::PlanSmem plan;
     stg::SampleSmem sample;
-    uint32_t hist[stg::kRadix];
     uint32_t warp_sum[stg::kWarps];
     struct {
-        stg::TileSmem sm;
-        uint32_t sval[stg::kTile];
-    } down;
-    stg::YTab ytab;
+        uint32_t off[kMaxBands + 1], bits[kMaxBands];
+    } tables;
+    struct {
+        stg::BucketSmem bucket;
+        uint32_t info[kThreads], s[kThreads], cnt[kThreads];
+    } slots;
     struct {
         BandShared S[kWarps];
         BatchSmem<true> W[kWarps];
@@ -1516,37 +1517,42 @@ __global__ void __launch_bounds__(kThreads, kPersistMinBlocks) batch_persistent_
     if (!sync()) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) C->stage_ns[0] = t_start;  // after the plan cleared the block
     for (uint32_t vb = blockIdx.x; vb < tiles; vb += nblocks)
-        stg::sample_tile(b.metas, bt, b.keys0, b.ids0, b.r_by_pos, vb, U.sample);
+        stg::sample_tile(b.metas, bt, b.keys0, b.r_by_pos, b.bk_counts, vb, U.sample);
     if (!sync()) return;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += nblocks * blockDim.x)
-        stg::band_offsets_one(b.metas + g, bt.pt_off[g], bt.idx_base[g]);
+    // bucket sort (angular sort within each band), the gather fused into its last pass
+    for (uint32_t vb = blockIdx.x; vb < G; vb += nblocks)
+        stg::bucket_scan_graph(b.metas, bt, b.bk_counts, b.bk_start, b.bk_info, vb, U.warp_sum);
     if (!sync()) return;
-    // segmented radix sort of (band << 32 | angle key) with the ids, 8-bit digits
-    uint64_t *kin = b.keys0, *kout = b.keys1;
-    uint32_t *vin = b.ids0, *vout = b.ids1;
-    for (int pass = 0; pass < kBatchSortPasses; ++pass) {
-        const int shift = 8 * pass;
-        for (uint32_t vb = blockIdx.x; vb < tiles; vb += nblocks)
-            stg::seg_upsweep_tile(kin, bt, shift, b.sort_counts, vb, U.hist);
-        if (!sync()) return;
-        for (uint32_t vb = blockIdx.x; vb < G; vb += nblocks) stg::seg_scan_graph(bt, b.sort_counts, vb, U.warp_sum);
-        if (!sync()) return;
-        for (uint32_t vb = blockIdx.x; vb < tiles; vb += nblocks)
-            stg::seg_downsweep_tile<true>(kin, kout, vin, vout, bt, shift, b.sort_counts, vb, U.down.sm, U.down.sval);
-        if (!sync()) return;
-        uint64_t *tk = kin;
-        kin = kout;
-        kout = tk;
-        uint32_t *tv = vin;
-        vin = vout;
-        vout = tv;
+    for (uint32_t vb = blockIdx.x; vb < tiles; vb += nblocks)
+        stg::bucket_scatter_tile(b.metas, bt, b.keys0, b.bk_counts, b.keys1, vb, U.tables.off, U.tables.bits);
+    if (!sync()) return;
+    // bucket slots in rounds of kThreads per CTA: each thread looks up one slot, so
+    // the unused and empty slots cost no serial loads
+    const uint32_t nbk = bt.bk_base[G];
+    for (uint32_t r0 = blockIdx.x; r0 < nbk; r0 += kThreads * nblocks) {
+        __syncthreads();  // the previous round is done with the slot table
+        const uint32_t vb = r0 + threadIdx.x * nblocks;
+        uint32_t info = 0xffffffffu, s0 = 0, s1 = 0;
+        if (vb < nbk) {
+            info = b.bk_info[vb];
+            if (info != 0xffffffffu) {
+                s0 = b.bk_start[vb];
+                s1 = b.bk_start[vb + 1];
+            }
+        }
+        U.slots.info[threadIdx.x] = s1 > s0 ? info : 0xffffffffu;
+        U.slots.s[threadIdx.x] = s0;
+        U.slots.cnt[threadIdx.x] = s1 - s0;
+        __syncthreads();
+        for (int t = 0; t < kThreads; ++t) {
+            const uint32_t info_t = U.slots.info[t];
+            if (info_t == 0xffffffffu) continue;
+            stg::bucket_gather_item(b.metas, bt, info_t, U.slots.s[t], U.slots.cnt[t], b.keys1, b.keys0, b.r_by_pos,
+                                    b.P, U.slots.bucket);
+        }
     }
-    // gather (a tile's graph is in filter or in FP64 mode: one of the two writes)
-    for (uint32_t vb = blockIdx.x; vb < tiles; vb += nblocks) {
-        stg::gather_filter_tile(b.metas, bt, kin, vin, b.P, vb, U.ytab);
-        stg::gather_fp64_tile(b.metas, bt, kin, vin, b.r_by_pos, b.P, vb);
-    }
     if (!sync()) return;
+    const uint64_t *kin = b.keys1;
     for (uint32_t vb = blockIdx.x; vb < tiles; vb += nblocks) bucket_index_tile(b.metas, bt, kin, b.bidx, vb);
     if (!sync()) return;
     // range query: the filter graphs, then the FP64 graphs

@@ -107,8 +107,6 @@ size_t radix_temp_bytes(uint64_t n)
     return static_cast<size_t>(kRadix) * (g.ctas + 1) * sizeof(uint32_t);
 }
 
-size_t segmented_temp_bytes(uint32_t num_tiles) { return static_cast<size_t>(kRadix) * (num_tiles + 1) * 4; }
-
 Status radix_sort(uint64_t n, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                   const int *shifts, int num_shifts, void *temp, uint64_t **keys_out,
                   uint32_t **vals_out, cudaStream_t stream)

@@ -1,10 +1,11 @@
 // stages.cuh -- device bodies of the point pipeline's stages that both the
 // per-stage kernels and the persistent batch kernel run: the plan (R and band
 // boundaries, Sec. III-A/B), sampling (Alg. 1 sampling step, Eq. 1), band
-// offsets, the filter values and gathers, the stable radix-sort tile passes
-// (Alg. 1, angular sort within each band) and the per-graph results.  A body that
-// works on one tile or graph takes its index and its shared memory from the
-// caller, so that one CTA can run several items one after another.
+// offsets, the filter values, the stable radix-sort tile pass and the bucket sort
+// (Alg. 1, angular sort within each band) with the gather fused in, and the
+// per-graph results.  A body that works on one tile, graph or bucket takes its
+// index and its shared memory from the caller, so that one CTA can run several
+// items one after another.
 #pragma once
 #include "kernels.h"
 
@@ -281,6 +282,7 @@ constexpr int kSampleThreads = 256;
 struct SampleSmem {
     double c[kMaxBands + 1];
     uint64_t bu[kMaxBands + 1];
+    uint32_t bk_off[kMaxBands + 1], bk_bits[kMaxBands];
     unsigned int hist[kMaxBands];
 };
 
@@ -296,7 +298,7 @@ __device__ __forceinline__ void hist_add_warp(unsigned int *hist, uint32_t b)
 
 // Batch, tile t (one CTA): position p of graph g holds vertex p - pt_off[g]; the
 // FP64 radius (FP64 mode) is stored by position.
-__device__ void sample_tile(Meta *metas, const BatchTables &bt, uint64_t *keys, uint32_t *ids, double *r_by_pos,
+__device__ void sample_tile(Meta *metas, const BatchTables &bt, uint64_t *keys, double *r_by_pos, uint32_t *bk_counts,
                             uint32_t t, SampleSmem &SS)
 {
     double *c = SS.c;
@@ -312,18 +314,22 @@ __device__ void sample_tile(Meta *metas, const BatchTables &bt, uint64_t *keys, 
     if (threadIdx.x <= B) {
         c[threadIdx.x] = M->c[threadIdx.x];
         bu[threadIdx.x] = M->band_u[threadIdx.x];
+        SS.bk_off[threadIdx.x] = M->bk_off[threadIdx.x];
+        if (threadIdx.x < B) SS.bk_bits[threadIdx.x] = M->bk_bits[threadIdx.x];
     }
     if (threadIdx.x < kMaxBands) hist[threadIdx.x] = 0;
     __syncthreads();
     if (M->error) return;
     const uint32_t first_id = T.y - bt.pt_off[T.x];
-    // warp-uniform trip count (the histogram is counted per warp)
+    uint32_t *counts = bk_counts + bt.bk_base[T.x];
+    // warp-uniform trip count (the histograms are counted per warp)
     for (uint32_t j0 = threadIdx.x & ~31u; j0 < T.z; j0 += blockDim.x) {
         const uint32_t j = j0 + (threadIdx.x & 31u);
-        uint32_t b = kMaxBands;
+        uint32_t b = kMaxBands, akey = 0;
         if (j < T.z) {
             const uint32_t id = first_id + j, pos = T.y + j;
             const U64x4 x = draw(id, seed);
+            akey = static_cast<uint32_t>(x.x0 >> 32);
             if (filter) {
                 b = band_of_u53(x.x1 >> 11, bu, B);
             } else {
@@ -331,10 +337,14 @@ __device__ void sample_tile(Meta *metas, const BatchTables &bt, uint64_t *keys, 
                 r_by_pos[pos] = r;
                 b = band_of(r, c, B);
             }
-            keys[pos] = (static_cast<uint64_t>(b) << 32) | static_cast<uint32_t>(x.x0 >> 32);
-            ids[pos] = id;
+            keys[pos] = (static_cast<uint64_t>(b) << 32) | akey;
         }
         hist_add_warp(hist, b);
+        const uint32_t bk = b < B ? bucket_of((static_cast<uint64_t>(b) << 32) | akey, SS.bk_off, SS.bk_bits)
+                                  : 0xffffffffu;
+        const unsigned peers = __match_any_sync(0xffffffffu, bk);
+        if (bk != 0xffffffffu && (peers & ((1u << (threadIdx.x & 31u)) - 1u)) == 0)
+            atomicAdd(&counts[bk], static_cast<uint32_t>(__popc(peers)));
     }
     __syncthreads();
     if (threadIdx.x < B && hist[threadIdx.x]) atomicAdd(&M->band_count[threadIdx.x], hist[threadIdx.x]);
@@ -418,6 +428,23 @@ __device__ __forceinline__ void load_ytab(YTab &Y, const Meta *M)
     }
 }
 
+// The same constants where filter_values_u53 reads them: shared memory (YTab) or
+// a graph's Meta in global memory.
+struct YRef {
+    const float *P, *M;
+    float cw, ia, y_one;
+    uint32_t alpha_one;
+    double G, inv_alpha;
+};
+__device__ __forceinline__ YRef yref(const YTab &Y)
+{
+    return YRef{Y.P, Y.M, Y.cw, Y.ia, Y.y_one, Y.alpha_one, Y.G, Y.inv_alpha};
+}
+__device__ __forceinline__ YRef yref(const Meta *M)
+{
+    return YRef{M->tabP, M->tabM, M->cw, M->inv_alpha_f, M->y_one, M->alpha_one, M->G, M->inv_alpha};
+}
+
 // Filter-mode values of a generated point from its variates (ua: angle, ur:
 // radius), in FP32 and integer arithmetic (the rare points with r < 1 aside):
 //   angle  angle_hilo_u53: the pair filter_values forms from the FP64 angle;
@@ -433,7 +460,7 @@ __device__ __forceinline__ void load_ytab(YTab &Y, const Meta *M)
 //          3.7e-7 + 2 u <= 1.2e-6 < kEpsPM for alpha > 1/2;
 //   S      (P - M) / sqrt 2 for r >= 1 (y >= e^alpha), as filter_values; below,
 //          from the radius ln(y) / alpha in FP64 (absolute error <= 6 u / alpha).
-__device__ __forceinline__ void filter_values_u53(uint64_t ua, uint64_t ur, const YTab &Y, float2 *ang,
+__device__ __forceinline__ void filter_values_u53(uint64_t ua, uint64_t ur, const YRef &Y, float2 *ang,
                                                   float4 *pms)
 {
     *ang = angle_hilo_u53(ua);
@@ -471,53 +498,6 @@ __device__ __forceinline__ void filter_values_u53(uint64_t ua, uint64_t ur, cons
         gam = 0.0f;
     }
     *pms = make_float4(P, Mv, S, gam);
-}
-
-// Batch gathers, tile t (one CTA); ids are local, the FP64 radius is by position.
-__device__ void gather_filter_tile(const Meta *metas, const BatchTables &bt, const uint64_t *keys,
-                                   const uint32_t *sids, const SortedPoints &P, uint32_t t, YTab &Y)
-{
-    __syncthreads();  // the CTA's previous item is done with Y
-    const uint4 T = bt.tiles[t];
-    const Meta *M = metas + T.x;
-    load_ytab(Y, M);
-    __syncthreads();
-    if (M->error || !M->filter) return;
-    const uint64_t seed = M->seed;
-    for (uint32_t j = threadIdx.x; j < T.z; j += blockDim.x) {
-        const uint32_t p = T.y + j;
-        const uint32_t id = sids[p];
-        const U64x4 x = draw(id, seed);
-        float2 a;
-        float4 q;
-        filter_values_u53(x.x0 >> 11, x.x1 >> 11, Y, &a, &q);
-        P.akey[p] = static_cast<uint32_t>(keys[p]);
-        P.ang[p] = a;
-        P.pms[p] = q;
-        P.id[p] = id;
-    }
-}
-
-__device__ void gather_fp64_tile(const Meta *metas, const BatchTables &bt, const uint64_t *keys,
-                                 const uint32_t *sids, const double *r_by_pos, const SortedPoints &P, uint32_t t)
-{
-    const uint4 T = bt.tiles[t];
-    const Meta *M = metas + T.x;
-    if (M->error || M->filter) return;
-    const uint64_t seed = M->seed;
-    const uint32_t pos0 = bt.pt_off[T.x];
-    for (uint32_t j = threadIdx.x; j < T.z; j += blockDim.x) {
-        const uint32_t p = T.y + j;
-        const uint32_t id = sids[p];
-        const double ph = phi_from_u53(draw(id, seed).x0 >> 11);
-        const double r = r_by_pos[pos0 + id];
-        P.phi[p] = ph;
-        P.r[p] = r;
-        P.ch[p] = dm::cosh(r);
-        P.sh[p] = dm::sinh(r);
-        P.akey[p] = static_cast<uint32_t>(keys[p]);
-        P.id[p] = id;
-    }
 }
 
 // Per-graph results of a batch: {m low, m high, R low, R high} and {B, error}.
@@ -640,69 +620,191 @@ __device__ __forceinline__ void tile_pass(const uint64_t *keys_in, uint64_t *key
     __syncthreads();
 }
 
-// ---- segmented (batch): tiles of one graph each, per-tile digit counts
-static_assert(kTile == static_cast<int>(kTilePoints), "batch tiles are sort tiles");
+// ---- bucket sort of generated points (one bucket per call; see bucket.cu)
+constexpr uint32_t kSubMax = 32;  // largest sub-bucket sorted by one thread
 
-// Tile t (one CTA of kThreads): the digit counts of the tile.
-__device__ void seg_upsweep_tile(const uint64_t *keys, const BatchTables &bt, int shift, uint32_t *counts,
-                                 uint32_t t, uint32_t *hist)
+// LSD radix sort of comp[s, s + cnt) by one CTA (8 passes of 8 bits through
+// scratch, tiles in order, so stable), for buckets the shared-memory path cannot
+// take.  The result is back in comp.
+__device__ void cta_sort_range(uint64_t *comp, uint64_t *scratch, uint32_t s, uint32_t cnt, TileSmem &ts,
+                               uint32_t *hist)
 {
-    __syncthreads();  // the CTA's previous item is done with hist
-    hist[threadIdx.x] = 0;
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 8 * pass;
+        const uint64_t *src = (pass & 1) ? scratch : comp;
+        uint64_t *dst = (pass & 1) ? comp : scratch;
+        __syncthreads();
+        hist[threadIdx.x] = 0;
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < cnt; k += kThreads) atomicAdd(&hist[(src[s + k] >> shift) & 255u], 1u);
+        __syncthreads();
+        ts.digit_base[threadIdx.x] = s + block_exclusive(hist[threadIdx.x], ts.warp_sum);
+        __syncthreads();
+        for (uint32_t t = 0; t < cnt; t += kTile) {
+            const uint32_t c = cnt - t < static_cast<uint32_t>(kTile) ? cnt - t : kTile;
+            tile_pass<false>(src, dst, nullptr, nullptr, s + t, c, shift, ts, nullptr);
+        }
+    }
     __syncthreads();
-    const uint4 T = bt.tiles[t];
-    for (uint32_t j = threadIdx.x; j < T.z; j += kThreads) atomicAdd(&hist[(keys[T.y + j] >> shift) & (kRadix - 1)], 1u);
-    __syncthreads();
-    counts[static_cast<uint64_t>(t) * kRadix + threadIdx.x] = hist[threadIdx.x];
 }
 
-// CTA per graph: counts[t][d] of the graph's tiles become the output position of
-// tile t's first key of digit d (graph start + keys of smaller digits + keys of
-// digit d in earlier tiles of the graph).
-__device__ void seg_scan_graph(const BatchTables &bt, uint32_t *counts, uint32_t g, uint32_t *warp_sum)
+struct BucketSmem {
+    union {
+        uint64_t buf[2][kBucketCap];
+        TileSmem ts;
+    } u;
+    uint32_t hist[256], cur[256], wsum[kWarps];
+    int big;
+};
+
+// Sorts the bucket comp[s, s + cnt), composites (angle key << 32 | id), by
+// (angle key, id): in shared memory a counting pass on the 8 angle-key bits at
+// composite shift dsh (the ones below the bucket's own), then every sub-bucket by
+// one thread (insertion sort); a bucket above kBucketCap, or with a sub-bucket
+// above kSubMax, by cta_sort_range in global memory.  Returns where element k of
+// the sorted bucket is (shared memory, or comp + s).  All threads of the CTA
+// (kThreads) call it; it begins and ends with a barrier.
+__device__ const uint64_t *sort_bucket(uint64_t *comp, uint64_t *scratch, uint32_t s, uint32_t cnt, int dsh,
+                                       BucketSmem &B)
+{
+    const uint32_t t = threadIdx.x;
+    __syncthreads();  // the CTA's previous bucket is done with B
+    if (cnt <= kBucketCap) {
+        B.hist[t] = 0;
+        if (t == 0) B.big = 0;
+        __syncthreads();
+        for (uint32_t k = t; k < cnt; k += kThreads) {
+            const uint64_t v = comp[s + k];
+            B.u.buf[0][k] = v;
+            atomicAdd(&B.hist[static_cast<uint32_t>(v >> dsh) & 255u], 1u);
+        }
+        __syncthreads();
+        const uint32_t h = B.hist[t];
+        B.cur[t] = block_exclusive(h, B.wsum);
+        if (h > kSubMax) B.big = 1;
+        __syncthreads();
+        for (uint32_t k = t; k < cnt; k += kThreads) {
+            const uint64_t v = B.u.buf[0][k];
+            B.u.buf[1][atomicAdd(&B.cur[static_cast<uint32_t>(v >> dsh) & 255u], 1u)] = v;
+        }
+        __syncthreads();
+        const bool big = B.big != 0;
+        if (!big) {  // sub-bucket t is [cur[t] - h, cur[t])
+            uint64_t *x = B.u.buf[1];
+            const uint32_t e1 = B.cur[t], s1 = e1 - h;
+            for (uint32_t i = s1 + 1; i < e1; ++i) {
+                const uint64_t v = x[i];
+                uint32_t j = i;
+                while (j > s1 && x[j - 1] > v) {
+                    x[j] = x[j - 1];
+                    --j;
+                }
+                x[j] = v;
+            }
+        }
+        __syncthreads();
+        if (!big) return B.u.buf[1];
+    }
+    cta_sort_range(comp, scratch, s, cnt, B.u.ts, B.hist);
+    return comp + s;
+}
+
+// Batch, graph g (one CTA): band offsets (band_offsets_one), then the exclusive
+// scan of the graph's bucket counts into bucket starts (global positions) and
+// scatter cursors; start[nb] = the graph's end.
+__device__ void bucket_scan_graph(Meta *metas, const BatchTables &bt, uint32_t *bk_counts, uint32_t *bk_start,
+                                  uint32_t *bk_info, uint32_t g, uint32_t *warp_sum)
 {
     __syncthreads();  // the CTA's previous item is done with warp_sum
-    const uint32_t d = threadIdx.x;
-    const uint32_t t0 = bt.tile_first[g], t1 = bt.tile_first[g + 1];
-    constexpr uint32_t kAhead = 8;  // tiles whose counts are loaded together (latency, not bandwidth)
-    uint32_t run = 0;
-    for (uint32_t t = t0; t < t1; t += kAhead) {
-        uint32_t v[kAhead];
-#pragma unroll
-        for (uint32_t u = 0; u < kAhead; ++u) v[u] = t + u < t1 ? counts[static_cast<uint64_t>(t + u) * kRadix + d] : 0u;
-#pragma unroll
-        for (uint32_t u = 0; u < kAhead; ++u) {
-            const uint32_t c = v[u];
-            v[u] = run;
-            run += c;
+    Meta *M = metas + g;
+    if (threadIdx.x == 0) band_offsets_one(M, bt.pt_off[g], bt.idx_base[g]);
+    const uint32_t nb = M->nbuckets, base = bt.bk_base[g], B = M->B;
+    const bool bad = M->error != 0;
+    uint32_t carry = bt.pt_off[g];
+    for (uint32_t j0 = 0; j0 < nb; j0 += kThreads) {
+        const uint32_t j = j0 + threadIdx.x;
+        const uint32_t v = j < nb && !bad ? bk_counts[base + j] : 0u;
+        const uint32_t excl = block_exclusive(v, warp_sum);  // ends with a barrier
+        uint32_t chunk = 0;
+        for (int w = 0; w < kWarps; ++w) chunk += warp_sum[w];
+        if (j < nb) {
+            bk_start[base + j] = carry + excl;
+            bk_counts[base + j] = carry + excl;
+            uint32_t band = 0;  // the largest band whose first bucket is <= j
+            for (uint32_t step = 32; step; step >>= 1)
+                if (band + step < B && M->bk_off[band + step] <= j) band += step;
+            bk_info[base + j] = (g << 6) | band;  // a graph in error has only empty buckets
         }
-#pragma unroll
-        for (uint32_t u = 0; u < kAhead; ++u)
-            if (t + u < t1) counts[static_cast<uint64_t>(t + u) * kRadix + d] = v[u];
+        carry += chunk;
+        __syncthreads();
     }
-    const uint32_t base = bt.pt_off[g] + block_exclusive(run, warp_sum);
-    for (uint32_t t = t0; t < t1; t += kAhead) {
-        uint32_t v[kAhead];
-#pragma unroll
-        for (uint32_t u = 0; u < kAhead; ++u) v[u] = t + u < t1 ? counts[static_cast<uint64_t>(t + u) * kRadix + d] : 0u;
-#pragma unroll
-        for (uint32_t u = 0; u < kAhead; ++u)
-            if (t + u < t1) counts[static_cast<uint64_t>(t + u) * kRadix + d] = v[u] + base;
-    }
+    if (threadIdx.x == 0) bk_start[base + nb] = carry;
+    // the graph's unused bucket slots
+    for (uint32_t j = nb + threadIdx.x; j < bt.bk_base[g + 1] - base; j += kThreads) bk_info[base + j] = 0xffffffffu;
 }
 
-template <bool kValues>
-__device__ void seg_downsweep_tile(const uint64_t *keys_in, uint64_t *keys_out, const uint32_t *vals_in,
-                                   uint32_t *vals_out, const BatchTables &bt, int shift, const uint32_t *offsets,
-                                   uint32_t t, TileSmem &sm, uint32_t *sval)
+// Batch, tile t (one CTA): each point's composite (angle key << 32 | id) to its
+// bucket, at a cursor taken with an atomic add.
+__device__ void bucket_scatter_tile(const Meta *metas, const BatchTables &bt, const uint64_t *keys, uint32_t *cursor,
+                                    uint64_t *comp, uint32_t t, uint32_t *off, uint32_t *bits)
 {
-    __syncthreads();  // the CTA's previous item is done with sm
+    __syncthreads();  // the CTA's previous item is done with the tables
     const uint4 T = bt.tiles[t];
-    sm.digit_base[threadIdx.x] = offsets[static_cast<uint64_t>(t) * kRadix + threadIdx.x];
+    const Meta *M = metas + T.x;
+    const uint32_t B = M->B;
+    if (threadIdx.x <= B) {
+        off[threadIdx.x] = M->bk_off[threadIdx.x];
+        if (threadIdx.x < B) bits[threadIdx.x] = M->bk_bits[threadIdx.x];
+    }
     __syncthreads();
-    tile_pass<kValues>(keys_in, keys_out, vals_in, vals_out, T.y, T.z, shift, sm, sval);
+    if (M->error) return;
+    uint32_t *cur = cursor + bt.bk_base[T.x];
+    const uint32_t first_id = T.y - bt.pt_off[T.x];
+    for (uint32_t j = threadIdx.x; j < T.z; j += blockDim.x) {
+        const uint64_t k = keys[T.y + j];
+        comp[atomicAdd(&cur[bucket_of(k, off, bits)], 1u)] = (k << 32) | (first_id + j);
+    }
 }
 
+// Batch, one bucket (one CTA): info = graph << 6 | band, the bucket's points
+// [s, s + cnt); the bucket sorted (sort_bucket), then the sorted key back into
+// comp (P.key) and each point's arrays, as the single-graph bucket sort writes
+// them (ids are the graph's own, the FP64 radius by position).
+__device__ void bucket_gather_item(Meta *metas, const BatchTables &bt, uint32_t info, uint32_t s, uint32_t cnt,
+                                   uint64_t *comp, uint64_t *scratch, const double *r_by_pos, const SortedPoints &P,
+                                   BucketSmem &SB)
+{
+    const uint32_t g = info >> 6, band = info & 63u;
+    const Meta *M = metas + g;
+    const int rest = 32 - static_cast<int>(M->bk_bits[band]);
+    const int dsh = 32 + (rest > 8 ? rest - 8 : 0);
+    const uint64_t *sorted = sort_bucket(comp, scratch, s, cnt, dsh, SB);
+    const bool filter = M->filter != 0;
+    const uint64_t seed = M->seed;
+    const YRef Y = yref(M);
+    const uint32_t pos0 = bt.pt_off[g];
+    for (uint32_t k = threadIdx.x; k < cnt; k += kThreads) {
+        const uint64_t c = sorted[k];
+        const uint32_t p = s + k, id = static_cast<uint32_t>(c), akey = static_cast<uint32_t>(c >> 32);
+        comp[p] = (static_cast<uint64_t>(band) << 32) | akey;
+        P.akey[p] = akey;
+        P.id[p] = id;
+        const U64x4 x = draw(id, seed);
+        if (filter) {
+            float2 ang;
+            float4 pms;
+            filter_values_u53(x.x0 >> 11, x.x1 >> 11, Y, &ang, &pms);
+            P.ang[p] = ang;
+            P.pms[p] = pms;
+        } else {
+            const double r = r_by_pos[pos0 + id];
+            P.phi[p] = phi_from_u53(x.x0 >> 11);
+            P.r[p] = r;
+            P.ch[p] = dm::cosh(r);
+            P.sh[p] = dm::sinh(r);
+        }
+    }
+}
 
 }  // namespace stg
 }  // namespace

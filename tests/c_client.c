@@ -26,7 +26,7 @@ int main(void)
     rhg_batch_graph res[2];
     rhg_result totals;
 
-    CHECK(rhg_version() == 3);
+    CHECK(rhg_version() == 4);
     CHECK(strcmp(rhg_status_str(RHG_OK), "RHG_OK") == 0);
     CHECK(strcmp(rhg_status_str(RHG_ERR_OVERFLOW), "RHG_ERR_OVERFLOW") == 0);
 

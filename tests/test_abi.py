@@ -39,7 +39,7 @@ def test_status_strings_and_version(rhg):
     assert rhg.status_str(0) == "RHG_OK"
     assert rhg.status_str(6) == "RHG_ERR_OVERFLOW"
     assert rhg.status_str(99) == "RHG_ERR_UNKNOWN"
-    assert rhg.load().rhg_version() == 3
+    assert rhg.load().rhg_version() == 4
 
 
 def test_params_layout_matches_header(rhg):
