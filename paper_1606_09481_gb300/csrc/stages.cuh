@@ -35,25 +35,36 @@ __device__ double kbar(double R, double nd, double alpha)
     return mul(pre, add(e1, mul(e2, br)));
 }
 
-constexpr int kPlanThreads = 256;  // grid points j = 0..255 of the bracket search
+constexpr int kBracket = 256;      // grid points j = 0..255 of the bracket search
+constexpr int kPlanThreads = 256;  // the single-graph plan: 8 bisection steps per round
+constexpr int kPlanNodes = 256;    // speculative nodes per round, at most (deeper rounds
+                                   // are bound by the FP64 pipe's throughput: measured slower)
 
 // Shared state of plan_block.
 struct PlanSmem {
-    double R_sh, lo_sh, hi_sh;
+    double R_sh, lo_sh, hi_sh, sq;
     int jstar, fail, walk_done;
-    uint8_t above[kPlanThreads];  // node t of a round's tree: kbar(its midpoint) > k
+    double mid[kPlanNodes];      // node t of a round's tree: its midpoint
+    uint8_t above[kPlanNodes];   // kbar(its midpoint) > k
+    uint8_t valid[kPlanNodes];   // its midpoint lies strictly inside its interval
 };
 
-// R, boundaries and the band constants of one graph, by one CTA of kPlanThreads.
-// depth: bisection steps taken per round (2^depth - 1 speculative evaluations;
-// 8 when one graph wants the lowest latency, fewer when many graphs share the
-// FP64 units).  All threads of the CTA call it (it synchronises the CTA).
+__device__ __forceinline__ bool same(double x, double y)
+{
+    return __double_as_longlong(x) == __double_as_longlong(y);  // non-negative, finite
+}
+
+// R, boundaries and the band constants of one graph, by one CTA.  depth:
+// bisection steps taken per round (2^depth - 1 speculative evaluations, at most
+// blockDim.x - 1 and kPlanNodes - 1; 8 when one graph wants the lowest latency,
+// fewer when many graphs share the FP64 units).  GB300's FP64 pipe takes tens of
+// ns per dependent operation, so the work is laid out for short serial chains.
+// All threads of the CTA call it (it synchronises the CTA); blockDim.x >= kBracket.
 __device__ void plan_block(Meta *M, const PlanArgs &a, int depth, PlanSmem &PS)
 {
     int &jstar = PS.jstar;
     double &R_sh = PS.R_sh, &lo_sh = PS.lo_sh, &hi_sh = PS.hi_sh;
     int &fail = PS.fail, &walk_done = PS.walk_done;
-    uint8_t *above = PS.above;
     const int t = threadIdx.x;
     const double nd = static_cast<double>(a.n);
     const double alpha = a.alpha, k = a.k;
@@ -65,10 +76,10 @@ __device__ void plan_block(Meta *M, const PlanArgs &a, int depth, PlanSmem &PS)
     __syncthreads();
     if (!(a.R_override > 0.0)) {
         // bracket: the largest integer grid point j with kbar(j) > k
-        if (kbar(static_cast<double>(t), nd, alpha) > k) atomicMax(&jstar, t);
+        if (t < kBracket && kbar(static_cast<double>(t), nd, alpha) > k) atomicMax(&jstar, t);
         __syncthreads();
         if (t == 0) {
-            fail = (jstar < 0 || jstar == kPlanThreads - 1) ? 1 : 0;
+            fail = (jstar < 0 || jstar == kBracket - 1) ? 1 : 0;
             walk_done = fail;
             lo_sh = static_cast<double>(jstar);
             hi_sh = static_cast<double>(jstar + 1);
@@ -77,46 +88,50 @@ __device__ void plan_block(Meta *M, const PlanArgs &a, int depth, PlanSmem &PS)
         // binary search: mid = (lo + hi) / 2, kbar(mid) > k ? lo = mid : hi = mid, until
         // lo and hi are adjacent (at most 200 steps); R = hi.  Each round takes
         // `depth` steps at once: thread t (heap order, root 1) replays the path its
-        // index spells from (lo, hi) and evaluates kbar at its midpoint, then thread
-        // 0 follows the comparisons: the same midpoints and decisions as one step
-        // at a time.
+        // index spells from (lo, hi), keeps its midpoint and evaluates kbar there;
+        // then thread 0 follows the comparisons through the kept midpoints: the
+        // same midpoints and decisions as one step at a time.
         const int nodes = 1 << depth;
         int steps = 0;
         for (int round = 0; round < 200; ++round) {
             if (walk_done) break;
             if (t >= 1 && t < nodes) {
                 double lo = lo_sh, hi = hi_sh;
-                const int depth = 31 - __clz(t);
+                const int level = 31 - __clz(t);
                 bool live = true;
-                for (int d = depth - 1; d >= 0 && live; --d) {
+                for (int d = level - 1; d >= 0 && live; --d) {
                     const double mid = mul(add(lo, hi), 0.5);
-                    if (mid == lo || mid == hi) live = false;
+                    if (same(mid, lo) || same(mid, hi)) live = false;
                     else if ((t >> d) & 1) lo = mid;
                     else hi = mid;
                 }
-                uint8_t b = 0;
+                uint8_t b = 0, v = 0;
                 if (live) {
                     const double mid = mul(add(lo, hi), 0.5);
-                    if (mid != lo && mid != hi) b = kbar(mid, nd, alpha) > k ? 1 : 0;
+                    if (!same(mid, lo) && !same(mid, hi)) {
+                        v = 1;
+                        PS.mid[t] = mid;
+                        b = kbar(mid, nd, alpha) > k ? 1 : 0;
+                    }
                 }
-                above[t] = b;
+                PS.above[t] = b;
+                PS.valid[t] = v;
             }
             __syncthreads();
             if (t == 0) {
                 double lo = lo_sh, hi = hi_sh;
                 int node = 1;
                 for (int d = 0; d < depth; ++d) {
-                    const double mid = mul(add(lo, hi), 0.5);
-                    if (mid == lo || mid == hi || steps == 200) {
+                    if (!PS.valid[node] || steps == 200) {
                         walk_done = 1;
                         break;
                     }
                     ++steps;
-                    if (above[node]) {
-                        lo = mid;
+                    if (PS.above[node]) {
+                        lo = PS.mid[node];
                         node = 2 * node + 1;
                     } else {
-                        hi = mid;
+                        hi = PS.mid[node];
                         node = 2 * node;
                     }
                 }
@@ -129,19 +144,23 @@ __device__ void plan_block(Meta *M, const PlanArgs &a, int depth, PlanSmem &PS)
     }
     __syncthreads();
     const double R = fail ? 1.0 : R_sh;
-    const double coshR = dm::cosh(R);
-    const double G = 0.5 * ::log(2.0 * coshR);
-    // e^k table (threads 0..128)
-    if (t <= 2 * kExpTab) M->etab[t] = static_cast<float>(::exp(static_cast<double>(t - kExpTab)));
     const uint32_t B = a.B;
-    if (t == 0) {  // scalars and the boundaries (a short recurrence)
-        M->error = fail ? kErrNoSolution : kErrNone;
-        M->R = R;
+    // e^k table (threads 0..128), cosh R, G, e^-G, the scalars and the boundaries
+    // (a short recurrence), each part by its own thread
+    if (t <= 2 * kExpTab) M->etab[t] = static_cast<float>(::exp(static_cast<double>(t - kExpTab)));
+    if (t == 2 * kExpTab + 1) {
+        const double coshR = dm::cosh(R);
+        const double G = 0.5 * ::log(2.0 * coshR);
         M->coshR = coshR;
         M->G = G;
+        PS.sq = ::exp(-G);
+    }
+    if (t == 2 * kExpTab + 2) M->cm1 = sub(dm::cosh(mul(alpha, R)), 1.0);
+    if (t == 0) {
+        M->error = fail ? kErrNoSolution : kErrNone;
+        M->R = R;
         M->alpha = alpha;
         M->inv_alpha = div(1.0, alpha);
-        M->cm1 = sub(dm::cosh(mul(alpha, R)), 1.0);
         const double p = a.p;
         M->B = B;
         M->batch_budget = a.batch_budget;
@@ -170,56 +189,73 @@ __device__ void plan_block(Meta *M, const PlanArgs &a, int depth, PlanSmem &PS)
         M->c[B] = R;
     }
     __syncthreads();
-    // FP32 window constants, one band per thread: band i is bounded by c_i - kDeltaR
-    // (inner) and c_{i+1} + kDeltaR (outer), a slack well above how far a member's
-    // FP64 radius can be from its band (1e-13: band_of_u53; caller points are
-    // assigned by their FP64 radius)
-    const double sq = ::exp(-G);
-    for (uint32_t j = t; j <= B; j += blockDim.x) {
-        M->cosh_c[j] = ::cosh(M->c[j]);
-        M->sinh_c[j] = ::sinh(M->c[j]);
-        const double ci = M->c[j] - kDeltaR > 0.0 ? M->c[j] - kDeltaR : 0.0;
-        M->band_P[j] = static_cast<float>(::exp(ci) * sq);
-        M->band_M[j] = static_cast<float>(::exp(-ci) * sq);
-        M->band_S[j] = static_cast<float>(::sinh(ci) * sq * 1.4142135623730951);
-        const double co = (j < B ? M->c[j + 1] : R) + kDeltaR;
-        M->band_PMn[j] = static_cast<float>(2.0 * ::cosh(co) * sq * (1.0 + 1e-6));
-        M->band_Po[j] = static_cast<float>(::exp(co) * sq);
-        M->band_Mo[j] = static_cast<float>(::exp(-co) * sq);
-        M->band_So[j] = static_cast<float>(::sinh(co) * sq * 1.4142135623730951);
-    }
-    // generated points in filter mode (band_of_u53, filter_values_u53)
-    const double cm1 = M->cm1;
-    for (uint32_t j = t; j <= B; j += blockDim.x) {
-        uint64_t bu = 0;
-        if (j == B) {
-            bu = uint64_t{1} << 53;
-        } else if (j > 0) {
-            const double sh = ::sinh(0.5 * alpha * M->c[j]);
-            const double F = 2.0 * sh * sh / cm1;  // (cosh(alpha c_j) - 1) / (cosh(alpha R) - 1)
-            const double T = ceil(F * 9007199254740992.0);
-            bu = T <= 0.0 ? 0 : (T >= 9007199254740992.0 ? uint64_t{1} << 53 : static_cast<uint64_t>(T));
+    const double G = M->G, sq = PS.sq, cm1 = M->cm1;
+    // per band j: the FP64 cosh / sinh of the boundary and the FP32 window constants
+    // (band i is bounded by c_i - kDeltaR (inner) and c_{i+1} + kDeltaR (outer), a
+    // slack well above how far a member's FP64 radius can be from its band: 1e-13,
+    // band_of_u53; caller points are assigned by their FP64 radius); the variate
+    // thresholds band_u (band_of_u53); the exponent tables (filter_values_u53).
+    // One value per thread.
+    const uint32_t nv = 10 * (B + 1) + 2 * kYTab;
+    for (uint32_t v = t; v < nv; v += blockDim.x) {
+        if (v < 10 * (B + 1)) {
+            const uint32_t j = v / 10, which = v % 10;
+            const double cj = M->c[j];
+            const double ci = cj - kDeltaR > 0.0 ? cj - kDeltaR : 0.0;
+            const double co = (j < B ? M->c[j + 1] : R) + kDeltaR;
+            switch (which) {
+                case 0: M->cosh_c[j] = ::cosh(cj); break;
+                case 1: M->sinh_c[j] = ::sinh(cj); break;
+                case 2: M->band_P[j] = static_cast<float>(::exp(ci) * sq); break;
+                case 3: M->band_M[j] = static_cast<float>(::exp(-ci) * sq); break;
+                case 4: M->band_S[j] = static_cast<float>(::sinh(ci) * sq * 1.4142135623730951); break;
+                case 5: M->band_PMn[j] = static_cast<float>(2.0 * ::cosh(co) * sq * (1.0 + 1e-6)); break;
+                case 6: M->band_Po[j] = static_cast<float>(::exp(co) * sq); break;
+                case 7: M->band_Mo[j] = static_cast<float>(::exp(-co) * sq); break;
+                case 8: M->band_So[j] = static_cast<float>(::sinh(co) * sq * 1.4142135623730951); break;
+                default: {
+                    uint64_t bu = 0;
+                    if (j == B) {
+                        bu = uint64_t{1} << 53;
+                    } else if (j > 0) {
+                        const double sh = ::sinh(0.5 * alpha * cj);
+                        const double F = 2.0 * sh * sh / cm1;  // (cosh(alpha c_j) - 1) / (cosh(alpha R) - 1)
+                        const double T = ceil(F * 9007199254740992.0);
+                        bu = T <= 0.0 ? 0 : (T >= 9007199254740992.0 ? uint64_t{1} << 53 : static_cast<uint64_t>(T));
+                    }
+                    M->band_u[j] = bu;
+                }
+            }
+        } else {
+            const uint32_t e = (v - 10 * (B + 1)) >> 1;
+            const double ea = static_cast<double>(e) * 0.69314718055994530942 / alpha;  // ln(2^(e/alpha))
+            if ((v - 10 * (B + 1)) & 1u) M->tabM[e] = static_cast<float>(::exp(-ea - G));
+            else M->tabP[e] = static_cast<float>(fmin(::exp(ea - G), 3.0e38));
         }
-        M->band_u[j] = bu;
-    }
-    for (int e = t; e < kYTab; e += blockDim.x) {
-        const double ea = static_cast<double>(e) * 0.69314718055994530942 / alpha;  // ln(2^(e/alpha))
-        M->tabP[e] = static_cast<float>(fmin(::exp(ea - G), 3.0e38));
-        M->tabM[e] = static_cast<float>(::exp(-ea - G));
     }
     if (t < kMaxBands) M->band_count[t] = 0;
     __syncthreads();  // band_u complete
     // sort buckets: 2^b per band with kBucketTarget <= E / 2^b < 2 kBucketTarget for
-    // the band's expected count E = n (F(c_{j+1}) - F(c_j)) (b = 0 below)
+    // the band's expected count E = n (F(c_{j+1}) - F(c_j)) (b = 0 below), from
+    // integers: E / kBucketTarget = n (band_u[j+1] - band_u[j]) 2^-62, so b is
+    // floor(log2) of that product minus 62, clamped to [0, 24]
+    if (t < kMaxBands) {
+        uint32_t b = 0;
+        if (static_cast<uint32_t>(t) < B) {
+            const uint64_t du = M->band_u[t + 1] - M->band_u[t];
+            const uint64_t lo = a.n * du, hi = __umul64hi(a.n, du);
+            const int L = hi ? 127 - __clzll(static_cast<long long>(hi))
+                             : (lo ? 63 - __clzll(static_cast<long long>(lo)) : -1);
+            b = L > 62 ? (L - 62 > 24 ? 24u : static_cast<uint32_t>(L - 62)) : 0u;
+        }
+        M->bk_bits[t] = b;
+    }
+    __syncthreads();
     if (t == 0) {
         uint32_t off = 0;
         for (uint32_t j = 0; j < B; ++j) {
-            const double E = nd * static_cast<double>(M->band_u[j + 1] - M->band_u[j]) * 0x1.0p-53;
-            uint32_t b = 0;
-            while (b < 24 && static_cast<double>(kBucketTarget) * static_cast<double>(2u << b) <= E) ++b;
             M->bk_off[j] = off;
-            M->bk_bits[j] = b;
-            off += 1u << b;
+            off += 1u << M->bk_bits[j];
         }
         M->bk_off[B] = off;
         M->nbuckets = off;
