@@ -289,7 +289,7 @@ __device__ void plan_batch_item(Meta *metas, const PlanArgs *args, uint32_t G, u
 {
     if (vb < G) {
         const PlanArgs a = args[vb];
-        plan_block(metas + vb, a, 3, PS);
+        plan_block(metas + vb, a, 5, PS);
         return;
     }
     if (threadIdx.x != 0) return;
