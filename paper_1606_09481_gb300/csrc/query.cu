@@ -36,7 +36,7 @@ constexpr int kListCap = 64;           // queued fringe entries per warp (>= 2 p
 constexpr int kBitWords = 128;         // decision words per warp: kChunk / 32
 constexpr uint32_t kFull = 0x80000000u;  // window half-width meaning "whole band"
 constexpr int kBatchMinBlocks = 4;         // resident CTAs per SM the batch kernel is compiled for
-constexpr int kCoreGroup = 4;              // core-writer windows whose loads are issued together
+constexpr int kCoreUnroll = 4;             // core-writer steps whose id loads are issued together
 constexpr int kHeavyGroup = 16;            // the same in the heavy kernel's core chunks
 constexpr int kFringeRounds = 4;           // heavy fringe-chunk rounds whose values load together
 
@@ -621,13 +621,12 @@ __device__ __forceinline__ void test_fringe_chunk(const QueryArgs &a, Meta *Mg, 
     }
 }
 
-// Per-warp shared state of the batch kernel.  For each band the 32 lanes' candidate
-// pieces are laid end to end as two streams: the fringe stream (every lane's
-// tested pieces, lane after lane) and the core stream (every lane's certain
-// range, lane after lane).  own[] tabulates the owner lane of kOwn consecutive
-// stream elements, one byte each, so that a lane finds the owner of any element
-// with one shared-memory load; the owners' values are read from fr / cr / oa / ob
-// (or od / osh in FP64 mode).
+// Per-warp shared state of the batch kernel.  For each band the 32 lanes' tested
+// pieces are laid end to end as the fringe stream (lane after lane).  own[]
+// tabulates the owner lane of kOwn consecutive stream elements, one byte each, so
+// that a lane finds the owner of any element with one shared-memory load; the
+// owners' values are read from fr / oid / oa / ob (or od / osh in FP64 mode).  The
+// core pieces need no table: they are written lane-major.
 constexpr uint32_t kOwn = 1024;       // stream elements whose owners are tabulated at once
 constexpr int kMaxFringe = 64;        // fringe candidates a lane keeps (two pieces of at most 32)
 
@@ -636,7 +635,7 @@ struct BatchSmem {
     uint32_t own[kOwn / 4];                  // owner lane of stream element j0 + e: byte e
     uint32_t bits[32 * kMaxFringe / 32];     // fringe decisions, bit j of word j / 32
     uint4 fr[32];                            // lane's fringe: stream start, f0, length of [f0, f1), f2
-    uint2 cr[32];                            // lane's core: c0 - stream start, vertex id
+    uint32_t oid[32];                        // lane's vertex id
     float4 oa[kFilter ? 32 : 1], ob[kFilter ? 32 : 1];  // filter values (as load_owner stores them)
     double2 od[kFilter ? 1 : 32];            // FP64 mode: phi, cosh r
     double osh[kFilter ? 1 : 32];            // FP64 mode: sinh r
@@ -704,7 +703,7 @@ __device__ __forceinline__ int decide_stream(const QueryArgs &a, const Meta *Mg,
                 else atomicMax(&C->error, kErrListFull);
             }
         }
-        if (kVerify && verify && in && dec != 2) verify_pair(a, Mg, C, W.cr[L].y, a.P.id[q], dec, coshR);
+        if (kVerify && verify && in && dec != 2) verify_pair(a, Mg, C, W.oid[L], a.P.id[q], dec, coshR);
     } else if (in) {
         const double2 v = W.od[L];
         const double chw = a.P.ch[q];
@@ -719,8 +718,8 @@ __device__ __forceinline__ int decide_stream(const QueryArgs &a, const Meta *Mg,
 // every lane computes its window and core (Sec. III-B) and the candidate pieces;
 // the warp decides the fringe stream 32 candidates at a time (all lanes busy
 // whatever the split between the lanes), reserves the band's edges with one
-// atomic add, and writes the core stream and the fringe edges as contiguous,
-// coalesced blocks.
+// atomic add, and writes the core pieces (lane-major) and the fringe edges (in
+// stream order) as contiguous blocks.
 // kMulti (a batch of graphs): batches are 32-point slices of the tiles, each warp
 // keeps the band table of its current graph in its own shared memory, and edges
 // go to the graph's output region and counter; lists and work counters live in
@@ -882,20 +881,17 @@ __device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, P
                 }
             }
             const uint32_t nl = f1 - f0, nf = nl + (f3 - f2), nc = c1 - c0;
-            uint32_t fi = nf, ci = nc;  // inclusive scans over the lanes
+            uint32_t fi = nf;  // inclusive scan over the lanes
             for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t y = __shfl_up_sync(full, fi, off), z = __shfl_up_sync(full, ci, off);
-                if (lane >= off) {
-                    fi += y;
-                    ci += z;
-                }
+                const uint32_t y = __shfl_up_sync(full, fi, off);
+                if (lane >= off) fi += y;
             }
-            const uint32_t F = __shfl_sync(full, fi, 31), T = __shfl_sync(full, ci, 31);
+            const uint32_t F = __shfl_sync(full, fi, 31), T = __reduce_add_sync(full, nc);
             if (F + T == 0) continue;
-            const uint32_t fs = fi - nf, cs = ci - nc;  // the lane's stream starts
+            const uint32_t fs = fi - nf;  // the lane's fringe stream start
             __syncwarp();  // the previous band's readers of W are done
             W.fr[lane] = make_uint4(fs, f0, nl, f2);
-            W.cr[lane] = make_uint2(c0 - cs, idv);
+            W.oid[lane] = idv;
             // 1. the fringe stream, 32 candidates per step: one decision bit each
             uint32_t nfe = 0;
             for (uint32_t j0 = 0; j0 < F; j0 += kOwn) {
@@ -918,7 +914,7 @@ __device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, P
                 __syncwarp();
             }
             // one reservation for the band's edges: [base, base + T) holds the core
-            // stream, then come the fringe edges in stream order
+            // edges, then come the fringe edges in stream order
             const uint32_t total = T + nfe;
             kept += total;
             unsigned long long base = 0;
@@ -942,40 +938,47 @@ __device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, P
                             const uint32_t j = jw + lane;
                             const uint32_t L = owner_of(W.own, j - j0);
                             const uint32_t q = fringe_pos(W.fr[L], j);
-                            write_edge<kCsr>(a, pos + __popc(word & lt), W.cr[L].y, __ldg(a.P.id + q));
+                            write_edge<kCsr>(a, pos + __popc(word & lt), W.oid[L], __ldg(a.P.id + q));
                         }
                         pos += __popc(word);
                     }
                 }
             }
-            // 3. the core stream: element j goes to base + j (coalesced); its owner
-            // from the table, the id loads of kCoreGroup windows issued together
-            for (uint32_t j0 = 0; j0 < T; j0 += kOwn) {
-                __syncwarp();
-                fill_owner(W.own, j0, cs, nc, lane);
-                __syncwarp();
-                const uint32_t jend = T - j0 > kOwn ? j0 + kOwn : T;
-                for (uint32_t jw = j0; jw < jend; jw += 32 * kCoreGroup) {
-                    uint2 o[kCoreGroup];
-                    uint32_t w[kCoreGroup];
+            // 3. the core pieces, lane-major: step t writes the t-th element of every
+            // lane's piece.  While every lane has one (t below the shortest piece)
+            // they go to base + 32 t + lane, kCoreUnroll steps with their id loads
+            // issued together; past it the lanes that still have one are ranked by
+            // a ballot.  No owner lookup per element, and every step's stores are
+            // contiguous.
+            {
+                const uint32_t mn = __reduce_min_sync(full, nc), mx = __reduce_max_sync(full, nc);
+                const uint32_t *idp = a.P.id + c0;
+                uint32_t t = 0;
+                for (; t + kCoreUnroll <= mn; t += kCoreUnroll) {
+                    uint32_t w[kCoreUnroll];
 #pragma unroll
-                    for (int g = 0; g < kCoreGroup; ++g) {
-                        const uint32_t j = jw + 32 * g + lane;
-                        o[g] = make_uint2(0u, 0u);
-                        w[g] = 0u;
-                        if (j < jend) {
-                            o[g] = W.cr[owner_of(W.own, j - j0)];
-                            w[g] = __ldg(a.P.id + (j + o[g].x));
-                        }
-                    }
+                    for (int g = 0; g < kCoreUnroll; ++g) w[g] = __ldg(idp + t + g);
 #pragma unroll
-                    for (int g = 0; g < kCoreGroup; ++g) {
-                        const uint32_t j = jw + 32 * g + lane;
-                        if (j < jend) {
-                            write_edge<kCsr>(a, base + j, o[g].y, w[g]);
-                            if (kVerify && verify) verify_pair(a, M, C, o[g].y, w[g], 1, coshR);
-                        }
+                    for (int g = 0; g < kCoreUnroll; ++g) {
+                        write_edge<kCsr>(a, base + static_cast<uint64_t>(t + g) * 32u + lane, idv, w[g]);
+                        if (kVerify && verify) verify_pair(a, M, C, idv, w[g], 1, coshR);
                     }
+                }
+                for (; t < mn; ++t) {
+                    const uint32_t w = __ldg(idp + t);
+                    write_edge<kCsr>(a, base + static_cast<uint64_t>(t) * 32u + lane, idv, w);
+                    if (kVerify && verify) verify_pair(a, M, C, idv, w, 1, coshR);
+                }
+                uint64_t pos = base + static_cast<uint64_t>(mn) * 32u;
+                for (; t < mx; ++t) {
+                    const bool act = t < nc;
+                    const uint32_t m = __ballot_sync(full, act);
+                    if (act) {
+                        const uint32_t w = __ldg(idp + t);
+                        write_edge<kCsr>(a, pos + __popc(m & lt), idv, w);
+                        if (kVerify && verify) verify_pair(a, M, C, idv, w, 1, coshR);
+                    }
+                    pos += __popc(m);
                 }
             }
         }
