@@ -629,13 +629,15 @@ __device__ __forceinline__ void test_fringe_chunk(const QueryArgs &a, Meta *Mg, 
 // core pieces need no table: they are written lane-major.
 constexpr uint32_t kOwn = 1024;       // stream elements whose owners are tabulated at once
 constexpr int kMaxFringe = 64;        // fringe candidates a lane keeps (two pieces of at most 32)
+constexpr uint32_t kAccCap = 128;     // accepted fringe pairs a warp keeps per band (single graph)
 
-template <bool kFilter>
+template <bool kFilter, uint32_t kAcc>
 struct BatchSmem {
     uint32_t own[kOwn / 4];                  // owner lane of stream element j0 + e: byte e
     uint32_t bits[32 * kMaxFringe / 32];     // fringe decisions, bit j of word j / 32
     uint4 fr[32];                            // lane's fringe: stream start, f0, length of [f0, f1), f2
     uint32_t oid[32];                        // lane's vertex id
+    uint2 acc[kAcc ? kAcc : 1];              // accepted fringe pairs (owner id, candidate id), stream order
     float4 oa[kFilter ? 32 : 1], ob[kFilter ? 32 : 1];  // filter values (as load_owner stores them)
     double2 od[kFilter ? 1 : 32];            // FP64 mode: phi, cosh r
     double osh[kFilter ? 1 : 32];            // FP64 mode: sinh r
@@ -645,9 +647,9 @@ struct BatchSmem {
 // with that per-warp size the batched range query (persistent launch) measured
 // 11.9 against 12.6 ms for the 4096-graph workload; the single-graph kernel runs
 // the same either way.
-template <bool kFilter>
+template <bool kFilter, uint32_t kAcc>
 union PerWarp {
-    BatchSmem<kFilter> b;
+    BatchSmem<kFilter, kAcc> b;
     WarpSmem unused;
 };
 
@@ -682,8 +684,8 @@ __device__ __forceinline__ uint32_t fringe_pos(uint4 r, uint32_t j)
 
 // Decide fringe stream element j (owner lane L at sorted position p, candidate q):
 // 1 = edge, 0 = no edge, 2 = undecided (queued for the FP64 recheck).
-template <bool kFilter, bool kVerify>
-__device__ __forceinline__ int decide_stream(const QueryArgs &a, const Meta *Mg, Meta *C, const BatchSmem<kFilter> &W,
+template <bool kFilter, bool kVerify, class WS>
+__device__ __forceinline__ int decide_stream(const QueryArgs &a, const Meta *Mg, Meta *C, const WS &W,
                                              uint32_t L, uint32_t p, uint32_t q, bool in, double coshR, bool verify,
                                              uint64_t &near)
 {
@@ -725,12 +727,13 @@ __device__ __forceinline__ int decide_stream(const QueryArgs &a, const Meta *Mg,
 // go to the graph's output region and counter; lists and work counters live in
 // the control block.
 template <bool kFilter, bool kCsr, bool kMulti, bool kVerify>
-__device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, PerWarp<kFilter> *Wsm)
+__device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, PerWarp<kFilter, kMulti ? 0u : kAccCap> *Wsm)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     BandShared &S = Sm[kMulti ? (threadIdx.x >> 5) : 0];
-    BatchSmem<kFilter> &W = Wsm[threadIdx.x >> 5].b;
+    auto &W = Wsm[threadIdx.x >> 5].b;
+    constexpr uint32_t kAcc = kMulti ? 0u : kAccCap;  // the persistent launch keeps its shared memory small
     Meta *C = kMulti ? a.M + a.bt.G : a.M;  // counters and lists
     Meta *M = a.M;                          // the current graph
     if (!kMulti) {
@@ -892,7 +895,9 @@ __device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, P
             __syncwarp();  // the previous band's readers of W are done
             W.fr[lane] = make_uint4(fs, f0, nl, f2);
             W.oid[lane] = idv;
-            // 1. the fringe stream, 32 candidates per step: one decision bit each
+            // 1. the fringe stream, 32 candidates per step: one decision bit each; the
+            // candidate's id is loaded with its values, and the first kAcc accepted
+            // pairs are kept in stream order
             uint32_t nfe = 0;
             for (uint32_t j0 = 0; j0 < F; j0 += kOwn) {
                 fill_owner(W.own, j0, fs, nf, lane);
@@ -901,14 +906,19 @@ __device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, P
                 for (uint32_t jw = j0; jw < jend; jw += 32) {
                     const uint32_t j = jw + lane;
                     const bool in = j < jend;
-                    uint32_t L = 0, q = 0;
+                    uint32_t L = 0, q = 0, idw = 0;
                     if (in) {
                         L = owner_of(W.own, j - j0);
                         q = fringe_pos(W.fr[L], j);
+                        if (kAcc) idw = __ldg(a.P.id + q);
                     }
                     const int dec = decide_stream<kFilter, kVerify>(a, M, C, W, L, p0 + L, q, in, coshR, verify, near);
                     const uint32_t word = __ballot_sync(full, dec == 1);
                     if (lane == 0) W.bits[jw >> 5] = word;
+                    if (kAcc && dec == 1) {
+                        const uint32_t at = nfe + __popc(word & lt);
+                        if (at < kAcc) W.acc[at] = make_uint2(W.oid[L], idw);
+                    }
                     nfe += __popc(word);
                 }
                 __syncwarp();
@@ -922,8 +932,14 @@ __device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, P
             base = __shfl_sync(full, base, 0);
             if (base + total > cap) continue;
             base += obase;
-            // 2. the fringe edges (the owner table still holds the last fringe chunk)
-            if (nfe) {
+            // 2. the fringe edges: from the kept pairs when all fit, else by a replay
+            // of the decision bits (the owner table still holds the last fringe chunk)
+            if (kAcc && nfe && nfe <= kAcc) {
+                for (uint32_t e = lane; e < nfe; e += 32) {
+                    const uint2 v = W.acc[e];
+                    write_edge<kCsr>(a, base + T + e, v.x, v.y);
+                }
+            } else if (nfe) {
                 uint64_t pos = base + T;
                 for (uint32_t j0 = 0; j0 < F; j0 += kOwn) {
                     if (F > kOwn) {
@@ -992,7 +1008,7 @@ template <bool kFilter, bool kCsr, bool kMulti, bool kVerify>
 __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryArgs a)
 {
     __shared__ BandShared Sm[kMulti ? kWarps : 1];
-    __shared__ PerWarp<kFilter> Wsm[kWarps];
+    __shared__ PerWarp<kFilter, kMulti ? 0u : kAccCap> Wsm[kWarps];
     batch_body<kFilter, kCsr, kMulti, kVerify>(a, Sm, Wsm);
 }
 
@@ -1504,11 +1520,11 @@ union PersistSmem {
     } slots;
     struct {
         BandShared S[kWarps];
-        PerWarp<true> W[kWarps];
+        PerWarp<true, 0u> W[kWarps];
     } qf;
     struct {
         BandShared S[kWarps];
-        PerWarp<false> W[kWarps];
+        PerWarp<false, 0u> W[kWarps];
     } qd;
     WarpSmem heavy[kWarps];
 };
