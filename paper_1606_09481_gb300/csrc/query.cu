@@ -629,7 +629,7 @@ __device__ __forceinline__ void test_fringe_chunk(const QueryArgs &a, Meta *Mg, 
 // core pieces need no table: they are written lane-major.
 constexpr uint32_t kOwn = 1024;       // stream elements whose owners are tabulated at once
 constexpr int kMaxFringe = 64;        // fringe candidates a lane keeps (two pieces of at most 32)
-constexpr uint32_t kAccCap = 128;     // accepted fringe pairs a warp keeps per band (single graph)
+constexpr uint32_t kAccCap = 128;     // accepted fringe pairs a warp keeps per band
 
 template <bool kFilter, uint32_t kAcc>
 struct BatchSmem {
@@ -643,10 +643,11 @@ struct BatchSmem {
     double osh[kFilter ? 1 : 32];            // FP64 mode: sinh r
 };
 
-// A warp's shared memory in the batch kernel.  The union also spans WarpSmem:
-// with that per-warp size the batched range query (persistent launch) measured
-// 11.9 against 12.6 ms for the 4096-graph workload; the single-graph kernel runs
-// the same either way.
+// A warp's shared memory in the batch kernel, at least the size of WarpSmem:
+// without kept fringe pairs, padding BatchSmem to that size made the batched
+// range query (persistent launch) 11.9 instead of 12.6 ms for the 4096-graph
+// workload.  With 128 kept pairs BatchSmem is the larger; the persistent
+// kernel's shared memory (65 KB) still leaves room for 3 CTAs per SM.
 template <bool kFilter, uint32_t kAcc>
 union PerWarp {
     BatchSmem<kFilter, kAcc> b;
@@ -727,13 +728,13 @@ __device__ __forceinline__ int decide_stream(const QueryArgs &a, const Meta *Mg,
 // go to the graph's output region and counter; lists and work counters live in
 // the control block.
 template <bool kFilter, bool kCsr, bool kMulti, bool kVerify>
-__device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, PerWarp<kFilter, kMulti ? 0u : kAccCap> *Wsm)
+__device__ __forceinline__ void batch_body(const QueryArgs &a, BandShared *Sm, PerWarp<kFilter, kAccCap> *Wsm)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     BandShared &S = Sm[kMulti ? (threadIdx.x >> 5) : 0];
     auto &W = Wsm[threadIdx.x >> 5].b;
-    constexpr uint32_t kAcc = kMulti ? 0u : kAccCap;  // the persistent launch keeps its shared memory small
+    constexpr uint32_t kAcc = kAccCap;
     Meta *C = kMulti ? a.M + a.bt.G : a.M;  // counters and lists
     Meta *M = a.M;                          // the current graph
     if (!kMulti) {
@@ -1008,7 +1009,7 @@ template <bool kFilter, bool kCsr, bool kMulti, bool kVerify>
 __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) batch_kernel(QueryArgs a)
 {
     __shared__ BandShared Sm[kMulti ? kWarps : 1];
-    __shared__ PerWarp<kFilter, kMulti ? 0u : kAccCap> Wsm[kWarps];
+    __shared__ PerWarp<kFilter, kAccCap> Wsm[kWarps];
     batch_body<kFilter, kCsr, kMulti, kVerify>(a, Sm, Wsm);
 }
 
@@ -1520,11 +1521,11 @@ union PersistSmem {
     } slots;
     struct {
         BandShared S[kWarps];
-        PerWarp<true, 0u> W[kWarps];
+        PerWarp<true, kAccCap> W[kWarps];
     } qf;
     struct {
         BandShared S[kWarps];
-        PerWarp<false, 0u> W[kWarps];
+        PerWarp<false, kAccCap> W[kWarps];
     } qd;
     WarpSmem heavy[kWarps];
 };
